@@ -1,0 +1,162 @@
+"""Plain CPU oracle for image-based invasion percolation (arXiv 2101.03240).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg may import this package; the product library
+never does.  The arithmetic lives in ``ibip_oracle.c`` (plain C, compiled
+with gcc on first use); this module only marshals numpy arrays to it.
+
+Functions mirror the C entry points; every array argument is a C-contiguous
+numpy array with the image's shape (nx, ny, nz) unless stated otherwise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ibip_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_SO = os.path.join(_OUT_DIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+OK = 0
+STEP_LIMIT = -4
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (gcc, OpenMP) unless the shared object is newer
+    than its source.  Returns the path of the shared object."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + ".%d.tmp" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            P = C.c_void_p
+            i32, i64, dbl = C.c_int, C.c_int64, C.c_double
+            sig = {
+                "or_edt_brute": (None, [P, i32, i32, i32, P]),
+                "or_edt_sep": (None, [P, i32, i32, i32, P]),
+                "or_invade_scan": (i64, [P, P, i32, i32, i32, i32, i64, P, P, P, i64, P]),
+                "or_invade_heap": (i64, [P, P, i32, i32, i32, i32, i64, P, P, P, i64, P]),
+                "or_trap_bfs": (None, [P, i32, i32, i32, i32, i32, P, P]),
+                "or_trap_uf": (None, [P, i32, i32, i32, i32, i32, P, P]),
+                "or_count_unconnected": (i64, [P, i32, i32, i32, i32]),
+                "or_mio_plain": (None, [P, P, i32, i32, i32, i32, P, i32, P, P]),
+                "or_mio_edt": (None, [P, P, i32, i32, i32, i32, P, i32, P, P]),
+                "or_pc_curve": (None, [P, i64, P, i64, dbl, dbl, dbl, P, P, P]),
+                "or_abi_version": (i32, []),
+            }
+            for name, (res, args) in sig.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data
+
+
+def _img(image):
+    a = np.ascontiguousarray(image, dtype=np.uint8)
+    assert a.ndim == 3
+    return a
+
+
+def edt_brute(image):
+    """Squared EDT by brute force over all solid voxels (Section 2.1)."""
+    a = _img(image)
+    out = np.empty(a.shape, np.int32)
+    lib().or_edt_brute(_p(a), *a.shape, _p(out))
+    return out
+
+
+def edt(image):
+    """Squared EDT by three separable 1-D min-plus passes (same values)."""
+    a = _img(image)
+    out = np.empty(a.shape, np.int32)
+    lib().or_edt_sep(_p(a), *a.shape, _p(out))
+    return out
+
+
+def invade(image, dt2, inlet=0, max_steps=None, method="heap", capacity=None):
+    """Run the invasion (Section 2.1).  Returns (seq, step_r2, step_centre,
+    status).  method: "heap" (priority queue) or "scan" (rescan every step)."""
+    a = _img(image)
+    d = np.ascontiguousarray(dt2, dtype=np.int32)
+    n = a.size
+    npore = int(np.count_nonzero(a))
+    if max_steps is None:
+        max_steps = npore
+    cap = npore if capacity is None else int(capacity)
+    seq = np.empty(a.shape, np.int32)
+    r2 = np.zeros(max(cap, 1), np.int32)
+    cen = np.zeros(max(cap, 1), np.int32)
+    st = C.c_int(0)
+    f = lib().or_invade_heap if method == "heap" else lib().or_invade_scan
+    k = f(_p(a), _p(d), *a.shape, int(inlet), int(max_steps), _p(seq), _p(r2), _p(cen), cap,
+          C.addressof(st))
+    k = int(k)
+    kk = min(k, cap)
+    del n
+    return seq, r2[:kk].copy(), cen[:kk].copy(), int(st.value), k
+
+
+def trapping(seq, outlet=1, rerank=False, method="uf"):
+    """Defending-phase trapping (Section 2.2.3).  Returns (trapped uint8,
+    seq_out int32)."""
+    s = np.ascontiguousarray(seq, dtype=np.int32)
+    tr = np.empty(s.shape, np.uint8)
+    out = np.empty(s.shape, np.int32)
+    f = lib().or_trap_uf if method == "uf" else lib().or_trap_bfs
+    f(_p(s), *s.shape, int(outlet), int(bool(rerank)), _p(tr), _p(out))
+    return tr, out
+
+
+def count_unconnected(seq, inlet=0):
+    """Invaded voxels not joined to the inlet face through voxels invaded no
+    later than themselves (0 for a valid invasion)."""
+    s = np.ascontiguousarray(seq, dtype=np.int32)
+    return int(lib().or_count_unconnected(_p(s), *s.shape, int(inlet)))
+
+
+def morph_drainage(image, dt2, levels, inlet=0, method="edt"):
+    """Morphological-opening drainage (Section 2.4.1).  Returns (level int32,
+    counts int64[L])."""
+    a = _img(image)
+    d = np.ascontiguousarray(dt2, dtype=np.int32)
+    T = np.ascontiguousarray(levels, dtype=np.int32)
+    lev = np.empty(a.shape, np.int32)
+    cnt = np.zeros(max(len(T), 1), np.int64)
+    f = lib().or_mio_edt if method == "edt" else lib().or_mio_plain
+    f(_p(a), _p(d), *a.shape, int(inlet), _p(T), len(T), _p(lev), _p(cnt))
+    return lev, cnt[:len(T)].copy()
+
+
+def pc_curve(seq, step_r2, voxel_m=5e-6, sigma=0.072, theta_deg=180.0, sat_image=False):
+    """Saturation and capillary pressure per step (Sections 2.2.1-2.2.2).
+    Returns (S float32[K], Pc float32[K], sat_image float32 or None)."""
+    s = np.ascontiguousarray(seq, dtype=np.int32)
+    r2 = np.ascontiguousarray(step_r2, dtype=np.int32)
+    K = len(r2)
+    S = np.zeros(max(K, 1), np.float32)
+    P = np.zeros(max(K, 1), np.float32)
+    img = np.empty(s.shape, np.float32) if sat_image else None
+    lib().or_pc_curve(_p(s), s.size, _p(r2), K, float(voxel_m), float(sigma), float(theta_deg),
+                      _p(S), _p(P), _p(img))
+    return S[:K].copy(), P[:K].copy(), img

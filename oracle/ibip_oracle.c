@@ -1,0 +1,659 @@
+/*
+ * ibip_oracle.c -- plain, slow CPU oracle for image-based invasion
+ * percolation (IBIP; Gostick, Yang & Boek, "Simulating volume-controlled
+ * invasion of a non-wetting fluid in volumetric images using basic image
+ * processing tools", arXiv 2101.03240).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the correctness reference for the
+ * CUDA library.  Only the test suite, the smoke check and the benchmark's
+ * CPU-baseline leg may load it.  It shares no source, header, table or helper
+ * with the CUDA path, and the CUDA path never calls it.
+ *
+ * Conventions (the paper is silent on all of them):
+ *   - image shape (nx, ny, nz), C order, idx = (x*ny + y)*nz + z;
+ *   - image byte nonzero = pore (void), 0 = solid; 6-connectivity;
+ *   - voxels outside the image are NOT solid;
+ *   - dt2: squared Euclidean distance to the nearest solid voxel, 0 on solid,
+ *     INT32_MAX on pore when the image has no solid at all;
+ *   - seq: 0 solid, -1 pore never invaded, k >= 1 invaded at step k;
+ *   - faces: 0=X0 (x=0) 1=X1 (x=nx-1) 2=Y0 3=Y1 4=Z0 5=Z1.
+ *
+ * Each function names the passage of the paper it follows.  Everything is
+ * written for obviousness, not speed, except where a second, faster variant
+ * is provided for large images; every fast variant is checked bit-exact
+ * against its plain twin by the tests.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_INF32 INT32_MAX
+#define OR_OK 0
+#define OR_STEP_LIMIT (-4)
+#define OR_CAPACITY (-1)
+
+static int64_t lin(int64_t x, int64_t y, int64_t z, int64_t ny, int64_t nz)
+{
+    return (x * ny + y) * nz + z;
+}
+
+static void coords(int64_t v, int64_t ny, int64_t nz, int64_t *x, int64_t *y, int64_t *z)
+{
+    *z = v % nz;
+    *y = (v / nz) % ny;
+    *x = v / (nz * ny);
+}
+
+static int on_face(int64_t x, int64_t y, int64_t z, int nx, int ny, int nz, int face)
+{
+    switch (face) {
+    case 0: return x == 0;
+    case 1: return x == nx - 1;
+    case 2: return y == 0;
+    case 3: return y == ny - 1;
+    case 4: return z == 0;
+    case 5: return z == nz - 1;
+    default: return 0;
+    }
+}
+
+static const int NB[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
+
+/* largest r >= 0 with r*r < r2 (r2 >= 1), i.e. the half-width of the ball
+ * d^2 < r2 along one axis */
+static int64_t ball_halfwidth(int64_t r2)
+{
+    int64_t r = (int64_t)sqrt((double)(r2 - 1));
+    while (r > 0 && r * r > r2 - 1) r--;
+    while ((r + 1) * (r + 1) <= r2 - 1) r++;
+    return r;
+}
+
+/* ------------------------------------------------------------------------
+ * Distance transform (Section 2.1: "the distance transform (dt) of the pore
+ * space image").  dt2 is the squared Euclidean distance from each pore voxel
+ * to the nearest solid voxel.
+ * ---------------------------------------------------------------------- */
+
+/* EDT-brute: the definition written out.  O(N * Nsolid). */
+void or_edt_brute(const uint8_t *img, int nx, int ny, int nz, int32_t *dt2)
+{
+    int64_t N = (int64_t)nx * ny * nz, ns = 0;
+    int64_t *sx = malloc(sizeof(int64_t) * (N ? N : 1) * 3);
+    for (int64_t v = 0; v < N; v++)
+        if (!img[v]) {
+            int64_t x, y, z;
+            coords(v, ny, nz, &x, &y, &z);
+            sx[3 * ns] = x; sx[3 * ns + 1] = y; sx[3 * ns + 2] = z;
+            ns++;
+        }
+    for (int64_t v = 0; v < N; v++) {
+        if (!img[v]) { dt2[v] = 0; continue; }
+        if (ns == 0) { dt2[v] = OR_INF32; continue; }
+        int64_t x, y, z, best = INT64_MAX;
+        coords(v, ny, nz, &x, &y, &z);
+        for (int64_t s = 0; s < ns; s++) {
+            int64_t dx = x - sx[3 * s], dy = y - sx[3 * s + 1], dz = z - sx[3 * s + 2];
+            int64_t d = dx * dx + dy * dy + dz * dz;
+            if (d < best) best = d;
+        }
+        dt2[v] = (int32_t)best;
+    }
+    free(sx);
+}
+
+/* One 1-D min-plus pass  g'(i) = min_j g(j) + (i-j)^2  along a line of n
+ * values with stride s.  INT64_MAX marks "no solid seen on this line".  The
+ * search walks j outward from i and stops once (i-j)^2 alone is no smaller
+ * than the best value found: every later term is at least that large. */
+static void minplus_line(const int64_t *g, int64_t *out, int64_t n, int64_t s)
+{
+    for (int64_t i = 0; i < n; i++) {
+        int64_t best = g[i * s];
+        for (int64_t d = 1; d < n; d++) {
+            if (best != INT64_MAX && d * d >= best) break;
+            int64_t j0 = i - d, j1 = i + d;
+            if (j0 < 0 && j1 >= n) break;
+            if (j0 >= 0 && g[j0 * s] != INT64_MAX && g[j0 * s] + d * d < best) best = g[j0 * s] + d * d;
+            if (j1 < n && g[j1 * s] != INT64_MAX && g[j1 * s] + d * d < best) best = g[j1 * s] + d * d;
+        }
+        out[i * s] = best;
+    }
+}
+
+/* EDT-sep: the squared EDT is separable (a sum of squared per-axis offsets),
+ * so three 1-D min-plus passes give the same value as EDT-brute.  `feat`
+ * marks the feature voxels the distance is taken to (solid for the pore
+ * EDT).  Output INT32_MAX where no feature exists in the whole image. */
+static void edt_sep_core(const uint8_t *feat, int nx, int ny, int nz, int32_t *out)
+{
+    int64_t N = (int64_t)nx * ny * nz;
+    int64_t *a = malloc(sizeof(int64_t) * (N ? N : 1));
+    int64_t *b = malloc(sizeof(int64_t) * (N ? N : 1));
+    for (int64_t v = 0; v < N; v++) a[v] = feat[v] ? 0 : INT64_MAX;
+    /* along z */
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t r = 0; r < (int64_t)nx * ny; r++) minplus_line(a + r * nz, b + r * nz, nz, 1);
+    /* along y */
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t q = 0; q < (int64_t)nx * nz; q++) {
+        int64_t x = q / nz, z = q % nz;
+        minplus_line(b + x * ny * nz + z, a + x * ny * nz + z, ny, nz);
+    }
+    /* along x */
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t q = 0; q < (int64_t)ny * nz; q++) minplus_line(a + q, b + q, nx, (int64_t)ny * nz);
+    for (int64_t v = 0; v < N; v++) out[v] = b[v] == INT64_MAX ? OR_INF32 : (int32_t)b[v];
+    free(a);
+    free(b);
+}
+
+void or_edt_sep(const uint8_t *img, int nx, int ny, int nz, int32_t *dt2)
+{
+    int64_t N = (int64_t)nx * ny * nz;
+    uint8_t *solid = malloc(N ? N : 1);
+    for (int64_t v = 0; v < N; v++) solid[v] = img[v] == 0;
+    edt_sep_core(solid, nx, ny, nz, dt2);
+    free(solid);
+}
+
+/* ------------------------------------------------------------------------
+ * Invasion (Section 2.1, Figures 1 and 2).  Each step picks the candidate
+ * voxel with the largest distance value and inserts a sphere there, writing
+ * the step number only into voxels not invaded before.
+ *
+ * Readings used (the paper describes a variant; these fix the variant):
+ *   candidates = uninvaded pore voxels that are 6-adjacent to an invaded
+ *                voxel, or lie on the inlet face (the face behaves as an
+ *                invaded reservoir just outside the image);
+ *   one sphere per step; equal dt2 -> lowest linear index;
+ *   the sphere of step k is {p : |p - c|^2 < dt2[c]}.
+ * ---------------------------------------------------------------------- */
+
+/* write step k into every uninvaded voxel of the ball; returns how many */
+static int64_t stamp(int32_t *seq, int nx, int ny, int nz, int64_t c, int64_t r2, int32_t k,
+                     int64_t *newlist)
+{
+    int64_t cx, cy, cz, n = 0;
+    coords(c, ny, nz, &cx, &cy, &cz);
+    int64_t r = ball_halfwidth(r2);
+    int64_t x0 = cx - r < 0 ? 0 : cx - r, x1 = cx + r > nx - 1 ? nx - 1 : cx + r;
+    int64_t y0 = cy - r < 0 ? 0 : cy - r, y1 = cy + r > ny - 1 ? ny - 1 : cy + r;
+    int64_t z0 = cz - r < 0 ? 0 : cz - r, z1 = cz + r > nz - 1 ? nz - 1 : cz + r;
+    for (int64_t x = x0; x <= x1; x++)
+        for (int64_t y = y0; y <= y1; y++)
+            for (int64_t z = z0; z <= z1; z++) {
+                int64_t d = (x - cx) * (x - cx) + (y - cy) * (y - cy) + (z - cz) * (z - cz);
+                if (d >= r2) continue;
+                int64_t p = lin(x, y, z, ny, nz);
+                if (seq[p] != -1) continue;
+                seq[p] = k;
+                if (newlist) newlist[n] = p;
+                n++;
+            }
+    return n;
+}
+
+static int has_invaded_nb(const int32_t *seq, int nx, int ny, int nz, int64_t x, int64_t y, int64_t z)
+{
+    for (int d = 0; d < 6; d++) {
+        int64_t a = x + NB[d][0], b = y + NB[d][1], c = z + NB[d][2];
+        if (a < 0 || b < 0 || c < 0 || a >= nx || b >= ny || c >= nz) continue;
+        if (seq[lin(a, b, c, ny, nz)] >= 1) return 1;
+    }
+    return 0;
+}
+
+/* Invade-scan: every step rescans the whole image for the candidate set,
+ * exactly as the definition reads.  O(steps * N).  Returns the number of
+ * steps K; *status = OR_STEP_LIMIT if max_steps stopped a non-empty front. */
+int64_t or_invade_scan(const uint8_t *img, const int32_t *dt2, int nx, int ny, int nz, int inlet,
+                       int64_t max_steps, int32_t *seq, int32_t *step_r2, int32_t *step_centre,
+                       int64_t cap, int *status)
+{
+    int64_t N = (int64_t)nx * ny * nz, k = 0;
+    for (int64_t v = 0; v < N; v++) seq[v] = img[v] ? -1 : 0;
+    *status = OR_OK;
+    for (;;) {
+        int64_t best = -1, bestd = -1;
+        for (int64_t v = 0; v < N; v++) {
+            if (seq[v] != -1) continue;
+            int64_t x, y, z;
+            coords(v, ny, nz, &x, &y, &z);
+            if (!on_face(x, y, z, nx, ny, nz, inlet) && !has_invaded_nb(seq, nx, ny, nz, x, y, z)) continue;
+            if (dt2[v] > bestd) { bestd = dt2[v]; best = v; }
+        }
+        if (best < 0) break;
+        if (k >= max_steps) { *status = OR_STEP_LIMIT; break; }
+        k++;
+        stamp(seq, nx, ny, nz, best, bestd, (int32_t)k, NULL);
+        if (k <= cap) {
+            step_r2[k - 1] = (int32_t)bestd;
+            if (step_centre) step_centre[k - 1] = (int32_t)best;
+        }
+    }
+    return k;
+}
+
+/* max-heap of 64-bit keys; key = dt2 << 32 | (0xffffffff - idx), so the
+ * largest key is the largest dt2 with the smallest index */
+typedef struct { uint64_t *a; int64_t n, cap; } heap_t;
+
+static void hpush(heap_t *h, uint64_t key)
+{
+    if (h->n == h->cap) {
+        h->cap = h->cap ? 2 * h->cap : 1024;
+        h->a = realloc(h->a, sizeof(uint64_t) * h->cap);
+    }
+    int64_t i = h->n++;
+    while (i > 0) {
+        int64_t p = (i - 1) / 2;
+        if (h->a[p] >= key) break;
+        h->a[i] = h->a[p];
+        i = p;
+    }
+    h->a[i] = key;
+}
+
+static uint64_t hpop(heap_t *h)
+{
+    uint64_t top = h->a[0], last = h->a[--h->n];
+    int64_t i = 0;
+    for (;;) {
+        int64_t l = 2 * i + 1, r = l + 1, m = i;
+        uint64_t mv = last;
+        if (l < h->n && h->a[l] > mv) { m = l; mv = h->a[l]; }
+        if (r < h->n && h->a[r] > mv) { m = r; mv = h->a[r]; }
+        if (m == i) break;
+        h->a[i] = h->a[m];
+        i = m;
+    }
+    if (h->n) h->a[i] = last;
+    return top;
+}
+
+static uint64_t hkey(int32_t d, int64_t idx)
+{
+    return ((uint64_t)(uint32_t)d << 32) | (uint64_t)(0xffffffffu - (uint32_t)idx);
+}
+
+/* Invade-heap: the same process with the candidate set kept in a priority
+ * queue (the classic invasion-percolation queue of Wilkinson & Willemsen,
+ * cited in Section 1).  A voxel is queued once, when it first becomes a
+ * candidate; popped entries already invaded are skipped.  Same result as
+ * invade-scan, far faster; used on large images and as the timed CPU
+ * baseline. */
+int64_t or_invade_heap(const uint8_t *img, const int32_t *dt2, int nx, int ny, int nz, int inlet,
+                       int64_t max_steps, int32_t *seq, int32_t *step_r2, int32_t *step_centre,
+                       int64_t cap, int *status)
+{
+    int64_t N = (int64_t)nx * ny * nz, k = 0;
+    uint8_t *queued = calloc(N ? N : 1, 1);
+    int64_t *newlist = malloc(sizeof(int64_t) * (N ? N : 1));
+    heap_t h = {0};
+    for (int64_t v = 0; v < N; v++) {
+        seq[v] = img[v] ? -1 : 0;
+        int64_t x, y, z;
+        coords(v, ny, nz, &x, &y, &z);
+        if (img[v] && on_face(x, y, z, nx, ny, nz, inlet)) {
+            queued[v] = 1;
+            hpush(&h, hkey(dt2[v], v));
+        }
+    }
+    *status = OR_OK;
+    while (h.n) {
+        uint64_t key = h.a[0];
+        int64_t c = (int64_t)(0xffffffffu - (uint32_t)(key & 0xffffffffu));
+        if (seq[c] != -1) { hpop(&h); continue; }
+        if (k >= max_steps) { *status = OR_STEP_LIMIT; break; }
+        hpop(&h);
+        k++;
+        int64_t r2 = dt2[c];
+        int64_t n = stamp(seq, nx, ny, nz, c, r2, (int32_t)k, newlist);
+        if (k <= cap) {
+            step_r2[k - 1] = (int32_t)r2;
+            if (step_centre) step_centre[k - 1] = (int32_t)c;
+        }
+        for (int64_t i = 0; i < n; i++) {
+            int64_t x, y, z;
+            coords(newlist[i], ny, nz, &x, &y, &z);
+            for (int d = 0; d < 6; d++) {
+                int64_t a = x + NB[d][0], b = y + NB[d][1], cc = z + NB[d][2];
+                if (a < 0 || b < 0 || cc < 0 || a >= nx || b >= ny || cc >= nz) continue;
+                int64_t q = lin(a, b, cc, ny, nz);
+                if (seq[q] != -1 || queued[q]) continue;
+                queued[q] = 1;
+                hpush(&h, hkey(dt2[q], q));
+            }
+        }
+    }
+    free(h.a);
+    free(queued);
+    free(newlist);
+    return k;
+}
+
+/* ------------------------------------------------------------------------
+ * Trapping (Section 2.2.3).  Thresholding the sequence in decreasing order,
+ * a voxel invaded at step k is trapped when, just before step k, it is cut
+ * off from the outlet face by invaded voxels: no 6-path through pore voxels
+ * whose sequence value is >= k (never-invaded pore counts as +infinity)
+ * joins it to a pore voxel on the outlet face.  Only invaded voxels can be
+ * trapped; outlet-face voxels never are.
+ * ---------------------------------------------------------------------- */
+
+static int64_t seq_inf(int32_t s) { return s == -1 ? INT64_MAX : s; }
+
+static int32_t max_seq(const int32_t *seq, int64_t N)
+{
+    int32_t K = 0;
+    for (int64_t v = 0; v < N; v++) if (seq[v] > K) K = seq[v];
+    return K;
+}
+
+/* dense rank of the step values that survive (Section 2.2.3: the sequence is
+ * re-ranked to be contiguous after trapped voxels are reset) */
+static void rerank(int32_t *s, int64_t N)
+{
+    int32_t K = max_seq(s, N);
+    int32_t *map = calloc((size_t)K + 1, sizeof(int32_t));
+    for (int64_t v = 0; v < N; v++) if (s[v] >= 1) map[s[v]] = 1;
+    int32_t r = 0;
+    for (int32_t k = 1; k <= K; k++) if (map[k]) map[k] = ++r;
+    for (int64_t v = 0; v < N; v++) if (s[v] >= 1) s[v] = map[s[v]];
+    free(map);
+}
+
+static void finish_trap(const int32_t *seq, int64_t N, const uint8_t *trapped, int do_rerank, int32_t *seq_out)
+{
+    if (!seq_out) return;
+    for (int64_t v = 0; v < N; v++) seq_out[v] = trapped[v] ? -1 : seq[v];
+    if (do_rerank) rerank(seq_out, N);
+}
+
+/* Trap-BFS: for every step k, flood from the outlet face through voxels with
+ * seq >= k; the step-k voxels not reached are trapped.  O(K * N). */
+void or_trap_bfs(const int32_t *seq, int nx, int ny, int nz, int outlet, int do_rerank,
+                 uint8_t *trapped, int32_t *seq_out)
+{
+    int64_t N = (int64_t)nx * ny * nz;
+    int32_t K = max_seq(seq, N);
+    uint8_t *seen = malloc(N ? N : 1);
+    int64_t *q = malloc(sizeof(int64_t) * (N ? N : 1));
+    memset(trapped, 0, N);
+    for (int32_t k = 1; k <= K; k++) {
+        memset(seen, 0, N);
+        int64_t qh = 0, qt = 0;
+        for (int64_t v = 0; v < N; v++) {
+            if (seq[v] == 0 || seq_inf(seq[v]) < k) continue;
+            int64_t x, y, z;
+            coords(v, ny, nz, &x, &y, &z);
+            if (on_face(x, y, z, nx, ny, nz, outlet)) { seen[v] = 1; q[qt++] = v; }
+        }
+        while (qh < qt) {
+            int64_t v = q[qh++], x, y, z;
+            coords(v, ny, nz, &x, &y, &z);
+            for (int d = 0; d < 6; d++) {
+                int64_t a = x + NB[d][0], b = y + NB[d][1], c = z + NB[d][2];
+                if (a < 0 || b < 0 || c < 0 || a >= nx || b >= ny || c >= nz) continue;
+                int64_t u = lin(a, b, c, ny, nz);
+                if (seen[u] || seq[u] == 0 || seq_inf(seq[u]) < k) continue;
+                seen[u] = 1;
+                q[qt++] = u;
+            }
+        }
+        for (int64_t v = 0; v < N; v++) if (seq[v] == k && !seen[v]) trapped[v] = 1;
+    }
+    finish_trap(seq, N, trapped, do_rerank, seq_out);
+    free(seen);
+    free(q);
+}
+
+static int64_t uf_find(int64_t *p, int64_t a)
+{
+    while (p[a] != a) { p[a] = p[p[a]]; a = p[a]; }
+    return a;
+}
+
+static void uf_union(int64_t *p, int64_t *sz, int64_t a, int64_t b)
+{
+    a = uf_find(p, a);
+    b = uf_find(p, b);
+    if (a == b) return;
+    if (sz[a] < sz[b]) { int64_t t = a; a = b; b = t; }
+    p[b] = a;
+    sz[a] += sz[b];
+}
+
+/* voxel indices grouped by sequence value: never-invaded pore first, then
+ * k = K, K-1, ..., 1 (order[start[g] .. start[g+1]) is group g) */
+static void group_desc(const int32_t *seq, int64_t N, int32_t K, int64_t **order_out, int64_t **start_out)
+{
+    int64_t G = (int64_t)K + 1; /* group 0: seq = -1; group g >= 1: seq = K + 1 - g */
+    int64_t *cnt = calloc(G + 1, sizeof(int64_t));
+    int64_t *order = malloc(sizeof(int64_t) * (N ? N : 1));
+    for (int64_t v = 0; v < N; v++) {
+        if (seq[v] == 0) continue;
+        int64_t g = seq[v] == -1 ? 0 : (int64_t)K + 1 - seq[v];
+        cnt[g + 1]++;
+    }
+    for (int64_t g = 0; g < G; g++) cnt[g + 1] += cnt[g];
+    int64_t *pos = malloc(sizeof(int64_t) * (G + 1));
+    memcpy(pos, cnt, sizeof(int64_t) * (G + 1));
+    for (int64_t v = 0; v < N; v++) {
+        if (seq[v] == 0) continue;
+        int64_t g = seq[v] == -1 ? 0 : (int64_t)K + 1 - seq[v];
+        order[pos[g]++] = v;
+    }
+    free(pos);
+    *order_out = order;
+    *start_out = cnt;
+}
+
+/* Trap-UF: the reverse search of Section 2.2.3 (after Masson 2016) done once
+ * with a union-find: voxels are added in decreasing sequence order, joined to
+ * already-added pore neighbours and to a virtual outlet node; a step-k voxel
+ * is trapped iff, after all step-k voxels are added, its set does not hold
+ * the outlet node.  Same result as Trap-BFS in O(N alpha(N)). */
+void or_trap_uf(const int32_t *seq, int nx, int ny, int nz, int outlet, int do_rerank,
+                uint8_t *trapped, int32_t *seq_out)
+{
+    int64_t N = (int64_t)nx * ny * nz;
+    int32_t K = max_seq(seq, N);
+    int64_t *order, *start;
+    group_desc(seq, N, K, &order, &start);
+    int64_t *p = malloc(sizeof(int64_t) * (N + 1)), *sz = malloc(sizeof(int64_t) * (N + 1));
+    uint8_t *added = calloc(N ? N : 1, 1);
+    for (int64_t v = 0; v <= N; v++) { p[v] = v; sz[v] = 1; }
+    memset(trapped, 0, N);
+    for (int64_t g = 0; g <= K; g++) {
+        for (int64_t i = start[g]; i < start[g + 1]; i++) {
+            int64_t v = order[i], x, y, z;
+            added[v] = 1;
+            coords(v, ny, nz, &x, &y, &z);
+            if (on_face(x, y, z, nx, ny, nz, outlet)) uf_union(p, sz, v, N);
+            for (int d = 0; d < 6; d++) {
+                int64_t a = x + NB[d][0], b = y + NB[d][1], c = z + NB[d][2];
+                if (a < 0 || b < 0 || c < 0 || a >= nx || b >= ny || c >= nz) continue;
+                int64_t u = lin(a, b, c, ny, nz);
+                if (added[u]) uf_union(p, sz, v, u);
+            }
+        }
+        if (g == 0) continue; /* never-invaded voxels are not "trapped" */
+        for (int64_t i = start[g]; i < start[g + 1]; i++)
+            if (uf_find(p, order[i]) != uf_find(p, N)) trapped[order[i]] = 1;
+    }
+    finish_trap(seq, N, trapped, do_rerank, seq_out);
+    free(order); free(start); free(p); free(sz); free(added);
+}
+
+/* ------------------------------------------------------------------------
+ * Checks used by the tests to pin the invasion (not part of the method).
+ * ---------------------------------------------------------------------- */
+
+/* Number of invaded voxels that are NOT 6-connected to the inlet face
+ * through voxels with 1 <= seq <= their own step (voxels added in
+ * increasing step order to a union-find with a virtual inlet node). */
+int64_t or_count_unconnected(const int32_t *seq, int nx, int ny, int nz, int inlet)
+{
+    int64_t N = (int64_t)nx * ny * nz, bad = 0;
+    int32_t K = max_seq(seq, N);
+    int64_t *cnt = calloc((size_t)K + 2, sizeof(int64_t));
+    int64_t *order = malloc(sizeof(int64_t) * (N ? N : 1));
+    for (int64_t v = 0; v < N; v++) if (seq[v] >= 1) cnt[seq[v] + 1]++;
+    for (int32_t k = 0; k <= K; k++) cnt[k + 1] += cnt[k];
+    int64_t *pos = malloc(sizeof(int64_t) * ((size_t)K + 2));
+    memcpy(pos, cnt, sizeof(int64_t) * ((size_t)K + 2));
+    for (int64_t v = 0; v < N; v++) if (seq[v] >= 1) order[pos[seq[v]]++] = v;
+    int64_t *p = malloc(sizeof(int64_t) * (N + 1)), *sz = malloc(sizeof(int64_t) * (N + 1));
+    for (int64_t v = 0; v <= N; v++) { p[v] = v; sz[v] = 1; }
+    for (int32_t k = 1; k <= K; k++) {
+        for (int64_t i = cnt[k]; i < cnt[k + 1]; i++) {
+            int64_t v = order[i], x, y, z;
+            coords(v, ny, nz, &x, &y, &z);
+            if (on_face(x, y, z, nx, ny, nz, inlet)) uf_union(p, sz, v, N);
+            for (int d = 0; d < 6; d++) {
+                int64_t a = x + NB[d][0], b = y + NB[d][1], c = z + NB[d][2];
+                if (a < 0 || b < 0 || c < 0 || a >= nx || b >= ny || c >= nz) continue;
+                int64_t u = lin(a, b, c, ny, nz);
+                if (seq[u] >= 1 && seq[u] <= k) uf_union(p, sz, v, u);
+            }
+        }
+        for (int64_t i = cnt[k]; i < cnt[k + 1]; i++)
+            if (uf_find(p, order[i]) != uf_find(p, N)) bad++;
+    }
+    free(cnt); free(order); free(pos); free(p); free(sz);
+    return bad;
+}
+
+/* ------------------------------------------------------------------------
+ * Morphological image opening drainage, MIO (Section 1 and Section 2.4.1):
+ * for decreasing sphere sizes, erode the pore space, trim what is not
+ * connected to the inlet (after the erosion, before the dilation), dilate.
+ * Level i uses the squared radius T[i] (strictly decreasing):
+ *   E_i = {pore v : dt2[v] >= T_i}                       (erosion)
+ *   trimmed E_i = members of E_i 6-connected within E_i to E_i's inlet face
+ *   D_i = {p : exists c in trimmed E_i with |p - c|^2 < T_i}   (dilation)
+ * level[p] = i+1 for the first level i with p in D_i; -1 pore never reached;
+ * 0 solid.  counts[i] = number of voxels with 1 <= level <= i+1.
+ * ---------------------------------------------------------------------- */
+
+static void mio_trim(const uint8_t *img, const int32_t *dt2, int nx, int ny, int nz, int inlet,
+                     int64_t T, uint8_t *trim, int64_t *q)
+{
+    int64_t N = (int64_t)nx * ny * nz, qh = 0, qt = 0;
+    memset(trim, 0, N);
+    for (int64_t v = 0; v < N; v++) {
+        if (!img[v] || dt2[v] < T) continue;
+        int64_t x, y, z;
+        coords(v, ny, nz, &x, &y, &z);
+        if (on_face(x, y, z, nx, ny, nz, inlet)) { trim[v] = 1; q[qt++] = v; }
+    }
+    while (qh < qt) {
+        int64_t v = q[qh++], x, y, z;
+        coords(v, ny, nz, &x, &y, &z);
+        for (int d = 0; d < 6; d++) {
+            int64_t a = x + NB[d][0], b = y + NB[d][1], c = z + NB[d][2];
+            if (a < 0 || b < 0 || c < 0 || a >= nx || b >= ny || c >= nz) continue;
+            int64_t u = lin(a, b, c, ny, nz);
+            if (trim[u] || !img[u] || dt2[u] < T) continue;
+            trim[u] = 1;
+            q[qt++] = u;
+        }
+    }
+}
+
+static void mio_counts(const int32_t *level, int64_t N, int32_t L, int64_t *counts)
+{
+    if (!counts) return;
+    for (int32_t i = 0; i < L; i++) counts[i] = 0;
+    for (int64_t v = 0; v < N; v++) if (level[v] >= 1 && level[v] <= L) counts[level[v] - 1]++;
+    for (int32_t i = 1; i < L; i++) counts[i] += counts[i - 1];
+}
+
+/* MIO-plain: dilation by stamping the ball around every trimmed voxel. */
+void or_mio_plain(const uint8_t *img, const int32_t *dt2, int nx, int ny, int nz, int inlet,
+                  const int32_t *T, int32_t L, int32_t *level, int64_t *counts)
+{
+    int64_t N = (int64_t)nx * ny * nz;
+    uint8_t *trim = malloc(N ? N : 1), *dil = malloc(N ? N : 1);
+    int64_t *q = malloc(sizeof(int64_t) * (N ? N : 1));
+    for (int64_t v = 0; v < N; v++) level[v] = img[v] ? -1 : 0;
+    for (int32_t i = 0; i < L; i++) {
+        int64_t t = T[i];
+        mio_trim(img, dt2, nx, ny, nz, inlet, t, trim, q);
+        memset(dil, 0, N);
+        int64_t r = ball_halfwidth(t);
+        for (int64_t c = 0; c < N; c++) {
+            if (!trim[c]) continue;
+            int64_t cx, cy, cz;
+            coords(c, ny, nz, &cx, &cy, &cz);
+            for (int64_t x = cx - r; x <= cx + r; x++)
+                for (int64_t y = cy - r; y <= cy + r; y++)
+                    for (int64_t z = cz - r; z <= cz + r; z++) {
+                        if (x < 0 || y < 0 || z < 0 || x >= nx || y >= ny || z >= nz) continue;
+                        if ((x - cx) * (x - cx) + (y - cy) * (y - cy) + (z - cz) * (z - cz) < t)
+                            dil[lin(x, y, z, ny, nz)] = 1;
+                    }
+        }
+        for (int64_t v = 0; v < N; v++) if (dil[v] && level[v] == -1) level[v] = i + 1;
+    }
+    mio_counts(level, N, L, counts);
+    free(trim); free(dil); free(q);
+}
+
+/* MIO-edt: identical result; the dilation of the trimmed set by the ball
+ * d^2 < T is the set where the squared distance to the trimmed set is < T,
+ * computed with EDT-sep taken to the trimmed voxels. */
+void or_mio_edt(const uint8_t *img, const int32_t *dt2, int nx, int ny, int nz, int inlet,
+                const int32_t *T, int32_t L, int32_t *level, int64_t *counts)
+{
+    int64_t N = (int64_t)nx * ny * nz;
+    uint8_t *trim = malloc(N ? N : 1);
+    int64_t *q = malloc(sizeof(int64_t) * (N ? N : 1));
+    int32_t *d = malloc(sizeof(int32_t) * (N ? N : 1));
+    for (int64_t v = 0; v < N; v++) level[v] = img[v] ? -1 : 0;
+    for (int32_t i = 0; i < L; i++) {
+        mio_trim(img, dt2, nx, ny, nz, inlet, T[i], trim, q);
+        edt_sep_core(trim, nx, ny, nz, d);
+        for (int64_t v = 0; v < N; v++) if (d[v] < T[i] && level[v] == -1) level[v] = i + 1;
+    }
+    mio_counts(level, N, L, counts);
+    free(trim); free(q); free(d);
+}
+
+/* ------------------------------------------------------------------------
+ * Saturation and capillary pressure per step (Sections 2.2.1 and 2.2.2,
+ * Washburn relation as written in Section 2.4.1: Pc = -2 sigma cos(theta)/R).
+ *   cnt[k] = voxels with seq == k;  S_k = (sum_{j<=k} cnt[j]) / Npore,
+ *   Npore = every pore voxel of the image (seq != 0);
+ *   R_k = sqrt(step_r2[k]) * voxel_m  (the radius of the sphere d^2 < r2);
+ *   Pc_k = (-2 sigma cos(theta)) / R_k,  cos(theta) = cos(theta_deg*pi/180).
+ * All in double, one rounding to float.  sat_image[v] = S_{seq[v]} for
+ * 1 <= seq[v] <= K, +infinity otherwise (never below any threshold).
+ * ---------------------------------------------------------------------- */
+void or_pc_curve(const int32_t *seq, int64_t N, const int32_t *step_r2, int64_t K, double voxel_m,
+                 double sigma, double theta_deg, float *S, float *Pc, float *sat_image)
+{
+    const double pi = 3.14159265358979323846;
+    int64_t *cnt = calloc((size_t)K + 1, sizeof(int64_t));
+    int64_t npore = 0;
+    for (int64_t v = 0; v < N; v++) {
+        if (seq[v] != 0) npore++;
+        if (seq[v] >= 1 && seq[v] <= K) cnt[seq[v]]++;
+    }
+    double ct = cos(theta_deg * pi / 180.0);
+    int64_t cum = 0;
+    for (int64_t k = 1; k <= K; k++) {
+        cum += cnt[k];
+        S[k - 1] = (float)((double)cum / (double)npore);
+        Pc[k - 1] = (float)((-2.0 * sigma * ct) / (sqrt((double)step_r2[k - 1]) * voxel_m));
+    }
+    if (sat_image)
+        for (int64_t v = 0; v < N; v++)
+            sat_image[v] = (seq[v] >= 1 && seq[v] <= K) ? S[seq[v] - 1] : INFINITY;
+    free(cnt);
+}
+
+int or_abi_version(void) { return 1; }
