@@ -1,0 +1,200 @@
+/*
+ * ibip.h -- C ABI of libibip: image-based invasion percolation (IBIP) on one
+ * NVIDIA GB300 GPU.
+ *
+ * The method: Gostick, Yang & Boek, "Simulating volume-controlled invasion of
+ * a non-wetting fluid in volumetric images using basic image processing
+ * tools", arXiv 2101.03240.  Section numbers below refer to that paper.
+ *
+ * Conventions shared by every call
+ *   - A voxel image has shape (nx, ny, nz) in C order: the linear index of
+ *     voxel (x, y, z) is idx = (x*ny + y)*nz + z, so z is contiguous.
+ *   - uint8 images: nonzero = pore (void), 0 = solid.  Connectivity is 6
+ *     (face neighbours) everywhere.  Voxels outside the image are not solid.
+ *   - dt2 (int32): squared Euclidean distance from a pore voxel to the
+ *     nearest solid voxel; 0 on solid; INT32_MAX on pore when the image holds
+ *     no solid voxel at all.
+ *   - seq (int32): 0 solid, -1 pore never invaded (or reset by trapping),
+ *     k >= 1 invaded at step k.
+ *   - Every dimension must be in [1, 16384] and nx*ny*nz < 2^31.
+ *
+ * Memory, streams and errors
+ *   - Array arguments are DEVICE pointers on the context's device unless the
+ *     name starts with h_ (host memory).  The caller owns every argument
+ *     buffer; the context owns its scratch memory and reuses it across calls.
+ *   - Work is queued on the context's stream.  Calls that return a value
+ *     through an h_ pointer synchronise that stream before returning; the
+ *     others return as soon as the work is queued.
+ *   - Arguments are validated on the host before any launch; a bad argument
+ *     returns IBIP_ERR_ARG and queues nothing.  Limits reached on the device
+ *     (step limit, round limit) are reported by the synchronising calls.
+ *     Results are unspecified after any status other than IBIP_OK, except
+ *     where a call documents otherwise.
+ *   - No C++ exception crosses this interface.  A context is not thread-safe;
+ *     use one context per host thread.
+ */
+#ifndef IBIP_H
+#define IBIP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define IBIP_API __attribute__((visibility("default")))
+#else
+#define IBIP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    IBIP_OK = 0,
+    IBIP_ERR_ARG = -1,           /* invalid argument (nothing queued) */
+    IBIP_ERR_CUDA = -2,          /* a CUDA runtime call failed */
+    IBIP_ERR_OOM = -3,           /* scratch allocation failed */
+    IBIP_ERR_STEP_LIMIT = -4,    /* invasion stopped at max_steps with candidates left */
+    IBIP_ERR_NOT_CONVERGED = -5, /* propagation hit its round limit */
+    IBIP_ERR_CANCELLED = -6,     /* reserved */
+    IBIP_ERR_BOUNDS = -7         /* a device-side index check failed */
+} ibip_status;
+
+/* Image faces: X0 is the face x = 0, X1 is x = nx-1, and so on. */
+typedef enum { IBIP_X0 = 0, IBIP_X1, IBIP_Y0, IBIP_Y1, IBIP_Z0, IBIP_Z1 } ibip_face;
+
+typedef struct { int32_t nx, ny, nz; } ibip_dims;
+
+typedef struct ibip_ctx ibip_ctx;
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * to queue work on, or NULL to use the device's legacy default stream.
+ * Writes the new context to *out.  Returns IBIP_OK, IBIP_ERR_ARG or
+ * IBIP_ERR_CUDA. */
+IBIP_API int ibip_create(ibip_ctx **out, int device, void *cuda_stream);
+
+/* Release the context and its scratch memory (synchronises its stream). */
+IBIP_API int ibip_destroy(ibip_ctx *ctx);
+
+/* Change the stream later calls queue on (NULL = legacy default stream). */
+IBIP_API int ibip_set_stream(ibip_ctx *ctx, void *cuda_stream);
+
+/* Squared Euclidean distance transform of the pore space (Section 2.1, the
+ * "distance transform (dt) of the pore space image", Figure 2b).
+ *   image: uint8[nx*ny*nz], nonzero = pore.
+ *   dt2:   int32[nx*ny*nz] output as defined above (exact integers).
+ * Asynchronous. */
+IBIP_API int ibip_edt(ibip_ctx *ctx, const uint8_t *image, ibip_dims dims, int32_t *dt2);
+
+/* Volume-controlled invasion (Section 2.1, Figures 1-2; footnote 1).
+ * Step k = 1, 2, ... picks the candidate voxel c with the largest dt2 --
+ * candidates are uninvaded pore voxels that are 6-adjacent to an invaded
+ * voxel or lie on the `inlet` face -- with ties going to the lowest linear
+ * index, then writes k into every uninvaded voxel p with |p - c|^2 < dt2[c]
+ * (never overwriting an earlier step).  Stops when no candidate is left or
+ * after max_steps steps.
+ *   image:       uint8[N] pore image.
+ *   dt2:         int32[N] squared EDT of `image`, or NULL to compute it here
+ *                (into context scratch).  Must be consistent with `image`.
+ *   inlet:       ibip_face the non-wetting phase enters through.
+ *   max_steps:   >= 0; the step limit.
+ *   seq:         int32[N] output sequence image.
+ *   step_r2:     int32[capacity_steps] output: dt2 of each step's centre.
+ *   step_centre: int32[capacity_steps] output: linear index of each centre,
+ *                or NULL.
+ *   capacity_steps: length of the step arrays.
+ *   h_n_steps:   host int64 output: number of steps K taken.
+ * Synchronous.  Returns IBIP_ERR_STEP_LIMIT when max_steps stopped the run
+ * with candidates left (seq and the step arrays hold the first max_steps
+ * steps), and IBIP_ERR_ARG with *h_n_steps = K when K > capacity_steps (seq
+ * is complete; only the first capacity_steps step entries are written).
+ * capacity_steps = number of pore voxels is always enough. */
+IBIP_API int ibip_invade(ibip_ctx *ctx, const uint8_t *image, const int32_t *dt2, ibip_dims dims,
+                int inlet, int64_t max_steps, int32_t *seq, int32_t *step_r2,
+                int32_t *step_centre, int64_t capacity_steps, int64_t *h_n_steps);
+
+/* Defending-phase trapping (Section 2.2.3).  A voxel invaded at step k is
+ * trapped when no 6-path through pore voxels whose sequence value is >= k
+ * (never-invaded pore counting as +infinity) joins it to a pore voxel on the
+ * `outlet` face.  Never-invaded voxels are not reported as trapped;
+ * outlet-face voxels never are.
+ *   seq:      int32[N] sequence image (from ibip_invade).
+ *   outlet:   ibip_face.
+ *   rerank:   nonzero to re-rank seq_out's surviving step values to
+ *             1..K' in order (Section 2.2.3, contiguous sequence).
+ *   trapped:  uint8[N] output, 1 = trapped.
+ *   seq_out:  int32[N] output (seq with trapped voxels set to -1), or NULL.
+ * Synchronous (the propagation loop checks convergence on the host);
+ * returns IBIP_ERR_NOT_CONVERGED if the round limit was reached. */
+IBIP_API int ibip_trapping(ibip_ctx *ctx, const int32_t *seq, ibip_dims dims, int outlet, int rerank,
+                  uint8_t *trapped, int32_t *seq_out);
+
+/* Pressure-based drainage by morphological image opening, MIO (Section 1,
+ * Section 2.4.1): for each squared radius T_i (strictly decreasing), keep
+ * the pore voxels with dt2 >= T_i (erosion), trim those not 6-connected
+ * inside that set to the inlet face (after the erosion, before the
+ * dilation), then dilate by the ball d^2 < T_i.
+ *   image, dt2:  as for ibip_invade (dt2 required).
+ *   h_r2_levels: host int32[n_levels], strictly decreasing, >= 1;
+ *                0 <= n_levels <= 8192.
+ *   level:       int32[N] output: i+1 for the first level i that invades the
+ *                voxel, -1 pore never invaded, 0 solid.
+ *   h_counts:    host int64[n_levels] output: voxels with 1 <= level <= i+1.
+ * Synchronous. */
+IBIP_API int ibip_morph_drainage(ibip_ctx *ctx, const uint8_t *image, const int32_t *dt2, ibip_dims dims,
+                        int inlet, const int32_t *h_r2_levels, int32_t n_levels, int32_t *level,
+                        int64_t *h_counts);
+
+/* Saturation and capillary pressure after each step (Sections 2.2.1 and
+ * 2.2.2; Washburn relation Pc = -2 sigma cos(theta) / R, Section 2.4.1).
+ *   S_k  = (voxels with 1 <= seq <= k) / (all pore voxels, seq != 0);
+ *   Pc_k = (-2 sigma cos(theta)) / (sqrt(step_r2[k]) * voxel_m), with
+ *          cos(theta) = cos(theta_deg * pi / 180); double precision, one
+ *          rounding to float.
+ *   seq:          int32[N] (seq or a trapping-corrected seq_out).
+ *   step_r2:      int32[n_steps].
+ *   sat_per_step, pc_per_step: float[n_steps] outputs.
+ *   sat_image:    float[N] output or NULL: S_{seq[v]} where 1 <= seq[v] <=
+ *                 n_steps, +infinity elsewhere (Section 2.2.1: thresholding
+ *                 it at s gives the configuration at saturation s).
+ * Asynchronous. */
+IBIP_API int ibip_pc_curve(ibip_ctx *ctx, const int32_t *seq, ibip_dims dims, const int32_t *step_r2,
+                  int64_t n_steps, double voxel_m, double sigma, double theta_deg,
+                  float *sat_per_step, float *pc_per_step, float *sat_image);
+
+/* Wait for everything queued on the context's stream; returns the first
+ * error seen. */
+IBIP_API int ibip_synchronize(ibip_ctx *ctx);
+
+/* Number of libibip kernel launches queued on this context so far. */
+IBIP_API int64_t ibip_launch_count(const ibip_ctx *ctx);
+
+/* Kernel classes timed by the profiler. */
+typedef enum {
+    IBIP_K_EDT = 0,       /* the three EDT passes of ibip_edt / ibip_invade */
+    IBIP_K_RANK = 1,      /* rank sort and bit-plane setup of ibip_invade */
+    IBIP_K_INVADE = 2,    /* the persistent invasion kernel */
+    IBIP_K_MAXIMIN = 3,   /* widest-path propagation rounds (trapping, opening) */
+    IBIP_K_TRAP = 4,      /* trapped mask, seq_out and re-ranking */
+    IBIP_K_PC = 5,        /* histogram, scan, saturation and Pc */
+    IBIP_K_DILATE = 6,    /* per-level dilation passes of the opening */
+    IBIP_K_NCLASSES = 7
+} ibip_kernel_class;
+
+/* Turn per-kernel timing on (nonzero) or off.  Turning it on clears the
+ * log.  While on, each kernel class is bracketed by a pair of CUDA events on
+ * the context's stream (events recorded: at most 65536 pairs). */
+IBIP_API int ibip_profile_enable(ibip_ctx *ctx, int on);
+
+/* Synchronise the stream and report, for kernel class `cls`, the summed
+ * device time in milliseconds (*h_ms) and the number of bracketed spans
+ * (*h_spans) since profiling was enabled. */
+IBIP_API int ibip_profile_read(ibip_ctx *ctx, int cls, double *h_ms, int64_t *h_spans);
+
+/* Static text for a status code. */
+IBIP_API const char *ibip_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IBIP_H */

@@ -1,0 +1,318 @@
+// api.cu -- the C ABI declared in include/ibip.h: argument checks, context
+// and scratch management, and the order of kernel launches for each call.
+#include <math.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+
+int ibip_invade_run(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, int64_t max_steps,
+                    int32_t *seq, int32_t *step_r2, int32_t *step_centre, int64_t cap, int64_t *h_out);
+int ibip_pc_launch(ibip_ctx *ctx, const int32_t *seq, ibip_dims d, const int32_t *r2, int64_t K, double voxel,
+                   double sigma, double cos_theta, float *S, float *Pc, float *sat);
+int ibip_trap_finish(ibip_ctx *ctx, const int32_t *seq, const int32_t *M, ibip_dims d, int rerank, uint8_t *trapped,
+                     int32_t *seq_out);
+int ibip_level_init(ibip_ctx *ctx, const uint8_t *img, ibip_dims d, int32_t *level);
+int ibip_level_counts(ibip_ctx *ctx, const int32_t *level, ibip_dims d, int L, int64_t *h_counts);
+
+namespace {
+
+constexpr int kMaxDim = 16384;
+constexpr int kMaxRounds = 1 << 20;
+
+bool dims_ok(ibip_dims d)
+{
+    if (d.nx < 1 || d.ny < 1 || d.nz < 1) return false;
+    if (d.nx > kMaxDim || d.ny > kMaxDim || d.nz > kMaxDim) return false;
+    return nvox(d) < (1ll << 31);
+}
+
+bool face_ok(int f) { return f >= 0 && f <= 5; }
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+struct ProfLog {
+    struct Rec { int cls; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
+    cudaEvent_t open[IBIP_K_NCLASSES] = {};
+    cudaEvent_t get()
+    {
+        cudaEvent_t e = nullptr;
+        if (!pool.empty()) { e = pool.back(); pool.pop_back(); return e; }
+        if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+        return e;
+    }
+    void clear()
+    {
+        for (auto &r : recs) { pool.push_back(r.a); pool.push_back(r.b); }
+        recs.clear();
+        for (auto &e : open) if (e) { pool.push_back(e); e = nullptr; }
+    }
+    ~ProfLog()
+    {
+        clear();
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+
+}  // namespace
+
+void ibip_prof_begin(ibip_ctx *ctx, int cls)
+{
+    ProfLog *p = (ProfLog *)ctx->prof;
+    if (!p || cls < 0 || cls >= IBIP_K_NCLASSES || p->open[cls] || p->recs.size() >= 65536) return;
+    cudaEvent_t e = p->get();
+    if (!e) return;
+    cudaEventRecord(e, ctx->stream);
+    p->open[cls] = e;
+}
+
+void ibip_prof_end(ibip_ctx *ctx, int cls)
+{
+    ProfLog *p = (ProfLog *)ctx->prof;
+    if (!p || cls < 0 || cls >= IBIP_K_NCLASSES || !p->open[cls]) return;
+    cudaEvent_t e = p->get();
+    if (!e) return;
+    cudaEventRecord(e, ctx->stream);
+    p->recs.push_back({cls, p->open[cls], e});
+    p->open[cls] = nullptr;
+}
+
+int ibip_cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return IBIP_OK;
+    if (e == cudaErrorMemoryAllocation) return IBIP_ERR_OOM;
+    return IBIP_ERR_CUDA;
+}
+
+void *ibip_scratch(ibip_ctx *ctx, int slot, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    if (ctx->slot_bytes[slot] >= bytes) return ctx->slot[slot];
+    if (ctx->slot[slot]) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(ctx->slot[slot]);
+        ctx->slot[slot] = nullptr;
+        ctx->slot_bytes[slot] = 0;
+    }
+    size_t want = bytes + bytes / 8;   // headroom so small growth does not reallocate
+    void *p = nullptr;
+    if (cudaMalloc(&p, want) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    ctx->slot[slot] = p;
+    ctx->slot_bytes[slot] = want;
+    return p;
+}
+
+extern "C" {
+
+int ibip_create(ibip_ctx **out, int device, void *cuda_stream)
+{
+    if (!out) return IBIP_ERR_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        return device < 0 || (n > 0 && device >= n) ? IBIP_ERR_ARG : IBIP_ERR_CUDA;
+    }
+    DeviceGuard g(device);
+    ibip_ctx *c = new (std::nothrow) ibip_ctx;
+    if (!c) return IBIP_ERR_OOM;
+    memset(c, 0, sizeof(*c));
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cudaMallocHost(&c->h_pinned, 65536) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return IBIP_ERR_CUDA;
+    }
+    *out = c;
+    return IBIP_OK;
+}
+
+int ibip_destroy(ibip_ctx *ctx)
+{
+    if (!ctx) return IBIP_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    delete (ProfLog *)ctx->prof;
+    for (int i = 0; i < SC_NSLOTS; i++)
+        if (ctx->slot[i]) cudaFree(ctx->slot[i]);
+    if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+    delete ctx;
+    return IBIP_OK;
+}
+
+int ibip_set_stream(ibip_ctx *ctx, void *cuda_stream)
+{
+    if (!ctx) return IBIP_ERR_ARG;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    return IBIP_OK;
+}
+
+int ibip_synchronize(ibip_ctx *ctx)
+{
+    if (!ctx) return IBIP_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    return ibip_cuda_status(cudaStreamSynchronize(ctx->stream));
+}
+
+int64_t ibip_launch_count(const ibip_ctx *ctx) { return ctx ? ctx->launches : -1; }
+
+int ibip_profile_enable(ibip_ctx *ctx, int on)
+{
+    if (!ctx) return IBIP_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    if (on) {
+        if (!ctx->prof) ctx->prof = new (std::nothrow) ProfLog;
+        if (!ctx->prof) return IBIP_ERR_OOM;
+        cudaStreamSynchronize(ctx->stream);
+        ((ProfLog *)ctx->prof)->clear();
+    } else if (ctx->prof) {
+        cudaStreamSynchronize(ctx->stream);
+        delete (ProfLog *)ctx->prof;
+        ctx->prof = nullptr;
+    }
+    return IBIP_OK;
+}
+
+int ibip_profile_read(ibip_ctx *ctx, int cls, double *h_ms, int64_t *h_spans)
+{
+    if (!ctx || !h_ms || !h_spans || cls < 0 || cls >= IBIP_K_NCLASSES) return IBIP_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    *h_ms = 0.0;
+    *h_spans = 0;
+    ProfLog *p = (ProfLog *)ctx->prof;
+    if (!p) return IBIP_OK;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return ibip_cuda_status(e);
+    for (auto &r : p->recs) {
+        if (r.cls != cls) continue;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) { *h_ms += ms; (*h_spans)++; }
+        else cudaGetLastError();
+    }
+    return IBIP_OK;
+}
+
+int ibip_edt(ibip_ctx *ctx, const uint8_t *image, ibip_dims dims, int32_t *dt2)
+{
+    if (!ctx || !image || !dt2 || !dims_ok(dims)) return IBIP_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    return ibip_edt_launch(ctx, image, dims, dt2);
+}
+
+int ibip_invade(ibip_ctx *ctx, const uint8_t *image, const int32_t *dt2, ibip_dims dims, int inlet,
+                int64_t max_steps, int32_t *seq, int32_t *step_r2, int32_t *step_centre, int64_t capacity_steps,
+                int64_t *h_n_steps)
+{
+    if (!ctx || !image || !seq || !h_n_steps || !dims_ok(dims) || !face_ok(inlet) || max_steps < 0 ||
+        capacity_steps < 0 || (capacity_steps > 0 && !step_r2))
+        return IBIP_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    *h_n_steps = 0;
+    const int32_t *d = dt2;
+    if (!d) {
+        int32_t *t = (int32_t *)ibip_scratch(ctx, SC_DT2, (size_t)nvox(dims) * sizeof(int32_t));
+        if (!t) return IBIP_ERR_OOM;
+        int st = ibip_edt_launch(ctx, image, dims, t);
+        if (st) return st;
+        d = t;
+    }
+    int64_t out[3] = {0, 0, 0};
+    int st = ibip_invade_run(ctx, d, dims, inlet, max_steps, seq, step_r2, step_centre, capacity_steps, out);
+    if (st) return st;
+    *h_n_steps = out[0];
+    if (out[1] != IBIP_OK) return (int)out[1];
+    if (out[0] > capacity_steps) return IBIP_ERR_ARG;
+    return IBIP_OK;
+}
+
+int ibip_trapping(ibip_ctx *ctx, const int32_t *seq, ibip_dims dims, int outlet, int rerank, uint8_t *trapped,
+                  int32_t *seq_out)
+{
+    if (!ctx || !seq || !trapped || !dims_ok(dims) || !face_ok(outlet)) return IBIP_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    int32_t *M = (int32_t *)ibip_scratch(ctx, SC_MM, (size_t)nvox(dims) * sizeof(int32_t));
+    if (!M) return IBIP_ERR_OOM;
+    int st = ibip_maximin_launch(ctx, seq, dims, outlet, M, kMaxRounds);
+    if (st) return st;
+    st = ibip_trap_finish(ctx, seq, M, dims, rerank, trapped, seq_out);
+    if (st) return st;
+    return ibip_cuda_status(cudaStreamSynchronize(ctx->stream));
+}
+
+int ibip_morph_drainage(ibip_ctx *ctx, const uint8_t *image, const int32_t *dt2, ibip_dims dims, int inlet,
+                        const int32_t *h_r2_levels, int32_t n_levels, int32_t *level, int64_t *h_counts)
+{
+    if (!ctx || !image || !dt2 || !level || !h_counts || !dims_ok(dims) || !face_ok(inlet) || n_levels < 0 ||
+        n_levels > 8192 ||
+        (n_levels > 0 && !h_r2_levels))
+        return IBIP_ERR_ARG;
+    for (int i = 0; i < n_levels; i++) {
+        if (h_r2_levels[i] < 1) return IBIP_ERR_ARG;
+        if (i > 0 && h_r2_levels[i] >= h_r2_levels[i - 1]) return IBIP_ERR_ARG;
+    }
+    DeviceGuard g(ctx->device);
+    int32_t *W = (int32_t *)ibip_scratch(ctx, SC_MM, (size_t)nvox(dims) * sizeof(int32_t));
+    if (!W) return IBIP_ERR_OOM;
+    int st = ibip_level_init(ctx, image, dims, level);
+    if (st) return st;
+    if (n_levels == 0) return ibip_cuda_status(cudaStreamSynchronize(ctx->stream));
+    st = ibip_maximin_launch(ctx, dt2, dims, inlet, W, kMaxRounds);
+    if (st) return st;
+    for (int i = 0; i < n_levels; i++) {
+        st = ibip_dilate_level_launch(ctx, W, h_r2_levels[i], i + 1, dims, level);
+        if (st) return st;
+    }
+    return ibip_level_counts(ctx, level, dims, n_levels, h_counts);
+}
+
+int ibip_pc_curve(ibip_ctx *ctx, const int32_t *seq, ibip_dims dims, const int32_t *step_r2, int64_t n_steps,
+                  double voxel_m, double sigma, double theta_deg, float *sat_per_step, float *pc_per_step,
+                  float *sat_image)
+{
+    if (!ctx || !seq || !dims_ok(dims) || n_steps < 0 || n_steps >= (1ll << 31) ||
+        (n_steps > 0 && (!step_r2 || !sat_per_step || !pc_per_step)) || (sat_image && !sat_per_step) ||
+        !(voxel_m > 0.0))
+        return IBIP_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    const double pi = 3.14159265358979323846;
+    const double ct = cos(theta_deg * pi / 180.0);
+    return ibip_pc_launch(ctx, seq, dims, step_r2, n_steps, voxel_m, sigma, ct, sat_per_step, pc_per_step,
+                          sat_image);
+}
+
+const char *ibip_status_string(int s)
+{
+    switch (s) {
+    case IBIP_OK: return "ok";
+    case IBIP_ERR_ARG: return "invalid argument";
+    case IBIP_ERR_CUDA: return "CUDA runtime error";
+    case IBIP_ERR_OOM: return "out of device memory";
+    case IBIP_ERR_STEP_LIMIT: return "step limit reached with candidates left";
+    case IBIP_ERR_NOT_CONVERGED: return "propagation did not converge within its round limit";
+    case IBIP_ERR_CANCELLED: return "cancelled";
+    case IBIP_ERR_BOUNDS: return "device index check failed";
+    default: return "unknown status";
+    }
+}
+
+}  // extern "C"

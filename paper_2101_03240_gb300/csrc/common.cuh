@@ -1,0 +1,99 @@
+// common.cuh -- internal helpers shared by the libibip CUDA sources.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ibip.h"
+
+#define IBIP_INF32 0x7fffffff
+
+// Scratch slots owned by a context (grown on demand, reused across calls).
+enum ScratchSlot {
+    SC_DT2 = 0,   // int32[N]      EDT when the caller passes none
+    SC_D1,        // uint16[N]     EDT pass-1 output
+    SC_G2,        // int32[N]      EDT pass-2 output
+    SC_RANK,      // int32[N]      rank of each pore voxel
+    SC_OKEY,      // int2[Npore]   (idx, dt2) by rank
+    SC_AVAIL,     // u32 bit-plane (pore and not yet invaded)
+    SC_ADDED,     // u32 bit-plane (ever queued as a candidate)
+    SC_FB,        // u64 frontier bitmap levels 0..3
+    SC_PRES,      // int32 presence / bucket id by dt2 value
+    SC_MAT,       // int32 per-(bucket, chunk) counts
+    SC_SCAN,      // scan partial sums
+    SC_MM,        // int32[N]      maximin field
+    SC_TILE,      // u8 tile activity flags
+    SC_HIST,      // int32 histogram
+    SC_SMALL,     // small device scalars
+    SC_NSLOTS
+};
+
+struct ibip_ctx {
+    int device;
+    cudaStream_t stream;
+    int sm_count;
+    int64_t launches;
+    void *slot[SC_NSLOTS];
+    size_t slot_bytes[SC_NSLOTS];
+    void *h_pinned;   // small pinned host buffer for scalar readback
+    void *prof;       // event log when profiling is on (api.cu), else null
+};
+
+// Profiling: CUDA-event pairs around each kernel class, on the context's
+// stream, only while ibip_profile_enable(ctx, 1) is in effect.
+void ibip_prof_begin(ibip_ctx *ctx, int cls);
+void ibip_prof_end(ibip_ctx *ctx, int cls);
+
+// Grow-only scratch.  Returns nullptr on failure.
+void *ibip_scratch(ibip_ctx *ctx, int slot, size_t bytes);
+
+#define IBIP_LAUNCH(ctx) ((ctx)->launches++)
+
+// Status helpers.
+int ibip_cuda_status(cudaError_t e);
+
+static inline int64_t nvox(ibip_dims d) { return (int64_t)d.nx * d.ny * d.nz; }
+
+// ---- internal launchers (one file each) ---------------------------------
+// EDT: feature = (image == 0).  Output dt2.
+int ibip_edt_launch(ibip_ctx *ctx, const uint8_t *image, ibip_dims d, int32_t *dt2);
+// MIO helper: for feature = (W >= T), marks level[v] = lvl where level[v] == -1
+// and the squared distance to the feature set is < T.
+int ibip_dilate_level_launch(ibip_ctx *ctx, const int32_t *W, int32_t T, int32_t lvl, ibip_dims d,
+                             int32_t *level);
+// Maximin propagation from a face through voxels with val != 0 (val == -1
+// counts as +inf).  Writes M (-1 where unreachable).
+int ibip_maximin_launch(ibip_ctx *ctx, const int32_t *val, ibip_dims d, int face, int32_t *M,
+                        int max_rounds);
+// Scans.
+int ibip_scan_excl_i32(ibip_ctx *ctx, const int32_t *in, int32_t *out, int64_t n);
+int ibip_scan_incl_i32(ibip_ctx *ctx, const int32_t *in, int32_t *out, int64_t n);
+
+__device__ __forceinline__ int64_t d_lin(int x, int y, int z, int ny, int nz)
+{
+    return ((int64_t)x * ny + y) * nz + z;
+}
+
+__device__ __forceinline__ bool d_on_face(int x, int y, int z, int nx, int ny, int nz, int face)
+{
+    switch (face) {
+    case 0: return x == 0;
+    case 1: return x == nx - 1;
+    case 2: return y == 0;
+    case 3: return y == ny - 1;
+    case 4: return z == 0;
+    default: return z == nz - 1;
+    }
+}
+
+// floor(sqrt(e)) for 0 <= e < 2^31, exact.
+__device__ __forceinline__ int d_isqrt(int e)
+{
+    int h = (int)sqrtf((float)e);
+    while (h > 0 && (int64_t)h * h > e) h--;
+    while ((int64_t)(h + 1) * (h + 1) <= e) h++;
+    return h;
+}
+
+// largest r >= 0 with r*r < r2 (r2 >= 1): the ball's half-width along an axis
+__device__ __forceinline__ int d_ball_hw(int r2) { return d_isqrt(r2 - 1); }

@@ -1,0 +1,234 @@
+"""Thin ctypes binding over libibip (include/ibip.h).
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels.  Tensors are PyTorch CUDA tensors (PyTorch provides device memory and
+streams); work is queued on the current PyTorch stream.  If the library is
+missing this module raises at import of the first call -- there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import torch
+
+from . import build_lib
+
+OK = 0
+ERR_ARG = -1
+ERR_CUDA = -2
+ERR_OOM = -3
+ERR_STEP_LIMIT = -4
+ERR_NOT_CONVERGED = -5
+
+FACES = {"x0": 0, "x1": 1, "y0": 2, "y1": 3, "z0": 4, "z1": 5}
+
+
+class Dims(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32)]
+
+
+class IbipError(RuntimeError):
+    def __init__(self, fn, status):
+        self.status = status
+        msg = _lib().ibip_status_string(status).decode()
+        super().__init__("%s failed: %s (%d)" % (fn, msg, status))
+
+
+_L = None
+_lock = threading.Lock()
+
+
+def lib_path() -> str:
+    return build_lib.LIB
+
+
+def _lib():
+    global _L
+    with _lock:
+        if _L is None:
+            if not os.path.exists(build_lib.LIB):
+                raise RuntimeError("libibip.so is not built (%s); run __graft_entry__.build()" % build_lib.LIB)
+            L = C.CDLL(build_lib.LIB)
+            P, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+            sig = {
+                "ibip_create": (C.c_int, [C.POINTER(P), C.c_int, P]),
+                "ibip_destroy": (C.c_int, [P]),
+                "ibip_set_stream": (C.c_int, [P, P]),
+                "ibip_edt": (C.c_int, [P, P, Dims, P]),
+                "ibip_invade": (C.c_int, [P, P, P, Dims, C.c_int, i64, P, P, P, i64, C.POINTER(i64)]),
+                "ibip_trapping": (C.c_int, [P, P, Dims, C.c_int, C.c_int, P, P]),
+                "ibip_morph_drainage": (C.c_int, [P, P, P, Dims, C.c_int, P, i32, P, P]),
+                "ibip_pc_curve": (C.c_int, [P, P, Dims, P, i64, dbl, dbl, dbl, P, P, P]),
+                "ibip_synchronize": (C.c_int, [P]),
+                "ibip_launch_count": (i64, [P]),
+                "ibip_status_string": (C.c_char_p, [C.c_int]),
+                "ibip_profile_enable": (C.c_int, [P, C.c_int]),
+                "ibip_profile_read": (C.c_int, [P, C.c_int, C.POINTER(dbl), C.POINTER(i64)]),
+            }
+            for name, (res, args) in sig.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _L = L
+    return _L
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _dims(shape):
+    nx, ny, nz = (int(s) for s in shape)
+    return Dims(nx, ny, nz)
+
+
+def _need(t, dtype, name):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous() and t.dim() == 3):
+        raise ValueError("%s must be a contiguous 3-D CUDA %s tensor" % (name, dtype))
+
+
+class Context:
+    """One libibip context on a CUDA device; calls queue on the current
+    PyTorch stream of that device."""
+
+    def __init__(self, device=None):
+        dev = torch.device("cuda", torch.cuda.current_device() if device is None else device) \
+            if not isinstance(device, torch.device) else device
+        self.device = dev
+        h = C.c_void_p()
+        st = _lib().ibip_create(C.byref(h), dev.index, None)
+        if st != OK:
+            raise IbipError("ibip_create", st)
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib().ibip_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _stream(self):
+        s = torch.cuda.current_stream(self.device)
+        _lib().ibip_set_stream(self._h, C.c_void_p(s.cuda_stream))
+
+    @property
+    def launches(self) -> int:
+        return int(_lib().ibip_launch_count(self._h))
+
+    def profile(self, on: bool):
+        """Per-kernel-class CUDA-event timing on (clears the log) or off."""
+        st = _lib().ibip_profile_enable(self._h, int(bool(on)))
+        if st != OK:
+            raise IbipError("ibip_profile_enable", st)
+
+    def profile_read(self, cls: int):
+        """(summed milliseconds, number of spans) of a kernel class since
+        profiling was turned on (classes: see ibip_kernel_class)."""
+        ms, n = C.c_double(0), C.c_int64(0)
+        st = _lib().ibip_profile_read(self._h, int(cls), C.byref(ms), C.byref(n))
+        if st != OK:
+            raise IbipError("ibip_profile_read", st)
+        return float(ms.value), int(n.value)
+
+    def synchronize(self):
+        st = _lib().ibip_synchronize(self._h)
+        if st != OK:
+            raise IbipError("ibip_synchronize", st)
+
+    # -- calls ------------------------------------------------------------
+    def edt(self, image, out=None):
+        """Squared EDT of the pore space (int32)."""
+        _need(image, torch.uint8, "image")
+        out = torch.empty(image.shape, dtype=torch.int32, device=image.device) if out is None else out
+        self._stream()
+        st = _lib().ibip_edt(self._h, _ptr(image), _dims(image.shape), _ptr(out))
+        if st != OK:
+            raise IbipError("ibip_edt", st)
+        return out
+
+    def invade(self, image, dt2=None, inlet=0, max_steps=None, capacity=None, centres=True, seq=None,
+               step_r2=None, step_centre=None, check=True):
+        """Invasion sequence.  Returns (seq, step_r2[:K], step_centre[:K] or
+        None, K, status)."""
+        _need(image, torch.uint8, "image")
+        if dt2 is not None:
+            _need(dt2, torch.int32, "dt2")
+        n = image.numel()
+        if capacity is None:
+            capacity = n if step_r2 is None else step_r2.numel()
+        if max_steps is None:
+            max_steps = n
+        dev = image.device
+        seq = torch.empty(image.shape, dtype=torch.int32, device=dev) if seq is None else seq
+        step_r2 = torch.empty(max(capacity, 1), dtype=torch.int32, device=dev) if step_r2 is None else step_r2
+        if centres and step_centre is None:
+            step_centre = torch.empty(max(capacity, 1), dtype=torch.int32, device=dev)
+        K = C.c_int64(0)
+        self._stream()
+        st = _lib().ibip_invade(self._h, _ptr(image), _ptr(dt2), _dims(image.shape), int(inlet), int(max_steps),
+                                _ptr(seq), _ptr(step_r2), _ptr(step_centre) if centres else None, int(capacity),
+                                C.byref(K))
+        if check and st not in (OK, ERR_STEP_LIMIT):
+            raise IbipError("ibip_invade", st)
+        k = int(K.value)
+        kk = min(k, capacity)
+        return seq, step_r2[:kk], (step_centre[:kk] if centres else None), k, st
+
+    def trapping(self, seq, outlet=1, rerank=False, seq_out=True):
+        _need(seq, torch.int32, "seq")
+        tr = torch.empty(seq.shape, dtype=torch.uint8, device=seq.device)
+        so = torch.empty_like(seq) if seq_out else None
+        self._stream()
+        st = _lib().ibip_trapping(self._h, _ptr(seq), _dims(seq.shape), int(outlet), int(bool(rerank)), _ptr(tr),
+                                  _ptr(so))
+        if st != OK:
+            raise IbipError("ibip_trapping", st)
+        return tr, so
+
+    def morph_drainage(self, image, dt2, levels, inlet=0):
+        _need(image, torch.uint8, "image")
+        _need(dt2, torch.int32, "dt2")
+        T = (C.c_int32 * max(len(levels), 1))(*[int(t) for t in levels])
+        cnt = (C.c_int64 * max(len(levels), 1))()
+        lev = torch.empty(image.shape, dtype=torch.int32, device=image.device)
+        self._stream()
+        st = _lib().ibip_morph_drainage(self._h, _ptr(image), _ptr(dt2), _dims(image.shape), int(inlet), T,
+                                        len(levels), _ptr(lev), cnt)
+        if st != OK:
+            raise IbipError("ibip_morph_drainage", st)
+        return lev, [int(c) for c in cnt[:len(levels)]]
+
+    def pc_curve(self, seq, step_r2, voxel_m=5e-6, sigma=0.072, theta_deg=180.0, sat_image=False):
+        _need(seq, torch.int32, "seq")
+        K = int(step_r2.numel())
+        dev = seq.device
+        S = torch.empty(max(K, 1), dtype=torch.float32, device=dev)
+        P = torch.empty(max(K, 1), dtype=torch.float32, device=dev)
+        img = torch.empty(seq.shape, dtype=torch.float32, device=dev) if sat_image else None
+        r2 = step_r2.contiguous()
+        self._stream()
+        st = _lib().ibip_pc_curve(self._h, _ptr(seq), _dims(seq.shape), _ptr(r2), K, float(voxel_m), float(sigma),
+                                  float(theta_deg), _ptr(S), _ptr(P), _ptr(img))
+        if st != OK:
+            raise IbipError("ibip_pc_curve", st)
+        return S[:K], P[:K], img
+
+
+_default = {}
+
+
+def context(device=None) -> Context:
+    """A cached context per device."""
+    idx = torch.cuda.current_device() if device is None else int(device)
+    c = _default.get(idx)
+    if c is None:
+        c = _default[idx] = Context(idx)
+    return c
