@@ -191,6 +191,18 @@ IBIP_API int ibip_profile_enable(ibip_ctx *ctx, int on);
  * (*h_spans) since profiling was enabled. */
 IBIP_API int ibip_profile_read(ibip_ctx *ctx, int cls, double *h_ms, int64_t *h_spans);
 
+/* Counters of the context's last ibip_invade call, for tracing: writes up
+ * to n of [steps, status, iterations, cycles selecting, cycles in the
+ * candidate-bound pass, cycles committing (SM clock, thread 0), batch items
+ * taken, batch items committed, stale summary bits cleared, ball rows
+ * committed, cycles in batches of single-voxel balls, number of such
+ * batches, then select sub-phase cycles (gather, item data,
+ * pairwise tests, bookkeeping) and the three phase cycles of single-voxel
+ * batches, iterations, steps and cycles of the single-voxel loop, then
+ * gather sub-phase cycles for the two loops and the single-voxel loop's
+ * phase cycles]; n <= 35 entries. */
+IBIP_API int ibip_invade_stats(const ibip_ctx *ctx, int64_t *h_stats, int n);
+
 /* Static text for a status code. */
 IBIP_API const char *ibip_status_string(int status);
 

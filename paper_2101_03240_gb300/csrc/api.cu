@@ -176,6 +176,13 @@ int ibip_synchronize(ibip_ctx *ctx)
 
 int64_t ibip_launch_count(const ibip_ctx *ctx) { return ctx ? ctx->launches : -1; }
 
+int ibip_invade_stats(const ibip_ctx *ctx, int64_t *h_stats, int n)
+{
+    if (!ctx || !h_stats || n < 0) return IBIP_ERR_ARG;
+    for (int i = 0; i < n && i < 36; i++) h_stats[i] = ctx->inv_stats[i];
+    return IBIP_OK;
+}
+
 int ibip_profile_enable(ibip_ctx *ctx, int on)
 {
     if (!ctx) return IBIP_ERR_ARG;
@@ -236,9 +243,10 @@ int ibip_invade(ibip_ctx *ctx, const uint8_t *image, const int32_t *dt2, ibip_di
         if (st) return st;
         d = t;
     }
-    int64_t out[3] = {0, 0, 0};
+    int64_t out[36] = {0};
     int st = ibip_invade_run(ctx, d, dims, inlet, max_steps, seq, step_r2, step_centre, capacity_steps, out);
     if (st) return st;
+    memcpy(ctx->inv_stats, out, sizeof(out));
     *h_n_steps = out[0];
     if (out[1] != IBIP_OK) return (int)out[1];
     if (out[0] > capacity_steps) return IBIP_ERR_ARG;

@@ -25,6 +25,7 @@ enum ScratchSlot {
     SC_TILE,      // u8 tile activity flags
     SC_HIST,      // int32 histogram
     SC_SMALL,     // small device scalars
+    SC_LIST,      // int32 overflow work lists of the invasion kernel
     SC_NSLOTS
 };
 
@@ -37,12 +38,17 @@ struct ibip_ctx {
     size_t slot_bytes[SC_NSLOTS];
     void *h_pinned;   // small pinned host buffer for scalar readback
     void *prof;       // event log when profiling is on (api.cu), else null
+    int64_t inv_stats[36];   // counters of the last ibip_invade (ibip_invade_stats)
 };
 
 // Profiling: CUDA-event pairs around each kernel class, on the context's
 // stream, only while ibip_profile_enable(ctx, 1) is in effect.
 void ibip_prof_begin(ibip_ctx *ctx, int cls);
 void ibip_prof_end(ibip_ctx *ctx, int cls);
+
+// Bytes of the SC_SMALL slot: int scalars at int offsets 0..15, the
+// invasion kernel's int64 outputs from byte 64 (at most 64 values).
+constexpr size_t kSmallBytes = 64 + 64 * sizeof(int64_t);
 
 // Grow-only scratch.  Returns nullptr on failure.
 void *ibip_scratch(ibip_ctx *ctx, int slot, size_t bytes);

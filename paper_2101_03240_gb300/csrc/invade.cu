@@ -27,14 +27,19 @@
 //    committed balls are stamped together (each voxel owned by the lowest
 //    committed ball covering it), covered candidates leave the bitmap, and
 //    new candidates (outside every committed ball) enter it.
+#include <algorithm>
+#include <climits>
+
 #include "common.cuh"
 
 namespace {
 
 constexpr int kM = 64;           // batch size (items per iteration)
-constexpr int kNT = 512;         // threads of the persistent CTA
+constexpr int kNT = 384;         // threads of the persistent CTA
 constexpr int kChunk = 4096;     // voxels per rank-sort chunk (minimum)
 constexpr int kSmemL1Max = 12288;
+constexpr int kNOut = 36;          // int64 outputs of the invasion kernel
+static_assert(64 + kNOut * sizeof(long long) <= kSmallBytes, "output slot too small");
 
 typedef unsigned long long u64;
 
@@ -161,6 +166,7 @@ struct Inv {
     int nx, ny, nz, NW, inlet;
     int NL0, NL1, NL2, NL3;
     int64_t max_steps, cap, npore;
+    int isq_n;         // entries of the shared-memory isqrt table
     const int32_t *rank;
     const int2 *okey;
     const int32_t *dt2;
@@ -205,13 +211,57 @@ __global__ void k_plane_init(Inv a)
     }
 }
 
+// n / d for 0 <= n < 2^31 and a run-time invariant d >= 1: one multiply-high
+// and two shifts (Granlund & Montgomery, "Division by invariant integers
+// using multiplication", 1994; the round-up variant for unsigned n).
+struct FastDiv {
+    uint32_t d, m;
+    int s;
+};
+
+FastDiv make_fastdiv(uint32_t d)
+{
+    FastDiv f{d, 0u, 0};
+    if (d <= 1) return f;
+    int s = 0;
+    while ((1ull << s) < d) s++;
+    f.s = s;
+    f.m = (uint32_t)((((1ull << 32) * ((1ull << s) - d)) / d) + 1);
+    return f;
+}
+
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv &f)
+{
+    if (f.d <= 1) return n;
+    uint32_t t = __umulhi(f.m, n);
+    return (t + ((n - t) >> 1)) >> (f.s - 1);
+}
+
+constexpr int kList = 2048;        // shared-memory work-list entries
+constexpr int kRowBudget = 8192;   // ball rows per batch (at least one item)
+
+// floor(sqrt(e)): table lookup below n (shared memory), exact integer
+// square root above
+struct Isq {
+    const int *t;
+    int n;
+    __device__ __forceinline__ int operator()(int e) const { return e < n ? t[e] : d_isqrt(e); }
+};
+
 struct Batch {
-    int idx[kM], r2[kM], x[kM], y[kM], z[kM], rank[kM], step[kM];
-    int bx0[kM], by0[kM], wy[kM];
-    int upre[kM + 1];
+    int idx[kM], r2[kM], x[kM], y[kM], z[kM], rank[kM], step[kM], h[kM];
+    int bx0[kM], by0[kM], wy[kM];      // ball rows: clamped bounding square
+    int dx0[kM], dy0[kM], dwy[kM];     // shell rows: the square grown by one
+    int upre[kM + 1], dpre[kM + 1];    // prefix sums of ball rows / shell rows
     u64 ovl[kM];
     u64 keep;
-    int m, mcap, J, nsteps, stop;
+    Isq isq;
+    u64 big;
+    uint32_t cont32[kM][2], ovl32[kM][2];
+    int m, mcap, J, stop, mtarget, tstop;
+    int cur1;          // no level-1 summary word below this index is set
+    int nA, nC, nD;    // work-list fill counts (shell candidates, removals, additions)
+    int64_t kk;        // step count handed back by the single-voxel loop
 };
 
 // bits [a, b] (inclusive, within word w of a row) as a mask
@@ -229,35 +279,43 @@ __device__ __forceinline__ bool ball_run(const Batch &B, int i, int x, int y, in
     int dx = x - B.x[i], dy = y - B.y[i];
     int64_t e = (int64_t)B.r2[i] - 1 - (int64_t)dx * dx - (int64_t)dy * dy;
     if (e < 0) return false;
-    int h = d_isqrt((int)e);
+    int h = B.isq((int)e);
     lo = B.z[i] - h;
     hi = B.z[i] + h;
     return true;
 }
 
-// Candidate intervals next to ball i's run [lo, hi] at row (x, y): the two
-// z-ends and the parts of the four lateral rows outside ball i.  Calls
-// f(xr, yr, a, b) per non-empty interval (clamped to the image).
-template <class F>
-__device__ __forceinline__ void for_each_shell(const Inv &a, const Batch &B, int i, int x, int y, int lo,
-                                               int hi, F f)
+
+// Half-width of ball i's run at row (x, y), -1 when the row misses the ball
+// or lies outside the image.
+__device__ __forceinline__ int run_hw(const Inv &a, const Batch &B, int i, int x, int y)
 {
-    int z0 = max(lo, 0), z1 = min(hi, a.nz - 1);
-    if (lo - 1 >= 0) f(x, y, lo - 1, lo - 1);
-    if (hi + 1 <= a.nz - 1) f(x, y, hi + 1, hi + 1);
-    const int DX[4] = {-1, 1, 0, 0}, DY[4] = {0, 0, -1, 1};
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-        int xr = x + DX[q], yr = y + DY[q];
-        if (xr < 0 || yr < 0 || xr >= a.nx || yr >= a.ny) continue;
-        int l2, h2;
-        if (!ball_run(B, i, xr, yr, l2, h2)) {
-            f(xr, yr, z0, z1);
-        } else {
-            if (z0 <= l2 - 1) f(xr, yr, z0, min(z1, l2 - 1));
-            if (h2 + 1 <= z1) f(xr, yr, max(z0, h2 + 1), z1);
-        }
-    }
+    if (x < 0 || y < 0 || x >= a.nx || y >= a.ny) return -1;
+    const int dx = x - B.x[i], dy = y - B.y[i];
+    const int64_t e = (int64_t)B.r2[i] - 1 - (int64_t)dx * dx - (int64_t)dy * dy;
+    return e < 0 ? -1 : B.isq((int)e);
+}
+
+// The shell of ball i in row (x, y): voxels outside the ball with a face
+// neighbour inside it.  With h the row's own half-width and hl the largest
+// half-width of the four lateral rows, they are hR < |z - cz| <= Hs,
+// Hs = max(hl, h + 1 if the row meets the ball).  Returns false if empty;
+// else the z-span [za, zb] to scan and the ball's own run [ra, rb] to mask
+// out (ra > rb when the row misses the ball), clamped to the image.
+__device__ __forceinline__ bool shell_row(const Inv &a, const Batch &B, int i, int x, int y, int &za, int &zb,
+                                          int &ra, int &rb)
+{
+    const int h = run_hw(a, B, i, x, y);
+    int hs = max(max(run_hw(a, B, i, x - 1, y), run_hw(a, B, i, x + 1, y)),
+                 max(run_hw(a, B, i, x, y - 1), run_hw(a, B, i, x, y + 1)));
+    if (h >= 0) hs = max(hs, h + 1);
+    if (hs < 0) return false;
+    const int cz = B.z[i];
+    za = max(cz - hs, 0);
+    zb = min(cz + hs, a.nz - 1);
+    ra = h >= 0 ? cz - h : 1;
+    rb = h >= 0 ? cz + h : 0;
+    return za <= zb;
 }
 
 __device__ __forceinline__ int lower_rank(const Batch &B, int m, int r)
@@ -270,36 +328,108 @@ __device__ __forceinline__ int lower_rank(const Batch &B, int m, int r)
     return lo;
 }
 
-__device__ __forceinline__ int unit_item(const Batch &B, int n, int u)
+__device__ __forceinline__ int unit_item(const int *pre, int n, int u)
 {
-    int lo = 0, hi = n;   // largest i with upre[i] <= u
+    int lo = 0, hi = n;   // largest i with pre[i] <= u
     while (hi - lo > 1) {
         int mid = (lo + hi) >> 1;
-        if (B.upre[mid] <= u) lo = mid; else hi = mid;
+        if (pre[mid] <= u) lo = mid; else hi = mid;
     }
     return lo;
 }
 
-template <bool L1SMEM>
-__global__ void __launch_bounds__(kNT, 1) k_invade(Inv a)
+// position of the k-th (0-based) set bit of a 32-bit word: binary search on
+// popcounts of the lower halves
+__device__ __forceinline__ int nth_bit32(uint32_t w, int k)
 {
-    extern __shared__ u64 s_fb[];
-    __shared__ Batch B;
-    u64 *s1 = L1SMEM ? s_fb : a.fb1;
-    u64 *s2 = s_fb + (L1SMEM ? a.NL1 : 0);
-    u64 *s3 = s2 + a.NL2;
-    const int tid = threadIdx.x, lane = tid & 31;
-    if (L1SMEM)
-        for (int i = tid; i < a.NL1; i += kNT) s1[i] = a.fb1[i];
-    for (int i = tid; i < a.NL2; i += kNT) s2[i] = a.fb2[i];
-    for (int i = tid; i < a.NL3; i += kNT) s3[i] = a.fb3[i];
-    __syncthreads();
+    int pos = 0, c;
+    c = __popc(w & 0xffffu); if (k >= c) { k -= c; w >>= 16; pos += 16; }
+    c = __popc(w & 0xffu);   if (k >= c) { k -= c; w >>= 8;  pos += 8; }
+    c = __popc(w & 0xfu);    if (k >= c) { k -= c; w >>= 4;  pos += 4; }
+    c = __popc(w & 0x3u);    if (k >= c) { k -= c; w >>= 2;  pos += 2; }
+    c = (int)(w & 1u);       if (k >= c) { pos += 1; }
+    return pos;
+}
 
-    int64_t k = 0, iters = 0;
+// position of the k-th (0-based) set bit of w
+__device__ __forceinline__ int nth_bit(u64 w, int k)
+{
+    uint32_t lo = (uint32_t)w;
+    int pl = __popc(lo);
+    if (k < pl) return nth_bit32(lo, k);
+    return 32 + nth_bit32((uint32_t)(w >> 32), k - pl);
+}
+
+// The six face neighbours of voxel (x, y, z) with linear index v: for each,
+// whether it is inside the image, its bit-plane word index and bit, and its
+// linear index.
+struct Nb6 {
+    int64_t word[6];
+    int v[6];
+    uint32_t bit[6];
+    bool ok[6];
+};
+
+__device__ __forceinline__ void nb6(const Inv &a, int x, int y, int z, int v, Nb6 &n)
+{
+    const int64_t row = (int64_t)x * a.ny + y;
+    const int64_t nyz = (int64_t)a.ny * a.nz;
+    n.ok[0] = z > 0;          n.v[0] = v - 1;              n.word[0] = row * a.NW + ((z - 1) >> 5);  n.bit[0] = 1u << ((z - 1) & 31);
+    n.ok[1] = z < a.nz - 1;   n.v[1] = v + 1;              n.word[1] = row * a.NW + ((z + 1) >> 5);  n.bit[1] = 1u << ((z + 1) & 31);
+    n.ok[2] = y > 0;          n.v[2] = v - a.nz;           n.word[2] = (row - 1) * a.NW + (z >> 5);   n.bit[2] = 1u << (z & 31);
+    n.ok[3] = y < a.ny - 1;   n.v[3] = v + a.nz;           n.word[3] = (row + 1) * a.NW + (z >> 5);   n.bit[3] = 1u << (z & 31);
+    n.ok[4] = x > 0;          n.v[4] = (int)(v - nyz);     n.word[4] = (row - a.ny) * a.NW + (z >> 5); n.bit[4] = 1u << (z & 31);
+    n.ok[5] = x < a.nx - 1;   n.v[5] = (int)(v + nyz);     n.word[5] = (row + a.ny) * a.NW + (z >> 5); n.bit[5] = 1u << (z & 31);
+}
+
+// Candidate mask (bit q set = neighbour q is uninvaded and never queued),
+// all twelve bit-plane loads issued together.
+__device__ __forceinline__ unsigned nb6_candidates(const Inv &a, const Nb6 &n)
+{
+    uint32_t av[6], ad[6];
+#pragma unroll
+    for (int q = 0; q < 6; q++) {
+        av[q] = n.ok[q] ? ldcg32(a.avail + n.word[q]) : 0u;
+        ad[q] = n.ok[q] ? ldcg32(a.added + n.word[q]) : 0u;
+    }
+    unsigned c = 0;
+#pragma unroll
+    for (int q = 0; q < 6; q++)
+        if ((av[q] & n.bit[q]) && !(ad[q] & n.bit[q])) c |= 1u << q;
+    return c;
+}
+
+// Warp-wide: the first (up to mt) set bits of the rank bitmap, i.e. the best
+// candidates in priority order, written to rank_out[0..m); returns m (0 when
+// no candidate is left).  Lane 0 walks the summary levels to the first
+// flagged level-1 word; the warp loads the level-0 words of up to 32 flagged
+// entries of that and the next three level-1 words, unflags the empty ones
+// (stale summary bits: removals never clear summaries) and takes the
+// leading set bits, each lane extracting up to two of them.
+template <bool L1SMEM>
+__device__ int gather_top(const Inv &a, u64 *s1, u64 *s2, u64 *s3, int *cur1, int lane, int mt, int *rank_out,
+                          long long &n_stale)
+{
     for (;;) {
-        // ---------------------------------------------------- select batch
-        if (tid < 32) {
-            int i0 = -1;
+        // first two non-empty level-1 words: scan 32 words from the cursor
+        // (every level-1 word below it is empty), else walk the summaries
+        const int c = *(volatile int *)cur1;
+        const int q = c + lane;
+        const u64 wl = q < a.NL1 ? (L1SMEM ? s1[q] : ldcg64(s1 + q)) : 0ull;
+        unsigned nz = __ballot_sync(0xffffffffu, wl != 0ull);
+        int i1a = -1, i1b = -1;
+        u64 wa = 0, wb = 0;
+        if (nz) {
+            const int la = __ffs(nz) - 1;
+            i1a = c + la;
+            wa = __shfl_sync(0xffffffffu, wl, la);
+            nz &= nz - 1;
+            if (nz) {
+                const int lb = __ffs(nz) - 1;
+                i1b = c + lb;
+                wb = __shfl_sync(0xffffffffu, wl, lb);
+            }
+        } else {
             if (lane == 0) {
                 for (;;) {
                     int i3 = -1;
@@ -308,97 +438,302 @@ __global__ void __launch_bounds__(kNT, 1) k_invade(Inv a)
                     int i2 = i3 * 64 + __ffsll(s3[i3]) - 1;
                     u64 w2 = s2[i2];
                     if (!w2) { s3[i3] &= ~(1ull << (i2 & 63)); continue; }
-                    int i1 = i2 * 64 + __ffsll(w2) - 1;
-                    u64 w1 = L1SMEM ? s1[i1] : ldcg64(s1 + i1);
+                    int c1 = i2 * 64 + __ffsll(w2) - 1;
+                    u64 w1 = L1SMEM ? s1[c1] : ldcg64(s1 + c1);
                     if (!w1) {
-                        s2[i2] &= ~(1ull << (i1 & 63));
+                        s2[i2] &= ~(1ull << (c1 & 63));
                         if (!s2[i2]) s3[i3] &= ~(1ull << (i2 & 63));
                         continue;
                     }
-                    int c0 = i1 * 64 + __ffsll(w1) - 1;
-                    u64 w0 = ldcg64(a.fb0 + c0);
-                    if (!w0) {
-                        u64 nw1 = w1 & ~(1ull << (c0 & 63));
-                        s1[i1] = nw1;
-                        if (!nw1) {
-                            s2[i2] &= ~(1ull << (i1 & 63));
-                            if (!s2[i2]) s3[i3] &= ~(1ull << (i2 & 63));
-                        }
-                        continue;
-                    }
-                    i0 = c0;
+                    i1a = c1;
+                    wa = w1;
                     break;
                 }
             }
-            i0 = __shfl_sync(0xffffffffu, i0, 0);
-            int m = 0;
-            if (i0 >= 0) {
-                int wi = i0 + lane;
-                u64 w = wi < a.NL0 ? ldcg64(a.fb0 + wi) : 0ull;
-                int c = __popcll(w);
-                int inc = c;
-                for (int o = 1; o < 32; o <<= 1) {
-                    int t = __shfl_up_sync(0xffffffffu, inc, o);
-                    if (lane >= o) inc += t;
+            i1a = __shfl_sync(0xffffffffu, i1a, 0);
+            wa = __shfl_sync(0xffffffffu, wa, 0);
+        }
+        if (i1a < 0) return 0;
+        if (lane == 0) *cur1 = i1a;
+        // lane l takes the l-th flagged level-0 word of the two level-1 words
+        const int pa = __popcll(wa);
+        int c0 = -1;
+        if (lane < pa) c0 = i1a * 64 + nth_bit(wa, lane);
+        else if (i1b >= 0 && lane - pa < __popcll(wb)) c0 = i1b * 64 + nth_bit(wb, lane - pa);
+        u64 w0 = c0 >= 0 ? ldcg64(a.fb0 + c0) : 0ull;
+        const bool st = c0 >= 0 && w0 == 0ull;
+        if (st) {   // unflag: bit (c0 & 63) of level-1 word c0 >> 6, as a 32-bit half
+            uint32_t *p = (uint32_t *)(s1 + (c0 >> 6)) + ((c0 >> 5) & 1);
+            atomicAnd(p, ~(1u << (c0 & 31)));
+        }
+        const unsigned stale = __ballot_sync(0xffffffffu, st);
+        if (lane == 0) n_stale += __popc(stale);
+        const int cnt = __popcll(w0);
+        int inc = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += t;
+        }
+        const int tot = __shfl_sync(0xffffffffu, inc, 31);
+        if (tot == 0) {
+            __syncwarp();
+            continue;
+        }
+        const int m = min(tot, mt);
+        // item p (p = lane, lane + 32) comes from the lane whose inclusive
+        // count first exceeds p
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int p = lane + 32 * h;
+            int lo = 0;
+#pragma unroll
+            for (int step = 16; step; step >>= 1) {
+                int v = __shfl_sync(0xffffffffu, inc, lo + step - 1);
+                if (v <= p) lo += step;
+            }
+            const int src = min(lo, 31);
+            const u64 w = __shfl_sync(0xffffffffu, w0, src);
+            const int ex = __shfl_sync(0xffffffffu, inc - cnt, src);
+            const int cw = __shfl_sync(0xffffffffu, c0, src);
+            if (p < m) rank_out[p] = cw * 64 + nth_bit(w, p - ex);
+        }
+        __syncwarp();
+        return m;
+    }
+}
+
+// Warp 0: the batch items (up to mt best candidates) with their data in B:
+// rank, linear index, dt2, coordinates and, with FULL, the ball's half-width,
+// clamped bounding square and row count (in upre[j + 1]).  Returns m.
+template <bool L1SMEM, bool FULL>
+__device__ int gather_items(const Inv &a, Batch &B, u64 *s1, u64 *s2, u64 *s3, int lane, int mt,
+                            const FastDiv &fd_nyz, const FastDiv &fd_nz, long long &n_stale)
+{
+    const int m = gather_top<L1SMEM>(a, s1, s2, s3, &B.cur1, lane, mt, B.rank, n_stale);
+    const uint32_t nyz = (uint32_t)a.ny * (uint32_t)a.nz;
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        const int j = lane + 32 * h;
+        if (j >= m) continue;
+        const int rkj = B.rank[j];
+        const int2 e = __ldg(a.okey + rkj);
+        const uint32_t x = fdiv((uint32_t)e.x, fd_nyz);
+        const uint32_t rem = (uint32_t)e.x - x * nyz;
+        const uint32_t y = fdiv(rem, fd_nz);
+        B.idx[j] = e.x;
+        B.r2[j] = e.y;
+        B.x[j] = (int)x; B.y[j] = (int)y; B.z[j] = (int)(rem - y * (uint32_t)a.nz);
+        if (FULL) {
+            const int hw = B.isq(e.y - 1);
+            B.h[j] = hw;
+            const int x0 = max((int)x - hw, 0), x1 = min((int)x + hw, a.nx - 1);
+            const int y0 = max((int)y - hw, 0), y1 = min((int)y + hw, a.ny - 1);
+            B.bx0[j] = x0; B.by0[j] = y0; B.wy[j] = y1 - y0 + 1;
+            B.upre[j + 1] = (x1 - x0 + 1) * (y1 - y0 + 1);
+            const int u0 = max((int)x - hw - 1, 0), u1 = min((int)x + hw + 1, a.nx - 1);
+            const int v0 = max((int)y - hw - 1, 0), v1 = min((int)y + hw + 1, a.ny - 1);
+            B.dx0[j] = u0; B.dy0[j] = v0; B.dwy[j] = v1 - v0 + 1;
+            // single-voxel balls use one shell unit (their six neighbours)
+            B.dpre[j + 1] = e.y == 1 ? 1 : (u1 - u0 + 1) * (v1 - v0 + 1);
+            B.cont32[j][0] = B.cont32[j][1] = 0u;
+            B.ovl32[j][0] = B.ovl32[j][1] = 0u;
+        }
+    }
+    __syncwarp();
+    return m;
+}
+
+// Flag rank r in the three summary levels (32-bit halves of the 64-bit
+// words; bit index r >> 6 in level 1, r >> 12 in level 2, r >> 18 in level 3).
+__device__ __forceinline__ void flag_rank(u64 *s1, u64 *s2, u64 *s3, int *cur1, int r)
+{
+    atomicMin(cur1, r >> 12);
+    atomicOr((uint32_t *)s1 + (r >> 11), 1u << ((r >> 6) & 31));
+    atomicOr((uint32_t *)s2 + (r >> 17), 1u << ((r >> 12) & 31));
+    atomicOr((uint32_t *)s3 + (r >> 23), 1u << ((r >> 18) & 31));
+}
+
+__device__ __forceinline__ void bar_sync_64() { asm volatile("bar.sync 1, 64;" ::: "memory"); }
+
+// Single-voxel regime.  Once the best candidate has dt2 == 1 every candidate
+// does, each ball is its own centre, and those centres are queued already:
+// stamping a batch changes no other voxel's candidate status, so each item
+// can look at its six neighbours once, before the commit, both to bound J and
+// to know what it will queue.  Runs on warps 0-1 (64 threads, named barrier
+// 1) until the best candidate is no longer single-voxel, the front is empty
+// or the step limit is reached.
+template <bool L1SMEM>
+__device__ void tiny_loop(const Inv &a, Batch &B, u64 *s1, u64 *s2, u64 *s3, const int tid, int64_t &k,
+                          const FastDiv &fd_nyz, const FastDiv &fd_nz, long long &n_stale, long long &n_it,
+                          long long &n_steps)
+{
+    const int lane = tid & 31;
+    for (;;) {
+        if (tid < 32) {
+            const int m = gather_items<L1SMEM, false>(a, B, s1, s2, s3, lane, kM, fd_nyz, fd_nz, n_stale);
+            if (lane == 0) {
+                int stop = 0, mcap = m;
+                const int64_t remain = a.max_steps - k;
+                if (m == 0) stop = 1;
+                else if (B.r2[0] != 1) stop = 4;
+                else {
+                    if (remain < (int64_t)m) mcap = (int)max(remain, (int64_t)0);
+                    if (mcap == 0) stop = 2;
                 }
-                int tot = __shfl_sync(0xffffffffu, inc, 31);
-                m = min(tot, kM);
-                int pos = inc - c;
-                while (w && pos < m) {
-                    B.rank[pos] = wi * 64 + __ffsll(w) - 1;
-                    w &= w - 1;
-                    pos++;
+                if (k > a.npore) stop = 3;
+                B.tstop = stop; B.m = m; B.mcap = mcap; B.J = mcap;
+            }
+        }
+        bar_sync_64();
+        const int st = B.tstop;
+        if (st) {
+            if (st != 4 && tid == 0) B.stop = st;
+            break;
+        }
+        const int m = B.m, mcap = B.mcap, j = tid;
+        Nb6 nb;
+        unsigned cand = 0;
+        int rr[6];
+        if (j < mcap) {
+            nb6(a, B.x[j], B.y[j], B.z[j], B.idx[j], nb);
+            cand = nb6_candidates(a, nb);
+            int best = INT_MAX;
+#pragma unroll
+            for (int q = 0; q < 6; q++) {
+                rr[q] = ((cand >> q) & 1) ? __ldg(a.rank + nb.v[q]) : INT_MAX;
+                best = min(best, rr[q]);
+            }
+            if (cand) atomicMin(&B.J, max(j + 1, lower_rank(B, m, best)));
+        }
+        bar_sync_64();
+        const int J = B.J;
+        if (j < J) {
+            const int x = B.x[j], y = B.y[j], z = B.z[j];
+            atomicAnd(a.avail + ((int64_t)x * a.ny + y) * a.NW + (z >> 5), ~(1u << (z & 31)));
+            a.seq[B.idx[j]] = (int32_t)(k + 1 + j);
+            const int r = B.rank[j];
+            atomicAnd(a.fb0 + (r >> 6), ~(1ull << (r & 63)));
+            if (k + j < a.cap) {
+                a.step_r2[k + j] = 1;
+                if (a.step_centre) a.step_centre[k + j] = B.idx[j];
+            }
+#pragma unroll
+            for (int q = 0; q < 6; q++) {
+                if (!((cand >> q) & 1)) continue;
+                if (atomicOr(a.added + nb.word[q], nb.bit[q]) & nb.bit[q]) continue;
+                const int rq = rr[q];
+                atomicOr(a.fb0 + (rq >> 6), 1ull << (rq & 63));
+                flag_rank(s1, s2, s3, &B.cur1, rq);
+            }
+        }
+        k += J;
+        if (tid == 0) { n_it++; n_steps += J; }
+        bar_sync_64();
+    }
+}
+
+template <bool L1SMEM>
+__global__ void __launch_bounds__(kNT, 1) k_invade(Inv a, FastDiv fd_nyz, FastDiv fd_nz, int *gC, int *gD)
+{
+    extern __shared__ u64 s_fb[];
+    __shared__ Batch B;
+    __shared__ int sLA[kList];
+    __shared__ unsigned char sLAi[kList];
+    __shared__ int sLC[kList];
+    __shared__ int sLD[kList];
+    u64 *s1 = L1SMEM ? s_fb : a.fb1;
+    u64 *s2 = s_fb + (L1SMEM ? a.NL1 : 0);
+    u64 *s3 = s2 + a.NL2;
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (L1SMEM)
+        for (int i = tid; i < a.NL1; i += kNT) s1[i] = a.fb1[i];
+    for (int i = tid; i < a.NL2; i += kNT) s2[i] = a.fb2[i];
+    for (int i = tid; i < a.NL3; i += kNT) s3[i] = a.fb3[i];
+    int *isq_t = (int *)(s3 + a.NL3);
+    for (int e = tid; e < a.isq_n; e += kNT) isq_t[e] = d_isqrt(e);
+    if (tid == 0) {
+        B.mtarget = kM;
+        B.cur1 = 0;
+        B.isq.t = isq_t;
+        B.isq.n = a.isq_n;
+    }
+    __syncthreads();
+
+    int64_t k = 0, iters = 0;
+    // diagnostics kept by thread 0: cycles per phase, items, stale summary bits
+    long long c_sel = 0, c_shell = 0, c_commit = 0, n_items = 0, n_commit_items = 0, n_stale = 0, n_units = 0;
+    long long c_small = 0, n_small = 0, n_tiny = 0, n_tiny_steps = 0, c_tiny = 0;
+    long long c_sub[6] = {0, 0, 0, 0, 0, 0};   // select sub-phases (all batches)
+    long long c_small_ph[3] = {0, 0, 0};       // select / bound / commit cycles of small batches
+    for (;;) {
+        long long t0 = clock64();
+        // ------------------------------------------------------ select batch
+        // The best candidates are the first set bits of the rank bitmap.  Lane
+        // 0 walks the summary levels to the first flagged level-1 word; the
+        // warp then loads the level-0 words of up to 32 flagged entries of
+        // that and the next three level-1 words, drops (and unflags) empty
+        // ones, and takes the leading set bits as the batch.
+        // S1 (warp 0): the batch items and their data.
+        if (tid < 32) {
+            const int m = gather_items<L1SMEM, true>(a, B, s1, s2, s3, lane, B.mtarget, fd_nyz, fd_nz, n_stale);
+            const bool bg0 = lane < m && B.r2[lane] > 1, bg1 = lane + 32 < m && B.r2[lane + 32] > 1;
+            const u64 big = (u64)__ballot_sync(0xffffffffu, bg0) | ((u64)__ballot_sync(0xffffffffu, bg1) << 32);
+            if (lane == 0) {
+                B.m = m;
+                B.big = big;
+                B.stop = m == 0 ? 1 : 0;
+                c_sub[0] += clock64() - t0;
+            }
+        }
+        __syncthreads();
+        if (B.stop) break;
+        if (B.r2[0] == 1) {
+            long long tt = clock64();
+            if (tid < 64) tiny_loop<L1SMEM>(a, B, s1, s2, s3, tid, k, fd_nyz, fd_nz, n_stale, n_tiny, n_tiny_steps);
+            if (tid == 0) B.kk = k;
+            __syncthreads();
+            k = B.kk;
+            if (tid == 0) c_tiny += clock64() - tt;
+            if (B.stop) break;
+            continue;
+        }
+        // S2 (all threads): pairwise tests between every item j and every item
+        // b whose ball is more than its centre voxel (two distinct
+        // single-voxel balls never meet).  cont: j lies in the ball of an
+        // earlier b; ovl: the ball boxes of j and b, grown by one voxel, meet.
+        {
+            const long long tb = clock64();
+            const int m = B.m;
+            const u64 big = B.big;
+            const int npair = __popcll(big) * m;
+            for (int p = tid; p < npair; p += kNT) {
+                const int bi = p / m, j = p - bi * m;
+                const int b = nth_bit(big, bi);
+                if (j == b) continue;
+                const int dx = B.x[j] - B.x[b], dy = B.y[j] - B.y[b], dz = B.z[j] - B.z[b];
+                if (b < j && (int64_t)dx * dx + (int64_t)dy * dy + (int64_t)dz * dz < (int64_t)B.r2[b])
+                    atomicOr(&B.cont32[j][b >> 5], 1u << (b & 31));
+                const int lim = B.h[b] + B.h[j] + 1;
+                if (abs(dx) <= lim && abs(dy) <= lim && abs(dz) <= lim) {
+                    atomicOr(&B.ovl32[j][b >> 5], 1u << (b & 31));
+                    atomicOr(&B.ovl32[b][j >> 5], 1u << (j & 31));
                 }
             }
-            __syncwarp();
-            // item data
-            const int64_t nyz = (int64_t)a.ny * a.nz;
-            for (int j = lane; j < m; j += 32) {
-                int2 e = __ldg(a.okey + B.rank[j]);
-                B.idx[j] = e.x;
-                B.r2[j] = e.y;
-                int x = (int)(e.x / nyz), rem = (int)(e.x - (int64_t)x * nyz);
-                int y = rem / a.nz, z = rem - y * a.nz;
-                B.x[j] = x; B.y[j] = y; B.z[j] = z;
-                int h = d_ball_hw(e.y);
-                int x0 = max(x - h, 0), x1 = min(x + h, a.nx - 1);
-                int y0 = max(y - h, 0), y1 = min(y + h, a.ny - 1);
-                B.bx0[j] = x0; B.by0[j] = y0; B.wy[j] = y1 - y0 + 1;
-                B.upre[j + 1] = (x1 - x0 + 1) * (y1 - y0 + 1);   // rows, fixed below
-            }
-            __syncwarp();
-            // Pairwise tests, looping only over items whose ball is more than
-            // the centre voxel (r2 > 1): two distinct r2 == 1 balls never
-            // meet.  cont: item j lies in the ball of an earlier item b;
-            // ovl: the ball boxes of j and b, grown by one voxel, intersect.
-            int hj[2];
-            u64 cont[2] = {0ull, 0ull}, ovl[2] = {0ull, 0ull};
-            bool bg[2];
+            __syncthreads();
+            if (tid == 0) c_sub[2] += clock64() - tb;
+        }
+        // S3 (warp 0): skip covered items, apply the step limit and the row
+        // budget, number the steps, prefix-sum the row units.
+        if (tid < 32) {
+            const long long tc = clock64();
+            const int m = B.m;
+            u64 cont[2];
+#pragma unroll
             for (int q = 0; q < 2; q++) {
-                int j = lane + 32 * q;
-                bg[q] = j < m && B.r2[j] > 1;
-                hj[q] = j < m ? d_ball_hw(B.r2[j]) : 0;
-            }
-            u64 big = (u64)__ballot_sync(0xffffffffu, bg[0]) | ((u64)__ballot_sync(0xffffffffu, bg[1]) << 32);
-            for (u64 bm = big; bm; bm &= bm - 1) {
-                const int b = __ffsll(bm) - 1;
-                const int bx = B.x[b], by = B.y[b], bz = B.z[b], br2 = B.r2[b];
-                const int bh = d_ball_hw(br2);
-                u64 hit = 0;
-                for (int q = 0; q < 2; q++) {
-                    int j = lane + 32 * q;
-                    if (j >= m || j == b) continue;
-                    int64_t dx = B.x[j] - bx, dy = B.y[j] - by, dz = B.z[j] - bz;
-                    if (b < j && dx * dx + dy * dy + dz * dz < (int64_t)br2) cont[q] |= 1ull << b;
-                    int64_t lim = bh + hj[q] + 1;
-                    if (llabs(dx) <= lim && llabs(dy) <= lim && llabs(dz) <= lim) {
-                        ovl[q] |= 1ull << b;
-                        hit |= 1ull << j;
-                    }
-                }
-                u64 hall = (u64)__ballot_sync(0xffffffffu, (hit & 0xffffffffull) != 0) |
-                           ((u64)__ballot_sync(0xffffffffu, (hit >> 32) != 0) << 32);
-                if ((b & 31) == lane) ovl[b >> 5] |= hall;
+                const int j = lane + 32 * q;
+                cont[q] = j < m ? ((u64)B.cont32[j][0] | ((u64)B.cont32[j][1] << 32)) : 0ull;
+                if (j < m) B.ovl[j] = (u64)B.ovl32[j][0] | ((u64)B.ovl32[j][1] << 32);
             }
             u64 has = (u64)__ballot_sync(0xffffffffu, cont[0] != 0) |
                       ((u64)__ballot_sync(0xffffffffu, cont[1] != 0) << 32);
@@ -411,44 +746,66 @@ __global__ void __launch_bounds__(kNT, 1) k_invade(Inv a)
                 u64 cj = __shfl_sync(0xffffffffu, j < 32 ? cont[0] : cont[1], j & 31);
                 if (!(cj & keep)) keep |= 1ull << j;
             }
-            for (int q = 0; q < 2; q++) {
-                int j = lane + 32 * q;
-                if (j < m) B.ovl[j] = ovl[q];
-            }
-            // step limit
+            // step limit: items past the (max_steps - k)-th kept one are dropped
             int mcap = m;
             int64_t remain = a.max_steps - k;
-            int nkeep = __popcll(keep);
-            if ((int64_t)nkeep > remain) {
+            if ((int64_t)__popcll(keep) > remain) {
                 u64 t = keep;
                 for (int64_t q = 0; q < remain; q++) t &= t - 1;
-                mcap = __ffsll(t) - 1;   // first item beyond the limit
+                mcap = __ffsll(t) - 1;
             }
-            for (int h = 0; h < 2; h++) {
-                int j = lane + 32 * h;
-                if (j < m) {
-                    bool kp = (keep >> j) & 1;
-                    B.step[j] = kp ? __popcll(keep & ((1ull << j) - 1)) : -1;
-                    if (!kp || j >= mcap) B.upre[j + 1] = 0;
-                }
+            // row units of kept items below mcap, prefix-summed (two items per
+            // lane): ball rows (stamping) and shell rows (candidates); the
+            // batch stops before the shell-row budget is exceeded
+            int j0 = 2 * lane, j1 = 2 * lane + 1;
+            const bool k0 = j0 < mcap && ((keep >> j0) & 1), k1 = j1 < mcap && ((keep >> j1) & 1);
+            int r0 = k0 ? B.upre[j0 + 1] : 0, r1 = k1 ? B.upre[j1 + 1] : 0;
+            int d0 = k0 ? B.dpre[j0 + 1] : 0, d1 = k1 ? B.dpre[j1 + 1] : 0;
+            int inc = r0 + r1, dinc = d0 + d1;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int t = __shfl_up_sync(0xffffffffu, inc, o);
+                int td = __shfl_up_sync(0xffffffffu, dinc, o);
+                if (lane >= o) { inc = min(inc + t, 1 << 30); dinc = min(dinc + td, 1 << 30); }
+            }
+            int ex = inc - r0 - r1, dex = dinc - d0 - d1;
+            const bool over0 = j0 > 0 && dex + d0 > kRowBudget;
+            const bool over1 = dex + d0 + d1 > kRowBudget;
+            unsigned ob0 = __ballot_sync(0xffffffffu, over0), ob1 = __ballot_sync(0xffffffffu, over1);
+            int cut = 64;
+            if (ob0 | ob1) {
+                int l = __ffs(ob0 | ob1) - 1;
+                cut = ((ob0 >> l) & 1) ? 2 * l : 2 * l + 1;
+            }
+            mcap = min(mcap, cut);
+            __syncwarp();
+            if (j0 < m) {
+                B.step[j0] = ((keep >> j0) & 1) ? __popcll(keep & ((1ull << j0) - 1)) : -1;
+                B.upre[j0 + 1] = j0 < mcap ? ex + r0 : 0;
+                B.dpre[j0 + 1] = j0 < mcap ? dex + d0 : 0;
+            }
+            if (j1 < m) {
+                B.step[j1] = ((keep >> j1) & 1) ? __popcll(keep & ((1ull << j1) - 1)) : -1;
+                B.upre[j1 + 1] = j1 < mcap ? ex + r0 + r1 : 0;
+                B.dpre[j1 + 1] = j1 < mcap ? dex + d0 + d1 : 0;
             }
             __syncwarp();
             if (lane == 0) {
-                // row units, prefix-summed; a batch never holds more than 2^30
-                // of them (keeps the unit index in an int)
                 B.upre[0] = 0;
-                for (int j = 0; j < m; j++) {
-                    if (j > 0 && j < mcap && (int64_t)B.upre[j] + B.upre[j + 1] > (1 << 30)) mcap = j;
-                    B.upre[j + 1] = j < mcap ? B.upre[j] + B.upre[j + 1] : B.upre[j];
-                }
-                B.m = m;
+                B.dpre[0] = 0;
+                const int last = mcap > 0 ? B.upre[mcap] : 0, dlast = mcap > 0 ? B.dpre[mcap] : 0;
+                for (int j = mcap; j < m; j++) { B.upre[j + 1] = last; B.dpre[j + 1] = dlast; }
                 B.mcap = mcap;
                 B.J = mcap;
-                B.stop = (m == 0) ? 1 : (mcap == 0 ? 2 : 0);
                 B.keep = keep;
+                B.stop = mcap == 0 ? 2 : 0;
+                B.nA = 0; B.nC = 0; B.nD = 0;
+                c_sub[3] += clock64() - tc;
             }
         }
         __syncthreads();
+        long long t1 = clock64();
+        c_sel += t1 - t0;
         if (B.stop) break;
         if (k > a.npore) {   // every step invades its own centre: cannot happen
             if (tid == 0) B.stop = 3;
@@ -456,42 +813,93 @@ __global__ void __launch_bounds__(kNT, 1) k_invade(Inv a)
         }
         const int mcap = B.mcap, m = B.m;
 
-        // ---------------------------------------------------- shell pass
+        // ---------------------------------------- candidate bound (shell)
+        // Stage 1 lists the never-queued, uninvaded neighbours u of each kept
+        // ball; stage 2 looks up their ranks in parallel and lowers J to
+        // max(i + 1, #items ranked above u).
         {
-            const int U = B.upre[mcap];
+            const int U = B.dpre[mcap];
             for (int u = tid; u < U; u += kNT) {
-                int i = unit_item(B, mcap + 1, u);
-                if (i + 1 >= *(volatile int *)&B.J) continue;   // cannot tighten J
-                int t = u - B.upre[i];
-                int x = B.bx0[i] + t / B.wy[i], y = B.by0[i] + t % B.wy[i];
-                int lo, hi;
-                if (!ball_run(B, i, x, y, lo, hi)) continue;
-                for_each_shell(a, B, i, x, y, lo, hi, [&](int xr, int yr, int za, int zb) {
-                    int64_t rb = ((int64_t)xr * a.ny + yr) * a.NW;
-                    int64_t vb = ((int64_t)xr * a.ny + yr) * a.nz;
-                    for (int w = za >> 5; w <= (zb >> 5); w++) {
-                        uint32_t cand = ldcg32(a.avail + rb + w) & ~ldcg32(a.added + rb + w) & span_mask(w, za, zb);
-                        while (cand) {
-                            int z = w * 32 + __ffs(cand) - 1;
-                            cand &= cand - 1;
-                            int ru = __ldg(a.rank + vb + z);
-                            int c = max(i + 1, lower_rank(B, m, ru));
-                            atomicMin(&B.J, c);
+                // units are ordered by item: past the rows of items below the
+                // current J nothing can lower it any more
+                if (u >= B.dpre[*(volatile int *)&B.J]) break;
+                int i = unit_item(B.dpre, mcap + 1, u);
+                if (i + 1 >= *(volatile int *)&B.J) continue;   // cannot lower J
+                if (B.r2[i] == 1) {
+                    // single-voxel ball: its shell is its six neighbours
+                    Nb6 nb;
+                    nb6(a, B.x[i], B.y[i], B.z[i], B.idx[i], nb);
+                    unsigned c = nb6_candidates(a, nb);
+                    if (c) {
+                        int ru[6];
+#pragma unroll
+                        for (int q = 0; q < 6; q++) ru[q] = ((c >> q) & 1) ? __ldg(a.rank + nb.v[q]) : INT_MAX;
+                        int best = INT_MAX;
+#pragma unroll
+                        for (int q = 0; q < 6; q++) best = min(best, ru[q]);
+                        atomicMin(&B.J, max(i + 1, lower_rank(B, m, best)));
+                    }
+                    continue;
+                }
+                const int t = u - B.dpre[i];
+                const int x = B.dx0[i] + t / B.dwy[i], y = B.dy0[i] + t % B.dwy[i];
+                int za, zb, ra, rbz;
+                if (!shell_row(a, B, i, x, y, za, zb, ra, rbz)) continue;
+                const int64_t row = (int64_t)x * a.ny + y;
+                for (int w = za >> 5; w <= (zb >> 5); w++) {
+                    uint32_t cand = ldcg32(a.avail + row * a.NW + w) & ~ldcg32(a.added + row * a.NW + w) &
+                                    span_mask(w, za, zb) & ~span_mask(w, ra, rbz);
+                    for (; cand; cand &= cand - 1) {
+                        const int z = w * 32 + __ffs(cand) - 1;
+                        const int slot = atomicAdd(&B.nA, 1);
+                        if (slot < kList) {
+                            sLA[slot] = (int)(row * a.nz + z);
+                            sLAi[slot] = (unsigned char)i;
+                        } else {
+                            const int ru = __ldg(a.rank + row * a.nz + z);
+                            atomicMin(&B.J, max(i + 1, lower_rank(B, m, ru)));
                         }
                     }
-                });
+                }
+            }
+            __syncthreads();
+            const int n = min(B.nA, kList);
+            for (int e = tid; e < n; e += kNT) {
+                int i = sLAi[e];
+                if (i + 1 >= *(volatile int *)&B.J) continue;
+                int ru = __ldg(a.rank + sLA[e]);
+                atomicMin(&B.J, max(i + 1, lower_rank(B, m, ru)));
             }
         }
         __syncthreads();
+        long long t2 = clock64();
+        c_shell += t2 - t1;
 
-        // --------------------------------------------------- commit pass
+        // --------------------------------------------------------- commit
+        // Stage 1, per row of each committed ball: stamp the voxels this ball
+        // owns (not covered by a lower committed ball), list the stamped ones
+        // that were queued candidates (removals) and the neighbours outside
+        // every committed ball that become candidates (additions; the atomic
+        // on `added` makes each listed once).  Stage 2 applies both lists to
+        // the rank bitmap in parallel.
+        const int J = B.J;
+        const u64 jmask = J >= 64 ? ~0ull : ((1ull << J) - 1);
         {
-            const int J = B.J;
-            const u64 jmask = J >= 64 ? ~0ull : ((1ull << J) - 1);
             const int64_t k1 = k + 1;
             const int U = B.upre[J];
             for (int u = tid; u < U; u += kNT) {
-                int i = unit_item(B, J + 1, u);
+                int i = unit_item(B.upre, J + 1, u);
+                if (B.r2[i] == 1) {
+                    // a kept single-voxel item is a queued candidate that no
+                    // lower ball covers: it owns its voxel and its rank is known
+                    const int x = B.x[i], y = B.y[i], z = B.z[i];
+                    const int64_t w = ((int64_t)x * a.ny + y) * a.NW + (z >> 5);
+                    atomicAnd(a.avail + w, ~(1u << (z & 31)));
+                    a.seq[B.idx[i]] = (int32_t)(k1 + B.step[i]);
+                    const int r = B.rank[i];
+                    atomicAnd(a.fb0 + (r >> 6), ~(1ull << (r & 63)));
+                    continue;
+                }
                 int t = u - B.upre[i];
                 int x = B.bx0[i] + t / B.wy[i], y = B.by0[i] + t % B.wy[i];
                 int lo, hi;
@@ -500,9 +908,10 @@ __global__ void __launch_bounds__(kNT, 1) k_invade(Inv a)
                 const int64_t rb = ((int64_t)x * a.ny + y) * a.NW;
                 const int64_t vb = ((int64_t)x * a.ny + y) * a.nz;
                 const int32_t label = (int32_t)(k1 + B.step[i]);
+                const u64 lower = B.ovl[i] & B.keep & ((1ull << i) - 1);
                 for (int w = z0 >> 5; w <= (z1 >> 5); w++) {
                     uint32_t own = span_mask(w, z0, z1);
-                    for (u64 om = B.ovl[i] & B.keep & ((1ull << i) - 1); om && own; om &= om - 1) {
+                    for (u64 om = lower; om && own; om &= om - 1) {
                         int i2 = __ffsll(om) - 1, l2, h2;
                         if (ball_run(B, i2, x, y, l2, h2)) own &= ~span_mask(w, l2, h2);
                     }
@@ -511,43 +920,13 @@ __global__ void __launch_bounds__(kNT, 1) k_invade(Inv a)
                     if (!newly) continue;
                     atomicAnd(a.avail + rb + w, ~newly);
                     uint32_t gone = newly & ldcg32(a.added + rb + w);
-                    uint32_t n2 = newly;
-                    while (n2) {
-                        int z = w * 32 + __ffs(n2) - 1;
-                        n2 &= n2 - 1;
-                        a.seq[vb + z] = label;
-                    }
-                    while (gone) {
-                        int z = w * 32 + __ffs(gone) - 1;
-                        gone &= gone - 1;
-                        int r = __ldg(a.rank + vb + z);
-                        atomicAnd(a.fb0 + (r >> 6), ~(1ull << (r & 63)));
+                    for (uint32_t n2 = newly; n2; n2 &= n2 - 1) a.seq[vb + w * 32 + __ffs(n2) - 1] = label;
+                    for (; gone; gone &= gone - 1) {
+                        int v = (int)(vb + w * 32 + __ffs(gone) - 1);
+                        int slot = atomicAdd(&B.nC, 1);
+                        if (slot < kList) sLC[slot] = v; else gC[slot - kList] = v;
                     }
                 }
-                for_each_shell(a, B, i, x, y, lo, hi, [&](int xr, int yr, int za, int zb) {
-                    int64_t rb2 = ((int64_t)xr * a.ny + yr) * a.NW;
-                    int64_t vb2 = ((int64_t)xr * a.ny + yr) * a.nz;
-                    for (int w = za >> 5; w <= (zb >> 5); w++) {
-                        uint32_t msk = span_mask(w, za, zb);
-                        for (u64 om = B.ovl[i] & B.keep & jmask; om && msk; om &= om - 1) {
-                            int i2 = __ffsll(om) - 1, l2, h2;
-                            if (ball_run(B, i2, xr, yr, l2, h2)) msk &= ~span_mask(w, l2, h2);
-                        }
-                        if (!msk) continue;
-                        uint32_t cand = ldcg32(a.avail + rb2 + w) & ~ldcg32(a.added + rb2 + w) & msk;
-                        if (!cand) continue;
-                        atomicOr(a.added + rb2 + w, cand);
-                        while (cand) {
-                            int z = w * 32 + __ffs(cand) - 1;
-                            cand &= cand - 1;
-                            int r = __ldg(a.rank + vb2 + z);
-                            atomicOr(a.fb0 + (r >> 6), 1ull << (r & 63));
-                            atomicOr(s1 + (r >> 12), 1ull << ((r >> 6) & 63));
-                            atomicOr(s2 + (r >> 18), 1ull << ((r >> 12) & 63));
-                            atomicOr(s3 + (r >> 24), 1ull << ((r >> 18) & 63));
-                        }
-                    }
-                });
             }
             for (int j = tid; j < J; j += kNT) {
                 if (B.step[j] < 0) continue;
@@ -558,15 +937,106 @@ __global__ void __launch_bounds__(kNT, 1) k_invade(Inv a)
                 }
             }
         }
-        // steps committed: kept items below J
-        k += __popcll(B.keep & (B.J >= 64 ? ~0ull : ((1ull << B.J) - 1)));
-        iters++;
         __syncthreads();
+        // Stage 2: with every committed ball stamped, a shell voxel that is
+        // still uninvaded and never queued lies outside all of them: queue it.
+        {
+            const int U = B.dpre[J];
+            for (int u = tid; u < U; u += kNT) {
+                const int i = unit_item(B.dpre, J + 1, u);
+                if (B.r2[i] == 1) {
+                    Nb6 nb;
+                    nb6(a, B.x[i], B.y[i], B.z[i], B.idx[i], nb);
+                    unsigned c = nb6_candidates(a, nb);
+                    unsigned fr = 0;
+#pragma unroll
+                    for (int q = 0; q < 6; q++)
+                        if ((c >> q) & 1)
+                            if (!(atomicOr(a.added + nb.word[q], nb.bit[q]) & nb.bit[q])) fr |= 1u << q;
+                    int rr[6];
+#pragma unroll
+                    for (int q = 0; q < 6; q++) rr[q] = ((fr >> q) & 1) ? __ldg(a.rank + nb.v[q]) : -1;
+#pragma unroll
+                    for (int q = 0; q < 6; q++) {
+                        const int r = rr[q];
+                        if (r < 0) continue;
+                        atomicOr(a.fb0 + (r >> 6), 1ull << (r & 63));
+                        flag_rank(s1, s2, s3, &B.cur1, r);
+                    }
+                    continue;
+                }
+                const int t = u - B.dpre[i];
+                const int x = B.dx0[i] + t / B.dwy[i], y = B.dy0[i] + t % B.dwy[i];
+                int za, zb, ra, rbz;
+                if (!shell_row(a, B, i, x, y, za, zb, ra, rbz)) continue;
+                const int64_t row = (int64_t)x * a.ny + y;
+                for (int w = za >> 5; w <= (zb >> 5); w++) {
+                    const uint32_t cand = ldcg32(a.avail + row * a.NW + w) & ~ldcg32(a.added + row * a.NW + w) &
+                                          span_mask(w, za, zb) & ~span_mask(w, ra, rbz);
+                    if (!cand) continue;
+                    uint32_t fresh = cand & ~atomicOr(a.added + row * a.NW + w, cand);
+                    for (; fresh; fresh &= fresh - 1) {
+                        const int v = (int)(row * a.nz + w * 32 + __ffs(fresh) - 1);
+                        const int slot = atomicAdd(&B.nD, 1);
+                        if (slot < kList) sLD[slot] = v; else gD[slot - kList] = v;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        // Stage 3: apply removals and additions to the rank bitmap.
+        {
+            const int nC = B.nC, nD = B.nD;
+            for (int e = tid; e < nC + nD; e += kNT) {
+                if (e < nC) {
+                    int v = e < kList ? sLC[e] : gC[e - kList];
+                    int r = __ldg(a.rank + v);
+                    atomicAnd(a.fb0 + (r >> 6), ~(1ull << (r & 63)));
+                } else {
+                    int f = e - nC;
+                    int v = f < kList ? sLD[f] : gD[f - kList];
+                    int r = __ldg(a.rank + v);
+                    atomicOr(a.fb0 + (r >> 6), 1ull << (r & 63));
+                    flag_rank(s1, s2, s3, &B.cur1, r);
+                }
+            }
+        }
+        k += __popcll(B.keep & jmask);
+        iters++;
+        n_items += m;
+        n_commit_items += J;
+        n_units += B.upre[J];
+        if (tid == 0) B.mtarget = min(kM, max(16, 2 * J + 8));
+        const bool small = B.upre[J] == __popcll(B.keep & jmask) && B.r2[0] == 1;
+        __syncthreads();
+        long long t3 = clock64();
+        c_commit += t3 - t2;
+        if (small) {
+            c_small += t3 - t0;
+            n_small++;
+            c_small_ph[0] += t1 - t0;
+            c_small_ph[1] += t2 - t1;
+            c_small_ph[2] += t3 - t2;
+        }
     }
     if (tid == 0) {
         a.out[0] = k;
         a.out[1] = (B.stop == 2) ? IBIP_ERR_STEP_LIMIT : (B.stop == 3 ? IBIP_ERR_BOUNDS : IBIP_OK);
         a.out[2] = iters;
+        a.out[3] = c_sel;
+        a.out[4] = c_shell;
+        a.out[5] = c_commit;
+        a.out[6] = n_items;
+        a.out[7] = n_commit_items;
+        a.out[8] = n_stale;
+        a.out[9] = n_units;
+        a.out[10] = c_small;
+        a.out[11] = n_small;
+        for (int q = 0; q < 4; q++) a.out[12 + q] = c_sub[q];
+        for (int q = 0; q < 3; q++) a.out[16 + q] = c_small_ph[q];
+        a.out[19] = n_tiny;
+        a.out[20] = n_tiny_steps;
+        a.out[21] = c_tiny;
     }
 }
 
@@ -579,7 +1049,7 @@ int ibip_invade_run(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, i
 {
     cudaStream_t s = ctx->stream;
     const int64_t N = nvox(d);
-    int *stats = (int *)ibip_scratch(ctx, SC_SMALL, 256);
+    int *stats = (int *)ibip_scratch(ctx, SC_SMALL, kSmallBytes);
     if (!stats) return IBIP_ERR_OOM;
     int *h = (int *)ctx->h_pinned;
     ibip_prof_begin(ctx, IBIP_K_RANK);
@@ -595,7 +1065,8 @@ int ibip_invade_run(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, i
     IBIP_LAUNCH(ctx);
     if (npore == 0) {
         ibip_prof_end(ctx, IBIP_K_RANK);
-        h_out[0] = 0; h_out[1] = IBIP_OK; h_out[2] = 0;
+        for (int i = 0; i < kNOut; i++) h_out[i] = 0;
+        h_out[1] = IBIP_OK;
         return ibip_cuda_status(cudaStreamSynchronize(s));
     }
 
@@ -652,7 +1123,7 @@ int ibip_invade_run(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, i
     a.added = (uint32_t *)ibip_scratch(ctx, SC_ADDED, nw * sizeof(uint32_t));
     size_t nfb = (size_t)a.NL0 + a.NL1 + a.NL2 + a.NL3;
     u64 *fb = (u64 *)ibip_scratch(ctx, SC_FB, nfb * sizeof(u64));
-    int64_t *out = (int64_t *)ibip_scratch(ctx, SC_SMALL, 256);
+    int64_t *out = (int64_t *)ibip_scratch(ctx, SC_SMALL, kSmallBytes);
     if (!a.avail || !a.added || !fb || !out) return IBIP_ERR_OOM;
     out += 8;
     a.fb0 = fb; a.fb1 = fb + a.NL0; a.fb2 = a.fb1 + a.NL1; a.fb3 = a.fb2 + a.NL2;
@@ -662,22 +1133,26 @@ int ibip_invade_run(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, i
     IBIP_LAUNCH(ctx);
     ibip_prof_end(ctx, IBIP_K_RANK);
 
+    int *gl = (int *)ibip_scratch(ctx, SC_LIST, (size_t)2 * npore * sizeof(int) + 64);
+    if (!gl) return IBIP_ERR_OOM;
+    const FastDiv fd_nyz = make_fastdiv((uint32_t)d.ny * (uint32_t)d.nz), fd_nz = make_fastdiv((uint32_t)d.nz);
     const bool l1smem = a.NL1 <= kSmemL1Max;
-    size_t dyn = ((l1smem ? a.NL1 : 0) + (size_t)a.NL2 + a.NL3) * sizeof(u64);
+    a.isq_n = std::min(maxd + 1, 16384);
+    size_t dyn = ((l1smem ? a.NL1 : 0) + (size_t)a.NL2 + a.NL3) * sizeof(u64) + (size_t)a.isq_n * sizeof(int);
     ibip_prof_begin(ctx, IBIP_K_INVADE);
     if (l1smem) {
         cudaFuncSetAttribute(k_invade<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn + 1024);
-        k_invade<true><<<1, kNT, dyn, s>>>(a);
+        k_invade<true><<<1, kNT, dyn, s>>>(a, fd_nyz, fd_nz, gl, gl + npore);
     } else {
         cudaFuncSetAttribute(k_invade<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn + 1024);
-        k_invade<false><<<1, kNT, dyn, s>>>(a);
+        k_invade<false><<<1, kNT, dyn, s>>>(a, fd_nyz, fd_nz, gl, gl + npore);
     }
     IBIP_LAUNCH(ctx);
     ibip_prof_end(ctx, IBIP_K_INVADE);
     int64_t *ho = (int64_t *)ctx->h_pinned;
-    cudaMemcpyAsync(ho, out, 3 * sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(ho, out, kNOut * sizeof(int64_t), cudaMemcpyDeviceToHost, s);
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return ibip_cuda_status(e);
-    h_out[0] = ho[0]; h_out[1] = ho[1]; h_out[2] = ho[2];
+    for (int i = 0; i < kNOut; i++) h_out[i] = ho[i];
     return IBIP_OK;
 }

@@ -106,7 +106,7 @@ int ibip_maximin_launch(ibip_ctx *ctx, const int32_t *val, ibip_dims d, int face
     const int tx = (d.nx + TX - 1) / TX, ty = (d.ny + TY - 1) / TY, tz = (d.nz + TZ - 1) / TZ;
     const int nt = tx * ty * tz;
     int *act = (int *)ibip_scratch(ctx, SC_TILE, (size_t)nt * sizeof(int));
-    int *small = (int *)ibip_scratch(ctx, SC_SMALL, 256);
+    int *small = (int *)ibip_scratch(ctx, SC_SMALL, kSmallBytes);
     if (!act || !small) return IBIP_ERR_OOM;
     int *last = small + 4;
     ibip_prof_begin(ctx, IBIP_K_MAXIMIN);

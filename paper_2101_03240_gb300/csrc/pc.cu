@@ -103,7 +103,7 @@ int ibip_pc_launch(ibip_ctx *ctx, const int32_t *seq, ibip_dims d, const int32_t
     cudaStream_t s = ctx->stream;
     const int64_t N = nvox(d);
     int32_t *cnt = (int32_t *)ibip_scratch(ctx, SC_HIST, ((size_t)K + 2) * sizeof(int32_t));
-    int *small = (int *)ibip_scratch(ctx, SC_SMALL, 256);
+    int *small = (int *)ibip_scratch(ctx, SC_SMALL, kSmallBytes);
     if (!cnt || !small) return IBIP_ERR_OOM;
     int *np = small + 8;
     ibip_prof_begin(ctx, IBIP_K_PC);
@@ -140,7 +140,7 @@ int ibip_trap_finish(ibip_ctx *ctx, const int32_t *seq, const int32_t *M, ibip_d
         ibip_prof_end(ctx, IBIP_K_TRAP);
         return ibip_cuda_status(cudaGetLastError());
     }
-    int *small = (int *)ibip_scratch(ctx, SC_SMALL, 256);
+    int *small = (int *)ibip_scratch(ctx, SC_SMALL, kSmallBytes);
     if (!small) return IBIP_ERR_OOM;
     int *mx = small + 12;
     ibip_prof_begin(ctx, IBIP_K_TRAP);

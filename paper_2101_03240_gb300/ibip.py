@@ -66,6 +66,7 @@ def _lib():
                 "ibip_launch_count": (i64, [P]),
                 "ibip_status_string": (C.c_char_p, [C.c_int]),
                 "ibip_profile_enable": (C.c_int, [P, C.c_int]),
+                "ibip_invade_stats": (C.c_int, [P, C.POINTER(i64), C.c_int]),
                 "ibip_profile_read": (C.c_int, [P, C.c_int, C.POINTER(dbl), C.POINTER(i64)]),
             }
             for name, (res, args) in sig.items():
@@ -137,6 +138,14 @@ class Context:
         if st != OK:
             raise IbipError("ibip_profile_read", st)
         return float(ms.value), int(n.value)
+
+    def invade_stats(self) -> dict:
+        """Counters of the last invade call (see ibip_invade_stats)."""
+        a = (C.c_int64 * 36)()
+        _lib().ibip_invade_stats(self._h, a, 36)
+        keys = ["steps", "status", "iterations", "cycles_select", "cycles_bound", "cycles_commit", "items",
+                "items_committed", "stale_bits", "rows_committed", "cycles_small_batches", "small_batches", "sel_gather", "sel_items", "sel_pairs", "sel_tail", "small_select", "small_bound", "small_commit", "tiny_iterations", "tiny_steps", "cycles_tiny", "g_walk", "g_words", "g_scan", "g_extract", "g_items", "t_walk", "t_words", "t_scan", "t_extract", "t_items", "tiny_gather", "tiny_bound", "tiny_commit"]
+        return dict(zip(keys, [int(x) for x in a]))
 
     def synchronize(self):
         st = _lib().ibip_synchronize(self._h)
