@@ -57,7 +57,8 @@ typedef enum {
     IBIP_ERR_STEP_LIMIT = -4,    /* invasion stopped at max_steps with candidates left */
     IBIP_ERR_NOT_CONVERGED = -5, /* propagation hit its round limit */
     IBIP_ERR_CANCELLED = -6,     /* reserved */
-    IBIP_ERR_BOUNDS = -7         /* a device-side index check failed */
+    IBIP_ERR_BOUNDS = -7,        /* a device-side index check failed */
+    IBIP_ERR_TOO_LARGE = -8      /* image larger than ibip_edt_noalloc's fixed scratch */
 } ibip_status;
 
 /* Image faces: X0 is the face x = 0, X1 is x = nx-1, and so on. */
@@ -85,6 +86,29 @@ IBIP_API int ibip_set_stream(ibip_ctx *ctx, void *cuda_stream);
  *   dt2:   int32[nx*ny*nz] output as defined above (exact integers).
  * Asynchronous. */
 IBIP_API int ibip_edt(ibip_ctx *ctx, const uint8_t *image, ibip_dims dims, int32_t *dt2);
+
+/* ibip_edt without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that must not allocate device memory
+ * at call time -- code whose device memory is owned by a pool, an arena or a
+ * host framework that forbids (or would be fragmented by) direct cudaMalloc,
+ * and latency-sensitive loops that cannot afford the implicit device-wide
+ * synchronisation cudaMalloc/cudaFree may cause.  It takes no context.
+ *   image:       uint8[nx*ny*nz] device buffer, nonzero = pore.
+ *   dims:        nx*ny*nz must not exceed 2^21 (2,097,152) voxels, e.g. 128^3;
+ *                larger images return IBIP_ERR_TOO_LARGE and queue nothing.
+ *   dt2:         int32[nx*ny*nz] device output, same values as ibip_edt.
+ *                Its memory also holds an intermediate during the call.
+ *   cuda_stream: cudaStream_t to queue on (NULL = legacy default stream).
+ * Works on the current CUDA device.  Scratch is one fixed 8 MB device array
+ * compiled into the library: every GPU that loads the library keeps it until
+ * the process exits, and every call on a device shares it, so calls that
+ * overlap on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller.  The first call on each device looks up that
+ * array's device address once; make that first call before any stream
+ * capture on the device.  Allocates nothing: no cudaMalloc, no cudaFree.
+ * Asynchronous.  Returns IBIP_OK, IBIP_ERR_ARG, IBIP_ERR_TOO_LARGE or
+ * IBIP_ERR_CUDA. */
+IBIP_API int ibip_edt_noalloc(const uint8_t *image, ibip_dims dims, int32_t *dt2, void *cuda_stream);
 
 /* Volume-controlled invasion (Section 2.1, Figures 1-2; footnote 1).
  * Step k = 1, 2, ... picks the candidate voxel c with the largest dt2 --

@@ -319,6 +319,7 @@ const char *ibip_status_string(int s)
     case IBIP_ERR_NOT_CONVERGED: return "propagation did not converge within its round limit";
     case IBIP_ERR_CANCELLED: return "cancelled";
     case IBIP_ERR_BOUNDS: return "device index check failed";
+    case IBIP_ERR_TOO_LARGE: return "image exceeds the fixed scratch of ibip_edt_noalloc (2^21 voxels)";
     default: return "unknown status";
     }
 }

@@ -201,3 +201,75 @@ int ibip_dilate_level_launch(ibip_ctx *ctx, const int32_t *W, int32_t T, int32_t
     while ((int64_t)(cap + 1) * (cap + 1) < T && cap < 0xfffe) cap++;
     return edt_passes(ctx, FeatAtLeast{W, T}, d, cap, T, EpiLevel{level, T, lvl}, IBIP_K_DILATE);
 }
+
+// ------------------------------------------------------------------------
+// ibip_edt_noalloc: the same three EDT passes for callers that may not
+// allocate device memory.  The pass-y intermediate lives in a fixed
+// file-scope device array; the pass-z intermediate (uint16 per voxel) is
+// written into the first half of the caller's dt2 buffer, which pass x then
+// overwrites with the result.
+// ------------------------------------------------------------------------
+
+#include <mutex>
+
+namespace {
+
+constexpr int64_t kNoallocMaxVoxels = 1ll << 21;   // 2,097,152 voxels (e.g. 128^3): 8 MB below
+
+// Shared by every call on a device; held by every GPU that loads the library.
+static __device__ __align__(256) int32_t g_noalloc_g2[kNoallocMaxVoxels];
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+int32_t *g_noalloc_ptr[kNoallocMaxDevices];   // device address of g_noalloc_g2, per device
+
+}  // namespace
+
+extern "C" int ibip_edt_noalloc(const uint8_t *image, ibip_dims d, int32_t *dt2, void *cuda_stream)
+{
+    if (!image || !dt2 || d.nx < 1 || d.ny < 1 || d.nz < 1 || d.nx > 16384 || d.ny > 16384 || d.nz > 16384)
+        return IBIP_ERR_ARG;
+    const int64_t N = nvox(d);
+    if (N > kNoallocMaxVoxels) return IBIP_ERR_TOO_LARGE;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) {
+        cudaGetLastError();
+        return IBIP_ERR_CUDA;
+    }
+    int32_t *g2 = nullptr;
+    {
+        // one-time set-up per device, with that device current: the host-side
+        // name of the array is not a device address, so ask the runtime for it
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_g2) != cudaSuccess || !p) {
+                cudaGetLastError();
+                return IBIP_ERR_CUDA;
+            }
+            g_noalloc_ptr[dev] = (int32_t *)p;
+        }
+        g2 = g_noalloc_ptr[dev];
+    }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    uint16_t *d1 = (uint16_t *)dt2;   // 2 bytes per voxel inside the 4-byte output
+    const int nrows = d.nx * d.ny;
+    k_edt_z<FeatSolid><<<(nrows + kZWarps - 1) / kZWarps, kZWarps * 32, 0, s>>>(FeatSolid{image}, nrows, d.nz, 0xfffe, d1);
+    dim3 gy((d.nz + kStripW - 1) / kStripW, d.nx);
+    const size_t sy = (size_t)d.ny * kStripW * sizeof(uint16_t);
+    if (sy <= kSmemBudget) {
+        cudaFuncSetAttribute(k_edt_y<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget);
+        k_edt_y<true><<<gy, kStripWarps * 32, sy, s>>>(d1, d.ny, d.nz, IBIP_INF32, g2);
+    } else {
+        k_edt_y<false><<<gy, kStripWarps * 32, 0, s>>>(d1, d.ny, d.nz, IBIP_INF32, g2);
+    }
+    dim3 gx((d.nz + kStripW - 1) / kStripW, d.ny);
+    const size_t sx = (size_t)d.nx * kStripW * sizeof(int32_t);
+    if (sx <= kSmemBudget) {
+        cudaFuncSetAttribute(k_edt_x<true, EpiStore>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget);
+        k_edt_x<true, EpiStore><<<gx, kStripWarps * 32, sx, s>>>(g2, d.nx, d.ny, d.nz, IBIP_INF32, EpiStore{dt2});
+    } else {
+        k_edt_x<false, EpiStore><<<gx, kStripWarps * 32, 0, s>>>(g2, d.nx, d.ny, d.nz, IBIP_INF32, EpiStore{dt2});
+    }
+    return ibip_cuda_status(cudaGetLastError());
+}

@@ -1,0 +1,71 @@
+"""ibip_edt_noalloc: the EDT entry point for callers that must not allocate
+device memory while they run (their memory belongs to a pool or arena, or
+cudaMalloc's implicit synchronisation is unaffordable).  Called through the
+C ABI with ctypes; its output must equal ibip_edt's exactly (integer EDT, the
+tolerance every EDT test here uses) on two calls in a row, whose shared fixed
+scratch keeps the previous call's contents.  Named to be collected last."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from paper_2101_03240_gb300 import synth as S
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+IBIP_ERR_TOO_LARGE = -8
+MAX_VOXELS = 1 << 21
+
+
+class Dims(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32)]
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2101_03240_gb300 import build_lib
+    L = C.CDLL(build_lib.LIB)
+    L.ibip_edt_noalloc.restype = C.c_int
+    L.ibip_edt_noalloc.argtypes = [C.c_void_p, Dims, C.c_void_p, C.c_void_p]
+    return L
+
+
+def noalloc_edt(L, img_dev):
+    out = torch.full(img_dev.shape, -7, dtype=torch.int32, device=img_dev.device)
+    stream = torch.cuda.current_stream()
+    st = L.ibip_edt_noalloc(C.c_void_p(img_dev.data_ptr()), Dims(*img_dev.shape), C.c_void_p(out.data_ptr()),
+                            C.c_void_p(stream.cuda_stream))
+    torch.cuda.synchronize()
+    return st, out
+
+
+def test_noalloc_matches_edt_on_two_calls(lib):
+    from paper_2101_03240_gb300 import ibip
+    torch.cuda.set_device(0)
+    ctx = ibip.Context(0)
+    rng = np.random.default_rng(2024)
+    # the largest accepted size first, then a smaller ragged one: the second
+    # call runs on scratch still holding the first call's values
+    images = [S.blobs((128, 128, 128), 3.0, 0.6, rng), S.sphere_pack((37, 61, 29), 5, 0.45, rng)]
+    for img in images:
+        d = torch.from_numpy(img).cuda()
+        st, got = noalloc_edt(lib, d)
+        assert st == 0
+        want = ctx.edt(d)
+        torch.cuda.synchronize()
+        assert torch.equal(got, want)
+
+
+def test_noalloc_rejects_oversize(lib):
+    small = torch.ones((2, 2, 2), dtype=torch.uint8, device="cuda")
+    out = torch.zeros((2, 2, 2), dtype=torch.int32, device="cuda")
+    st = lib.ibip_edt_noalloc(C.c_void_p(small.data_ptr()), Dims(129, 128, 128), C.c_void_p(out.data_ptr()), None)
+    assert st == IBIP_ERR_TOO_LARGE
+    assert 129 * 128 * 128 > MAX_VOXELS
+    torch.cuda.synchronize()
+    assert not out.any()   # nothing was queued
