@@ -140,7 +140,7 @@ def run_ours(args, rank, world):
     def step(image):
         d = ctx.edt(image, out=dt2)
         s, rr, cc, K, st = ctx.invade(image, d, inlet=w.inlet, seq=seq, step_r2=r2, step_centre=cen)
-        tr, so = ctx.trapping(s, w.outlet)
+        so = ctx.trapping(s, w.outlet)[1] if w.outlet is not None else s
         S, P, _ = ctx.pc_curve(so, rr, w.voxel_m, w.sigma, w.theta_deg)
         lev, cnt = ctx.morph_drainage(image, d, levels, inlet=w.inlet)
         return K, so, S, P
@@ -251,7 +251,7 @@ def run_ours(args, rank, world):
         "dtype": "int32",
         "data": "synthetic",
         "config": {"workload": w.name, "shape": list(img_h.shape), "porosity": float(npore / N),
-                   "inlet": "x0", "outlet": "x1", "mio_levels": len(levels),
+                   "inlet": "x0", "outlet": "x1" if w.outlet is not None else None, "mio_levels": len(levels),
                    "l2": "flushed between steps (256 MB write)", "parallelism": "replicas%d" % world},
         "invasion_steps": K,
         "invasion_steps_per_s": K / (prof["invade"][0] / args.steps * 1e-3) if prof["invade"][1] else None,
@@ -276,7 +276,7 @@ def oracle_pass(w, levels):
     import oracle as O
     d = O.edt(w.image)
     seq, r2, cen, st, K = O.invade(w.image, d, inlet=w.inlet)
-    tr, so = O.trapping(seq, w.outlet)
+    so = O.trapping(seq, w.outlet)[1] if w.outlet is not None else seq
     O.pc_curve(so, r2, w.voxel_m, w.sigma, w.theta_deg)
     O.morph_drainage(w.image, d, levels, inlet=w.inlet)
     return K

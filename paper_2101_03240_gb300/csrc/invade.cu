@@ -261,6 +261,7 @@ struct Batch {
     int m, mcap, J, stop, mtarget, tstop;
     int cur1;          // no level-1 summary word below this index is set
     int nA, nC, nD;    // work-list fill counts (shell candidates, removals, additions)
+    int ovf;           // the shell-candidate list overflowed this iteration
     int64_t kk;        // step count handed back by the single-voxel loop
 };
 
@@ -336,6 +337,39 @@ __device__ __forceinline__ int unit_item(const int *pre, int n, int u)
         if (pre[mid] <= u) lo = mid; else hi = mid;
     }
     return lo;
+}
+
+
+// Thread tid's contiguous share of the row units [0, U) of items [0, n):
+// f(u, i, x, y) for each unit u, i its item (pre = prefix sums of the items'
+// unit counts) and (x, y) its row in the item's square (origin sx0/sy0,
+// width swy).  Consecutive units of one item advance (x, y) without a
+// division; f returns false to stop early.
+template <class F>
+__device__ __forceinline__ void for_units(const int *pre, int n, int U, const int *sx0, const int *sy0,
+                                          const int *swy, int tid, F f)
+{
+    const int C = (U + kNT - 1) / kNT;
+    int u = tid * C;
+    const int u1 = min(U, u + C);
+    if (u >= u1) return;
+    int i = unit_item(pre, n + 1, u);
+    int t = u - pre[i];
+    int w = swy[i], y0 = sy0[i];
+    int x = sx0[i] + t / w, y = y0 + t % w;
+    int nxt = pre[i + 1];
+    for (; u < u1; u++) {
+        while (u >= nxt) {
+            i++;
+            nxt = pre[i + 1];
+            w = swy[i];
+            y0 = sy0[i];
+            x = sx0[i];
+            y = y0;
+        }
+        if (!f(u, i, x, y)) return;
+        if (++y >= y0 + w) { y = y0; x++; }
+    }
 }
 
 // position of the k-th (0-based) set bit of a 32-bit word: binary search on
@@ -640,6 +674,7 @@ __global__ void __launch_bounds__(kNT, 1) k_invade(Inv a, FastDiv fd_nyz, FastDi
     __shared__ Batch B;
     __shared__ int sLA[kList];
     __shared__ unsigned char sLAi[kList];
+    __shared__ int sLAr[kList];
     __shared__ int sLC[kList];
     __shared__ int sLD[kList];
     u64 *s1 = L1SMEM ? s_fb : a.fb1;
@@ -746,6 +781,8 @@ __global__ void __launch_bounds__(kNT, 1) k_invade(Inv a, FastDiv fd_nyz, FastDi
                 u64 cj = __shfl_sync(0xffffffffu, j < 32 ? cont[0] : cont[1], j & 31);
                 if (!(cj & keep)) keep |= 1ull << j;
             }
+            const long long tc2 = clock64();
+            if (tid == 0) c_sub[4] += tc2 - tc;
             // step limit: items past the (max_steps - k)-th kept one are dropped
             int mcap = m;
             int64_t remain = a.max_steps - k;
@@ -778,6 +815,7 @@ __global__ void __launch_bounds__(kNT, 1) k_invade(Inv a, FastDiv fd_nyz, FastDi
                 cut = ((ob0 >> l) & 1) ? 2 * l : 2 * l + 1;
             }
             mcap = min(mcap, cut);
+            if (tid == 0) c_sub[5] += clock64() - tc2;
             __syncwarp();
             if (j0 < m) {
                 B.step[j0] = ((keep >> j0) & 1) ? __popcll(keep & ((1ull << j0) - 1)) : -1;
@@ -799,7 +837,7 @@ __global__ void __launch_bounds__(kNT, 1) k_invade(Inv a, FastDiv fd_nyz, FastDi
                 B.J = mcap;
                 B.keep = keep;
                 B.stop = mcap == 0 ? 2 : 0;
-                B.nA = 0; B.nC = 0; B.nD = 0;
+                B.nA = 0; B.nC = 0; B.nD = 0; B.ovf = 0;
                 c_sub[3] += clock64() - tc;
             }
         }
@@ -819,32 +857,31 @@ __global__ void __launch_bounds__(kNT, 1) k_invade(Inv a, FastDiv fd_nyz, FastDi
         // max(i + 1, #items ranked above u).
         {
             const int U = B.dpre[mcap];
-            for (int u = tid; u < U; u += kNT) {
-                // units are ordered by item: past the rows of items below the
-                // current J nothing can lower it any more
-                if (u >= B.dpre[*(volatile int *)&B.J]) break;
-                int i = unit_item(B.dpre, mcap + 1, u);
-                if (i + 1 >= *(volatile int *)&B.J) continue;   // cannot lower J
+            for_units(B.dpre, mcap, U, B.dx0, B.dy0, B.dwy, tid, [&](int u, int i, int x, int y) -> bool {
+                // units are ordered by item; items at or past the current J will
+                // not be committed (the list also feeds the commit, so every
+                // item below J is enumerated in full)
+                if (i >= *(volatile int *)&B.J) return false;
                 if (B.r2[i] == 1) {
                     // single-voxel ball: its shell is its six neighbours
                     Nb6 nb;
                     nb6(a, B.x[i], B.y[i], B.z[i], B.idx[i], nb);
-                    unsigned c = nb6_candidates(a, nb);
-                    if (c) {
-                        int ru[6];
-#pragma unroll
-                        for (int q = 0; q < 6; q++) ru[q] = ((c >> q) & 1) ? __ldg(a.rank + nb.v[q]) : INT_MAX;
-                        int best = INT_MAX;
-#pragma unroll
-                        for (int q = 0; q < 6; q++) best = min(best, ru[q]);
-                        atomicMin(&B.J, max(i + 1, lower_rank(B, m, best)));
+                    for (unsigned c = nb6_candidates(a, nb); c; c &= c - 1) {
+                        const int q = __ffs(c) - 1;
+                        const int slot = atomicAdd(&B.nA, 1);
+                        if (slot < kList) {
+                            sLA[slot] = nb.v[q];
+                            sLAi[slot] = (unsigned char)i;
+                        } else {
+                            B.ovf = 1;
+                            const int ru = __ldg(a.rank + nb.v[q]);
+                            atomicMin(&B.J, max(i + 1, lower_rank(B, m, ru)));
+                        }
                     }
-                    continue;
+                    return true;
                 }
-                const int t = u - B.dpre[i];
-                const int x = B.dx0[i] + t / B.dwy[i], y = B.dy0[i] + t % B.dwy[i];
                 int za, zb, ra, rbz;
-                if (!shell_row(a, B, i, x, y, za, zb, ra, rbz)) continue;
+                if (!shell_row(a, B, i, x, y, za, zb, ra, rbz)) return true;
                 const int64_t row = (int64_t)x * a.ny + y;
                 for (int w = za >> 5; w <= (zb >> 5); w++) {
                     uint32_t cand = ldcg32(a.avail + row * a.NW + w) & ~ldcg32(a.added + row * a.NW + w) &
@@ -856,19 +893,22 @@ __global__ void __launch_bounds__(kNT, 1) k_invade(Inv a, FastDiv fd_nyz, FastDi
                             sLA[slot] = (int)(row * a.nz + z);
                             sLAi[slot] = (unsigned char)i;
                         } else {
+                            B.ovf = 1;
                             const int ru = __ldg(a.rank + row * a.nz + z);
                             atomicMin(&B.J, max(i + 1, lower_rank(B, m, ru)));
                         }
                     }
                 }
-            }
+                return true;
+            });
             __syncthreads();
             const int n = min(B.nA, kList);
             for (int e = tid; e < n; e += kNT) {
-                int i = sLAi[e];
-                if (i + 1 >= *(volatile int *)&B.J) continue;
-                int ru = __ldg(a.rank + sLA[e]);
-                atomicMin(&B.J, max(i + 1, lower_rank(B, m, ru)));
+                const int i = sLAi[e];
+                if (i >= *(volatile int *)&B.J) continue;   // never committed
+                const int ru = __ldg(a.rank + sLA[e]);
+                sLAr[e] = ru;
+                if (i + 1 < *(volatile int *)&B.J) atomicMin(&B.J, max(i + 1, lower_rank(B, m, ru)));
             }
         }
         __syncthreads();
@@ -887,23 +927,20 @@ __global__ void __launch_bounds__(kNT, 1) k_invade(Inv a, FastDiv fd_nyz, FastDi
         {
             const int64_t k1 = k + 1;
             const int U = B.upre[J];
-            for (int u = tid; u < U; u += kNT) {
-                int i = unit_item(B.upre, J + 1, u);
+            for_units(B.upre, J, U, B.bx0, B.by0, B.wy, tid, [&](int u, int i, int x, int y) -> bool {
                 if (B.r2[i] == 1) {
                     // a kept single-voxel item is a queued candidate that no
                     // lower ball covers: it owns its voxel and its rank is known
-                    const int x = B.x[i], y = B.y[i], z = B.z[i];
-                    const int64_t w = ((int64_t)x * a.ny + y) * a.NW + (z >> 5);
+                    const int z = B.z[i];
+                    const int64_t w = ((int64_t)B.x[i] * a.ny + B.y[i]) * a.NW + (z >> 5);
                     atomicAnd(a.avail + w, ~(1u << (z & 31)));
                     a.seq[B.idx[i]] = (int32_t)(k1 + B.step[i]);
                     const int r = B.rank[i];
                     atomicAnd(a.fb0 + (r >> 6), ~(1ull << (r & 63)));
-                    continue;
+                    return true;
                 }
-                int t = u - B.upre[i];
-                int x = B.bx0[i] + t / B.wy[i], y = B.by0[i] + t % B.wy[i];
                 int lo, hi;
-                if (!ball_run(B, i, x, y, lo, hi)) continue;
+                if (!ball_run(B, i, x, y, lo, hi)) return true;
                 const int z0 = max(lo, 0), z1 = min(hi, a.nz - 1);
                 const int64_t rb = ((int64_t)x * a.ny + y) * a.NW;
                 const int64_t vb = ((int64_t)x * a.ny + y) * a.nz;
@@ -927,7 +964,8 @@ __global__ void __launch_bounds__(kNT, 1) k_invade(Inv a, FastDiv fd_nyz, FastDi
                         if (slot < kList) sLC[slot] = v; else gC[slot - kList] = v;
                     }
                 }
-            }
+                return true;
+            });
             for (int j = tid; j < J; j += kNT) {
                 if (B.step[j] < 0) continue;
                 int64_t s = k + B.step[j];
@@ -938,12 +976,37 @@ __global__ void __launch_bounds__(kNT, 1) k_invade(Inv a, FastDiv fd_nyz, FastDi
             }
         }
         __syncthreads();
+        if (!B.ovf) {
+            // Stage 2 from the candidate list of the bound pass (complete for
+            // every committed item, ranks already loaded): a listed voxel
+            // that is still uninvaded after the stamping lies outside every
+            // committed ball; queue it once.  Apply the removals too.
+            const int n = min(B.nA, kList), nC = B.nC;
+            for (int e = tid; e < n + nC; e += kNT) {
+                if (e < n) {
+                    if (sLAi[e] >= J) continue;
+                    const uint32_t v = (uint32_t)sLA[e];
+                    const uint32_t row = fdiv(v, fd_nz), z = v - row * (uint32_t)a.nz;
+                    const int64_t w = (int64_t)row * a.NW + (z >> 5);
+                    const uint32_t bit = 1u << (z & 31);
+                    if (!(ldcg32(a.avail + w) & bit)) continue;
+                    if (atomicOr(a.added + w, bit) & bit) continue;
+                    const int r = sLAr[e];
+                    atomicOr(a.fb0 + (r >> 6), 1ull << (r & 63));
+                    flag_rank(s1, s2, s3, &B.cur1, r);
+                } else {
+                    const int f = e - n;
+                    const int v = f < kList ? sLC[f] : gC[f - kList];
+                    const int r = __ldg(a.rank + v);
+                    atomicAnd(a.fb0 + (r >> 6), ~(1ull << (r & 63)));
+                }
+            }
+        } else {
         // Stage 2: with every committed ball stamped, a shell voxel that is
         // still uninvaded and never queued lies outside all of them: queue it.
         {
             const int U = B.dpre[J];
-            for (int u = tid; u < U; u += kNT) {
-                const int i = unit_item(B.dpre, J + 1, u);
+            for_units(B.dpre, J, U, B.dx0, B.dy0, B.dwy, tid, [&](int u, int i, int x, int y) -> bool {
                 if (B.r2[i] == 1) {
                     Nb6 nb;
                     nb6(a, B.x[i], B.y[i], B.z[i], B.idx[i], nb);
@@ -963,12 +1026,10 @@ __global__ void __launch_bounds__(kNT, 1) k_invade(Inv a, FastDiv fd_nyz, FastDi
                         atomicOr(a.fb0 + (r >> 6), 1ull << (r & 63));
                         flag_rank(s1, s2, s3, &B.cur1, r);
                     }
-                    continue;
+                    return true;
                 }
-                const int t = u - B.dpre[i];
-                const int x = B.dx0[i] + t / B.dwy[i], y = B.dy0[i] + t % B.dwy[i];
                 int za, zb, ra, rbz;
-                if (!shell_row(a, B, i, x, y, za, zb, ra, rbz)) continue;
+                if (!shell_row(a, B, i, x, y, za, zb, ra, rbz)) return true;
                 const int64_t row = (int64_t)x * a.ny + y;
                 for (int w = za >> 5; w <= (zb >> 5); w++) {
                     const uint32_t cand = ldcg32(a.avail + row * a.NW + w) & ~ldcg32(a.added + row * a.NW + w) &
@@ -981,7 +1042,8 @@ __global__ void __launch_bounds__(kNT, 1) k_invade(Inv a, FastDiv fd_nyz, FastDi
                         if (slot < kList) sLD[slot] = v; else gD[slot - kList] = v;
                     }
                 }
-            }
+                return true;
+            });
         }
         __syncthreads();
         // Stage 3: apply removals and additions to the rank bitmap.
@@ -1000,6 +1062,7 @@ __global__ void __launch_bounds__(kNT, 1) k_invade(Inv a, FastDiv fd_nyz, FastDi
                     flag_rank(s1, s2, s3, &B.cur1, r);
                 }
             }
+        }
         }
         k += __popcll(B.keep & jmask);
         iters++;
@@ -1034,6 +1097,8 @@ __global__ void __launch_bounds__(kNT, 1) k_invade(Inv a, FastDiv fd_nyz, FastDi
         a.out[11] = n_small;
         for (int q = 0; q < 4; q++) a.out[12 + q] = c_sub[q];
         for (int q = 0; q < 3; q++) a.out[16 + q] = c_small_ph[q];
+        a.out[22] = c_sub[4];
+        a.out[23] = c_sub[5];
         a.out[19] = n_tiny;
         a.out[20] = n_tiny_steps;
         a.out[21] = c_tiny;
