@@ -10,18 +10,26 @@
 // started from M = val on F.  Trapping thresholds it against seq (a voxel of
 // step k is trapped iff M < k); opening keeps {M >= T}.
 //
-// GPU: tiles of 4 x 8 x 32 voxels (z contiguous) relax in shared memory until
-// they stop changing; a tile that changed wakes its six neighbours for the
-// next round; rounds repeat until no tile is awake.
+// GPU: one persistent cooperative grid.  The image is cut into 4 x 8 x 32
+// tiles (z contiguous); a block loads a tile with a one-voxel halo into
+// shared memory and relaxes it until it stops changing.  A tile that changed
+// puts its six neighbours on the next round's work list; rounds are separated
+// by a grid-wide barrier and end when a list is empty (or at the round cap).
+// Everything other blocks write (the field, the lists, the counters) is read
+// with L2-coherent loads: the SM's L1 may hold a line from an earlier round.
+#include <cooperative_groups.h>
+
 #include "common.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace {
 
 constexpr int TX = 4, TY = 8, TZ = 32;
-constexpr int HX = TX + 2, HY = TY + 2, HZ = TZ + 2;
 constexpr int kThreads = 256;
-constexpr int kPer = TX * TY * TZ / kThreads;
-constexpr int kInner = 96;
+constexpr int kPer = TX * TY * TZ / kThreads;   // voxels per thread
+constexpr int kInner = 96;                      // relaxation sweeps per activation
+constexpr int kMaxRoundsDev = 1 << 16;
 
 __device__ __forceinline__ int as_val(int v) { return v == -1 ? IBIP_INF32 : v; }
 
@@ -37,64 +45,125 @@ __global__ void k_mm_init(const int32_t *__restrict__ val, int nx, int ny, int n
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_mm_round(const int32_t *__restrict__ val, int nx, int ny, int nz,
-                                                      int tx, int ty, int tz, int32_t *M, int *act, int round,
-                                                      int *last)
+// tiles touching the face start the first round's list
+__global__ void k_mm_seed(int tx, int ty, int tz, int face, int *list, int *count, int *mark)
 {
-    __shared__ int32_t sM[HX][HY][HZ];
-    const int t = blockIdx.x;
-    if (act[t] != round) return;
-    const int bz = t % tz, by = (t / tz) % ty, bx = t / (tz * ty);
-    const int x0 = bx * TX, y0 = by * TY, z0 = bz * TZ;
-    // load tile + halo
-    for (int i = threadIdx.x; i < HX * HY * HZ; i += kThreads) {
-        int hz = i % HZ, hy = (i / HZ) % HY, hx = i / (HZ * HY);
-        int x = x0 + hx - 1, y = y0 + hy - 1, z = z0 + hz - 1;
-        int m = -1;
-        if (x >= 0 && y >= 0 && z >= 0 && x < nx && y < ny && z < nz) m = M[d_lin(x, y, z, ny, nz)];
-        sM[hx][hy][hz] = m;
-    }
-    int sval[kPer];
-    int lx[kPer], ly[kPer], lz[kPer];
-#pragma unroll
-    for (int k = 0; k < kPer; k++) {
-        int i = threadIdx.x + k * kThreads;
-        lz[k] = i % TZ; ly[k] = (i / TZ) % TY; lx[k] = i / (TZ * TY);
-        int x = x0 + lx[k], y = y0 + ly[k], z = z0 + lz[k];
-        sval[k] = (x < nx && y < ny && z < nz) ? as_val(val[d_lin(x, y, z, ny, nz)]) : 0;
-    }
-    __syncthreads();
-    bool any = false, conv = false;
-    for (int it = 0; it < kInner; it++) {
-        int ch = 0;
-#pragma unroll
-        for (int k = 0; k < kPer; k++) {
-            if (sval[k] == 0) continue;
-            int hx = lx[k] + 1, hy = ly[k] + 1, hz = lz[k] + 1;
-            int b = max(max(max(sM[hx - 1][hy][hz], sM[hx + 1][hy][hz]), max(sM[hx][hy - 1][hz], sM[hx][hy + 1][hz])),
-                        max(sM[hx][hy][hz - 1], sM[hx][hy][hz + 1]));
-            int nv = min(b, sval[k]);
-            if (nv > sM[hx][hy][hz]) { sM[hx][hy][hz] = nv; ch = 1; }
+    const int nt = tx * ty * tz;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+        const int bz = t % tz, by = (t / tz) % ty, bx = t / (tz * ty);
+        bool on = false;
+        switch (face) {
+        case 0: on = bx == 0; break;
+        case 1: on = bx == tx - 1; break;
+        case 2: on = by == 0; break;
+        case 3: on = by == ty - 1; break;
+        case 4: on = bz == 0; break;
+        default: on = bz == tz - 1; break;
         }
-        if (!__syncthreads_or(ch)) { conv = true; break; }
-        any = true;
+        if (on) {
+            mark[t] = 0;
+            list[atomicAdd(count, 1)] = t;
+        }
     }
-    if (!any) return;
+}
+
+struct MMArgs {
+    const int32_t *val;
+    int32_t *M;
+    int nx, ny, nz, tx, ty, tz;
+    int *list0, *list1;   // work lists, alternating by round
+    int *count, *head;    // per-round list sizes and take counters [max_rounds + 2]
+    int *mark;            // per tile: last round it was queued for
+    int *status;          // [0] rounds run, [1] 1 if the round cap was hit
+    int max_rounds;
+};
+
+__global__ void __launch_bounds__(kThreads) k_mm_persistent(MMArgs a)
+{
+    cg::grid_group grid = cg::this_grid();
+    __shared__ int32_t sM[TX + 2][TY + 2][TZ + 2];
+    __shared__ int s_tile;
+    int r = 0;
+    for (;; r++) {
+        const int cnt = *(volatile int *)&a.count[r];
+        if (cnt == 0 || r >= a.max_rounds) break;
+        const int *list = (r & 1) ? a.list1 : a.list0;
+        int *next = (r & 1) ? a.list0 : a.list1;
+        for (;;) {
+            if (threadIdx.x == 0) {
+                const int q = atomicAdd(&a.head[r], 1);
+                s_tile = q < cnt ? __ldcg(list + q) : -1;
+            }
+            __syncthreads();
+            const int t = s_tile;
+            if (t < 0) break;
+            const int bz = t % a.tz, by = (t / a.tz) % a.ty, bx = t / (a.tz * a.ty);
+            const int x0 = bx * TX, y0 = by * TY, z0 = bz * TZ;
+            // tile + one-voxel halo of the field
+            for (int i = threadIdx.x; i < (TX + 2) * (TY + 2) * (TZ + 2); i += kThreads) {
+                const int hz = i % (TZ + 2), hy = (i / (TZ + 2)) % (TY + 2), hx = i / ((TZ + 2) * (TY + 2));
+                const int x = x0 + hx - 1, y = y0 + hy - 1, z = z0 + hz - 1;
+                int m = -1;
+                if (x >= 0 && y >= 0 && z >= 0 && x < a.nx && y < a.ny && z < a.nz) m = __ldcg(a.M + d_lin(x, y, z, a.ny, a.nz));
+                sM[hx][hy][hz] = m;
+            }
+            int sval[kPer], lx[kPer], ly[kPer], lz[kPer];
 #pragma unroll
-    for (int k = 0; k < kPer; k++) {
-        int x = x0 + lx[k], y = y0 + ly[k], z = z0 + lz[k];
-        if (x < nx && y < ny && z < nz && sval[k] != 0) M[d_lin(x, y, z, ny, nz)] = sM[lx[k] + 1][ly[k] + 1][lz[k] + 1];
+            for (int k = 0; k < kPer; k++) {
+                const int i = threadIdx.x + k * kThreads;
+                lz[k] = i % TZ; ly[k] = (i / TZ) % TY; lx[k] = i / (TZ * TY);
+                const int x = x0 + lx[k], y = y0 + ly[k], z = z0 + lz[k];
+                sval[k] = (x < a.nx && y < a.ny && z < a.nz) ? as_val(a.val[d_lin(x, y, z, a.ny, a.nz)]) : 0;
+            }
+            __syncthreads();
+            bool any = false, conv = false;
+            for (int it = 0; it < kInner; it++) {
+                int ch = 0;
+#pragma unroll
+                for (int k = 0; k < kPer; k++) {
+                    if (sval[k] == 0) continue;
+                    const int hx = lx[k] + 1, hy = ly[k] + 1, hz = lz[k] + 1;
+                    const int b = max(max(max(sM[hx - 1][hy][hz], sM[hx + 1][hy][hz]), max(sM[hx][hy - 1][hz], sM[hx][hy + 1][hz])),
+                                      max(sM[hx][hy][hz - 1], sM[hx][hy][hz + 1]));
+                    const int nv = min(b, sval[k]);
+                    if (nv > sM[hx][hy][hz]) { sM[hx][hy][hz] = nv; ch = 1; }
+                }
+                if (!__syncthreads_or(ch)) { conv = true; break; }
+                any = true;
+            }
+            // the first round's tiles hold the seeds: they always wake their
+            // neighbours (a tile that is only the face layer does not change)
+            if (any || r == 0) {
+#pragma unroll
+                for (int k = 0; k < kPer; k++) {
+                    const int x = x0 + lx[k], y = y0 + ly[k], z = z0 + lz[k];
+                    if (x < a.nx && y < a.ny && z < a.nz && sval[k] != 0)
+                        a.M[d_lin(x, y, z, a.ny, a.nz)] = sM[lx[k] + 1][ly[k] + 1][lz[k] + 1];
+                }
+                if (threadIdx.x == 0) {
+                    const int nr = r + 1;
+                    int nb[7] = {-1, -1, -1, -1, -1, -1, -1};
+                    if (bx > 0) nb[0] = t - a.tz * a.ty;
+                    if (bx < a.tx - 1) nb[1] = t + a.tz * a.ty;
+                    if (by > 0) nb[2] = t - a.tz;
+                    if (by < a.ty - 1) nb[3] = t + a.tz;
+                    if (bz > 0) nb[4] = t - 1;
+                    if (bz < a.tz - 1) nb[5] = t + 1;
+                    if (!conv) nb[6] = t;
+                    for (int q = 0; q < 7; q++) {
+                        if (nb[q] < 0) continue;
+                        if (atomicMax(&a.mark[nb[q]], nr) < nr) next[atomicAdd(&a.count[nr], 1)] = nb[q];
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        __threadfence();
+        grid.sync();
     }
-    if (threadIdx.x == 0) {
-        const int nxt = round + 1;
-        if (bx > 0) act[t - tz * ty] = nxt;
-        if (bx < tx - 1) act[t + tz * ty] = nxt;
-        if (by > 0) act[t - tz] = nxt;
-        if (by < ty - 1) act[t + tz] = nxt;
-        if (bz > 0) act[t - 1] = nxt;
-        if (bz < tz - 1) act[t + 1] = nxt;
-        if (!conv) act[t] = nxt;
-        atomicMax(last, nxt);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.status[0] = r;
+        a.status[1] = (r >= a.max_rounds && __ldcg(a.count + r) != 0) ? 1 : 0;
     }
 }
 
@@ -105,30 +174,40 @@ int ibip_maximin_launch(ibip_ctx *ctx, const int32_t *val, ibip_dims d, int face
     cudaStream_t s = ctx->stream;
     const int tx = (d.nx + TX - 1) / TX, ty = (d.ny + TY - 1) / TY, tz = (d.nz + TZ - 1) / TZ;
     const int nt = tx * ty * tz;
-    int *act = (int *)ibip_scratch(ctx, SC_TILE, (size_t)nt * sizeof(int));
-    int *small = (int *)ibip_scratch(ctx, SC_SMALL, kSmallBytes);
-    if (!act || !small) return IBIP_ERR_OOM;
-    int *last = small + 4;
+    const int rounds = max_rounds < kMaxRoundsDev ? max_rounds : kMaxRoundsDev;
+    // layout: list0[nt] list1[nt] mark[nt] count[rounds+2] head[rounds+2] status[4]
+    const size_t ints = (size_t)3 * nt + 2 * ((size_t)rounds + 2) + 4;
+    int *w = (int *)ibip_scratch(ctx, SC_TILE, ints * sizeof(int));
+    if (!w) return IBIP_ERR_OOM;
+    MMArgs a;
+    a.val = val; a.M = M;
+    a.nx = d.nx; a.ny = d.ny; a.nz = d.nz; a.tx = tx; a.ty = ty; a.tz = tz;
+    a.list0 = w; a.list1 = w + nt; a.mark = w + 2 * nt;
+    a.count = w + 3 * nt; a.head = a.count + rounds + 2; a.status = a.head + rounds + 2;
+    a.max_rounds = rounds;
     ibip_prof_begin(ctx, IBIP_K_MAXIMIN);
-    cudaMemsetAsync(act, 0, (size_t)nt * sizeof(int), s);
-    cudaMemsetAsync(last, 0, sizeof(int), s);
+    cudaMemsetAsync(a.mark, 0xff, (size_t)nt * sizeof(int), s);   // -1: never queued
+    cudaMemsetAsync(a.count, 0, (2 * ((size_t)rounds + 2) + 4) * sizeof(int), s);
     k_mm_init<<<ctx->sm_count * 8, 256, 0, s>>>(val, d.nx, d.ny, d.nz, face, M);
     IBIP_LAUNCH(ctx);
-    int *h = (int *)ctx->h_pinned;
-    const int kBatch = 8;
-    for (int r = 0; r < max_rounds; r += kBatch) {
-        for (int q = r; q < r + kBatch; q++) {
-            k_mm_round<<<nt, kThreads, 0, s>>>(val, d.nx, d.ny, d.nz, tx, ty, tz, M, act, q, last);
-            IBIP_LAUNCH(ctx);
-        }
-        cudaMemcpyAsync(h, last, sizeof(int), cudaMemcpyDeviceToHost, s);
-        cudaError_t e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) return ibip_cuda_status(e);
-        if (h[0] < r + kBatch) {   // no tile woken for the next round
-            ibip_prof_end(ctx, IBIP_K_MAXIMIN);
-            return IBIP_OK;
-        }
+    k_mm_seed<<<(nt + 255) / 256, 256, 0, s>>>(tx, ty, tz, face, a.list0, a.count, a.mark);
+    IBIP_LAUNCH(ctx);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mm_persistent, kThreads, 0) != cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        return IBIP_ERR_CUDA;
     }
+    int grid = ctx->sm_count * per_sm;
+    if (grid > nt) grid = nt;
+    void *args[] = {&a};
+    cudaError_t e = cudaLaunchCooperativeKernel((void *)k_mm_persistent, grid, kThreads, args, 0, s);
+    IBIP_LAUNCH(ctx);
+    if (e != cudaSuccess) return ibip_cuda_status(e);
+    int *h = (int *)ctx->h_pinned;
+    cudaMemcpyAsync(h, a.status, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
+    e = cudaStreamSynchronize(s);
     ibip_prof_end(ctx, IBIP_K_MAXIMIN);
-    return IBIP_ERR_NOT_CONVERGED;
+    if (e != cudaSuccess) return ibip_cuda_status(e);
+    return h[1] ? IBIP_ERR_NOT_CONVERGED : IBIP_OK;
 }
