@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--config", choices=["spheres200", "blobs48"], default="spheres200")
+    ap.add_argument("--config", choices=["spheres200", "blobs48", "blobs512"], default="spheres200")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mio-levels", type=int, default=40)
     return ap.parse_args()
@@ -53,7 +53,8 @@ def parse():
 
 def workload(name):
     from paper_2101_03240_gb300 import synth
-    return synth.c2_spheres200() if name == "spheres200" else synth.c1_blobs48()
+    return {"spheres200": synth.c2_spheres200, "blobs48": synth.c1_blobs48,
+            "blobs512": synth.c3_blobs512}[name]()
 
 
 def peaks():

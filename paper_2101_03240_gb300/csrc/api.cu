@@ -286,9 +286,28 @@ int ibip_morph_drainage(ibip_ctx *ctx, const uint8_t *image, const int32_t *dt2,
     if (n_levels == 0) return ibip_cuda_status(cudaStreamSynchronize(ctx->stream));
     st = ibip_maximin_launch(ctx, dt2, dims, inlet, W, kMaxRounds);
     if (st) return st;
-    for (int i = 0; i < n_levels; i++) {
-        st = ibip_dilate_level_launch(ctx, W, h_r2_levels[i], i + 1, dims, level);
+    // radii above the largest widest-path value trim to the empty set: skip
+    int wmax = 0;
+    st = ibip_max_launch(ctx, W, nvox(dims), &wmax);
+    if (st) return st;
+    int first = 0;
+    while (first < n_levels && h_r2_levels[first] > wmax) first++;
+    if (n_levels <= 254) {
+        uint8_t *fl = (uint8_t *)ibip_scratch(ctx, SC_FL, (size_t)nvox(dims) + 256 * sizeof(int32_t) + 256);
+        if (!fl) return IBIP_ERR_OOM;
+        int32_t *T_dev = (int32_t *)(fl + (((size_t)nvox(dims) + 255) & ~(size_t)255));
+        cudaMemcpyAsync(T_dev, h_r2_levels, (size_t)n_levels * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream);
+        st = ibip_first_level_launch(ctx, W, dims, T_dev, n_levels, fl);
         if (st) return st;
+        for (int i = first; i < n_levels; i++) {
+            st = ibip_dilate_first_level_launch(ctx, fl, h_r2_levels[i], i, dims, level);
+            if (st) return st;
+        }
+    } else {
+        for (int i = first; i < n_levels; i++) {
+            st = ibip_dilate_level_launch(ctx, W, h_r2_levels[i], i + 1, dims, level);
+            if (st) return st;
+        }
     }
     return ibip_level_counts(ctx, level, dims, n_levels, h_counts);
 }

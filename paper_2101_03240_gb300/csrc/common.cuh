@@ -26,6 +26,7 @@ enum ScratchSlot {
     SC_HIST,      // int32 histogram
     SC_SMALL,     // small device scalars
     SC_LIST,      // int32 overflow work lists of the invasion kernel
+    SC_FL,        // uint8 first opening level per voxel, and the level radii
     SC_NSLOTS
 };
 
@@ -67,6 +68,12 @@ int ibip_edt_launch(ibip_ctx *ctx, const uint8_t *image, ibip_dims d, int32_t *d
 // and the squared distance to the feature set is < T.
 int ibip_dilate_level_launch(ibip_ctx *ctx, const int32_t *W, int32_t T, int32_t lvl, ibip_dims d,
                              int32_t *level);
+// MIO with a per-voxel first level (uint8, L <= 254): fl[v] = first i with
+// W[v] >= T[i]; then level i's trimmed set is {fl <= i}.
+int ibip_first_level_launch(ibip_ctx *ctx, const int32_t *W, ibip_dims d, const int32_t *T_dev, int L, uint8_t *fl);
+int ibip_dilate_first_level_launch(ibip_ctx *ctx, const uint8_t *fl, int32_t T, int32_t i, ibip_dims d,
+                                   int32_t *level);
+int ibip_max_launch(ibip_ctx *ctx, const int32_t *a, int64_t n, int *h_max);
 // Maximin propagation from a face through voxels with val != 0 (val == -1
 // counts as +inf).  Writes M (-1 where unreachable).
 int ibip_maximin_launch(ibip_ctx *ctx, const int32_t *val, ibip_dims d, int face, int32_t *M,

@@ -31,6 +31,28 @@ struct FeatAtLeast {
     int32_t t;
     __device__ bool operator()(int64_t v) const { return __ldg(w + v) >= t; }
 };
+// opening: voxel v belongs to the trimmed set of level i iff its first level
+// (the first radius index whose T it reaches) is <= i
+struct FeatFirstLevel {
+    const uint8_t *fl;
+    int i;
+    __device__ bool operator()(int64_t v) const { return __ldg(fl + v) <= i; }
+};
+
+// first level of every voxel: the smallest i with W >= T[i] (255 if none)
+__global__ void k_first_level(const int32_t *__restrict__ W, int64_t N, const int32_t *__restrict__ T, int L,
+                              uint8_t *fl)
+{
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (int64_t)gridDim.x * blockDim.x) {
+        const int w = W[v];
+        int lo = 0, hi = L;   // T is strictly decreasing: first index with T <= w
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (__ldg(T + mid) <= w) hi = mid; else lo = mid + 1;
+        }
+        fl[v] = (uint8_t)(lo < L ? lo : 255);
+    }
+}
 
 template <class Feat>
 __global__ void __launch_bounds__(kZWarps * 32) k_edt_z(Feat feat, int nrows, int nz, int cap,
@@ -45,12 +67,23 @@ __global__ void __launch_bounds__(kZWarps * 32) k_edt_z(Feat feat, int nrows, in
     const int nch = (nz + 31) >> 5;
     const int NONE = 1 << 29;
     int carry = -NONE;
-    for (int c = 0; c < nch; c++) {
-        int z = (c << 5) + lane;
-        bool f = z < nz && feat(base + z);
-        uint32_t m = __ballot_sync(0xffffffffu, f);
-        if (lane == 0) { s_mask[w][c] = m; s_left[w][c] = carry; }
-        if (m) carry = (c << 5) + 31 - __clz(m);
+    // feature tests of eight chunks are issued before their ballots so the
+    // loads overlap
+    for (int c0 = 0; c0 < nch; c0 += 8) {
+        bool f[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const int z = ((c0 + q) << 5) + lane;
+            f[q] = c0 + q < nch && z < nz && feat(base + z);
+        }
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const int c = c0 + q;
+            if (c >= nch) break;
+            const uint32_t m = __ballot_sync(0xffffffffu, f[q]);
+            if (lane == 0) { s_mask[w][c] = m; s_left[w][c] = carry; }
+            if (m) carry = (c << 5) + 31 - __clz(m);
+        }
     }
     __syncwarp();
     int right = NONE;
@@ -104,7 +137,8 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_edt_y(const uint16_t *__re
     const bool ok = z < nz;
     const int64_t b = (int64_t)x * ny * nz + z;
     if (SMEM) {
-        for (int y = w; y < ny; y += kStripWarps) s_col[y * kStripW + lane] = ok ? d1[b + (int64_t)y * nz] : 0xffff;
+#pragma unroll 8
+        for (int y = w; y < ny; y += kStripWarps) s_col[y * kStripW + lane] = ok ? __ldg(d1 + b + (int64_t)y * nz) : 0xffff;
         __syncthreads();
     }
     if (!ok) return;
@@ -141,7 +175,8 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_edt_x(const int32_t *__res
     const int64_t st = (int64_t)ny * nz;
     const int64_t b = (int64_t)y * nz + z;
     if (SMEM) {
-        for (int x = w; x < nx; x += kStripWarps) s_colx[x * kStripW + lane] = ok ? g2[b + x * st] : IBIP_INF32;
+#pragma unroll 8
+        for (int x = w; x < nx; x += kStripWarps) s_colx[x * kStripW + lane] = ok ? __ldg(g2 + b + x * st) : IBIP_INF32;
         __syncthreads();
     }
     if (!ok) return;
@@ -190,6 +225,20 @@ int edt_passes(ibip_ctx *ctx, Feat feat, ibip_dims d, int cap, int cap2, Epi epi
 int ibip_edt_launch(ibip_ctx *ctx, const uint8_t *image, ibip_dims d, int32_t *dt2)
 {
     return edt_passes(ctx, FeatSolid{image}, d, 0xfffe, IBIP_INF32, EpiStore{dt2}, IBIP_K_EDT);
+}
+
+int ibip_first_level_launch(ibip_ctx *ctx, const int32_t *W, ibip_dims d, const int32_t *T_dev, int L, uint8_t *fl)
+{
+    k_first_level<<<ctx->sm_count * 8, 256, 0, ctx->stream>>>(W, nvox(d), T_dev, L, fl);
+    IBIP_LAUNCH(ctx);
+    return ibip_cuda_status(cudaGetLastError());
+}
+
+int ibip_dilate_first_level_launch(ibip_ctx *ctx, const uint8_t *fl, int32_t T, int32_t i, ibip_dims d, int32_t *level)
+{
+    int cap = 0;
+    while ((int64_t)(cap + 1) * (cap + 1) < T && cap < 0xfffe) cap++;
+    return edt_passes(ctx, FeatFirstLevel{fl, i}, d, cap, T, EpiLevel{level, T, i + 1}, IBIP_K_DILATE);
 }
 
 int ibip_dilate_level_launch(ibip_ctx *ctx, const int32_t *W, int32_t T, int32_t lvl, ibip_dims d,

@@ -164,6 +164,22 @@ int ibip_trap_finish(ibip_ctx *ctx, const int32_t *seq, const int32_t *M, ibip_d
     return ibip_cuda_status(cudaGetLastError());
 }
 
+int ibip_max_launch(ibip_ctx *ctx, const int32_t *a, int64_t n, int *h_max)
+{
+    int *small = (int *)ibip_scratch(ctx, SC_SMALL, kSmallBytes);
+    if (!small) return IBIP_ERR_OOM;
+    int *mx = small + 13;
+    cudaStream_t s = ctx->stream;
+    cudaMemsetAsync(mx, 0x80, sizeof(int), s);   // INT_MIN-ish start
+    k_max_seq<<<ctx->sm_count * 8, 256, 0, s>>>(a, n, mx);
+    IBIP_LAUNCH(ctx);
+    cudaMemcpyAsync(ctx->h_pinned, mx, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return ibip_cuda_status(e);
+    *h_max = *(int *)ctx->h_pinned;
+    return IBIP_OK;
+}
+
 int ibip_level_init(ibip_ctx *ctx, const uint8_t *img, ibip_dims d, int32_t *level)
 {
     k_level_init<<<ctx->sm_count * 8, 256, 0, ctx->stream>>>(img, nvox(d), level);
