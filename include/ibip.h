@@ -186,6 +186,41 @@ IBIP_API int ibip_pc_curve(ibip_ctx *ctx, const int32_t *seq, ibip_dims dims, co
                   int64_t n_steps, double voxel_m, double sigma, double theta_deg,
                   float *sat_per_step, float *pc_per_step, float *sat_image);
 
+/* One image of a batched call.  Device pointers unless stated; the caller
+ * owns every buffer.  Outputs are those of ibip_edt, ibip_invade,
+ * ibip_trapping and ibip_pc_curve for this image. */
+typedef struct {
+    const uint8_t *image;     /* uint8[N] pore image */
+    ibip_dims dims;
+    int32_t inlet;            /* ibip_face */
+    int32_t outlet;           /* ibip_face for trapping, or -1 for none */
+    int32_t *dt2;             /* int32[N] output, or NULL (kept in scratch) */
+    int32_t *seq;             /* int32[N] output */
+    int32_t *step_r2;         /* int32[capacity_steps] output */
+    int32_t *step_centre;     /* int32[capacity_steps] output, or NULL */
+    int64_t capacity_steps;   /* >= number of pore voxels is always enough */
+    uint8_t *trapped;         /* uint8[N] output, or NULL: no trapping */
+    int32_t *seq_out;         /* int32[N] output (trapped voxels -1), or NULL */
+    float *sat_per_step;      /* float[capacity_steps] output, or NULL: no curve */
+    float *pc_per_step;       /* float[capacity_steps] output, or NULL */
+    double voxel_m, sigma, theta_deg;   /* Pc parameters (Section 2.2.2) */
+    int64_t n_steps;          /* filled: steps K of this image */
+    int32_t status;           /* filled: this image's status */
+} ibip_job;
+
+/* The whole path for n images of any sizes in one call: EDT, invasion
+ * (Section 2.1), trapping (Section 2.2.3) when `trapped` is given, and the
+ * saturation / Pc curve (Sections 2.2.1-2.2.2; computed from seq_out when
+ * trapping ran, else from seq) when `sat_per_step` is given.  The
+ * invasions of all images run in one launch, one persistent CTA per image,
+ * largest first; results equal the per-image calls bit for bit.
+ *   h_jobs: host array of n jobs (1 <= n <= 4096); n_steps and status are
+ *           written back.  An image's pore count must stay below 2^25.
+ * Synchronous.  Returns IBIP_OK when every job succeeded, else the first
+ * failing job's status (IBIP_ERR_ARG with n_steps = K when K exceeded
+ * capacity_steps). */
+IBIP_API int ibip_invade_batched(ibip_ctx *ctx, int32_t n, ibip_job *h_jobs);
+
 /* Wait for everything queued on the context's stream; returns the first
  * error seen. */
 IBIP_API int ibip_synchronize(ibip_ctx *ctx);

@@ -312,6 +312,64 @@ int ibip_morph_drainage(ibip_ctx *ctx, const uint8_t *image, const int32_t *dt2,
     return ibip_level_counts(ctx, level, dims, n_levels, h_counts);
 }
 
+int ibip_invade_batched(ibip_ctx *ctx, int32_t n, ibip_job *jobs)
+{
+    if (!ctx || !jobs || n < 1 || n > kMaxBatch) return IBIP_ERR_ARG;
+    int64_t need_dt2 = 0;
+    for (int j = 0; j < n; j++) {
+        const ibip_job &J = jobs[j];
+        if (!J.image || !J.seq || !dims_ok(J.dims) || !face_ok(J.inlet) || J.capacity_steps < 0 ||
+            (J.capacity_steps > 0 && !J.step_r2) || (J.trapped && !face_ok(J.outlet)) ||
+            ((J.sat_per_step != nullptr) != (J.pc_per_step != nullptr)) ||
+            (J.sat_per_step && !(J.voxel_m > 0.0)))
+            return IBIP_ERR_ARG;
+        if (!J.dt2) need_dt2 += (nvox(J.dims) + 63) & ~(int64_t)63;
+    }
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = ctx->stream;
+    int32_t *pool = need_dt2 ? (int32_t *)ibip_scratch(ctx, SC_BDT2, (size_t)need_dt2 * sizeof(int32_t)) : nullptr;
+    if (need_dt2 && !pool) return IBIP_ERR_OOM;
+    std::vector<IbipBatchItem> it(n);
+    int64_t off = 0;
+    for (int j = 0; j < n; j++) {
+        ibip_job &J = jobs[j];
+        int32_t *d = J.dt2;
+        if (!d) { d = pool + off; off += (nvox(J.dims) + 63) & ~(int64_t)63; }
+        int st = ibip_edt_launch(ctx, J.image, J.dims, d);
+        if (st) return st;
+        it[j] = IbipBatchItem{d, J.dims, J.inlet, nvox(J.dims), J.seq, J.step_r2, J.step_centre,
+                              J.capacity_steps, 0, 0};
+    }
+    int st = ibip_invade_batch_run(ctx, n, it.data());
+    if (st) return st;
+    int first_bad = IBIP_OK;
+    for (int j = 0; j < n; j++) {
+        ibip_job &J = jobs[j];
+        J.n_steps = it[j].n_steps;
+        J.status = it[j].status;
+        if (J.status == IBIP_OK && J.n_steps > J.capacity_steps) J.status = IBIP_ERR_ARG;
+        if (J.status != IBIP_OK) { if (first_bad == IBIP_OK) first_bad = J.status; continue; }
+        const int32_t *curve_seq = J.seq;
+        if (J.trapped) {
+            int32_t *M = (int32_t *)ibip_scratch(ctx, SC_MM, (size_t)nvox(J.dims) * sizeof(int32_t));
+            if (!M) return IBIP_ERR_OOM;
+            st = ibip_maximin_launch(ctx, J.seq, J.dims, J.outlet, M, kMaxRounds);
+            if (!st) st = ibip_trap_finish(ctx, J.seq, M, J.dims, 0, J.trapped, J.seq_out);
+            if (st) { J.status = st; if (first_bad == IBIP_OK) first_bad = st; continue; }
+            if (J.seq_out) curve_seq = J.seq_out;
+        }
+        if (J.sat_per_step) {
+            const double pi = 3.14159265358979323846;
+            st = ibip_pc_launch(ctx, curve_seq, J.dims, J.step_r2, J.n_steps, J.voxel_m, J.sigma,
+                                cos(J.theta_deg * pi / 180.0), J.sat_per_step, J.pc_per_step, nullptr);
+            if (st) { J.status = st; if (first_bad == IBIP_OK) first_bad = st; }
+        }
+    }
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return ibip_cuda_status(e);
+    return first_bad;
+}
+
 int ibip_pc_curve(ibip_ctx *ctx, const int32_t *seq, ibip_dims dims, const int32_t *step_r2, int64_t n_steps,
                   double voxel_m, double sigma, double theta_deg, float *sat_per_step, float *pc_per_step,
                   float *sat_image)

@@ -27,6 +27,10 @@ enum ScratchSlot {
     SC_SMALL,     // small device scalars
     SC_LIST,      // int32 overflow work lists of the invasion kernel
     SC_FL,        // uint8 first opening level per voxel, and the level radii
+    SC_BSTAT,     // batched invasion: per-image pore statistics
+    SC_BARENA,    // batched invasion: per-image ranks, bit-planes, bitmaps
+    SC_BJOBS,     // batched invasion: job table
+    SC_BDT2,      // batched invasion: EDTs of images given without one
     SC_NSLOTS
 };
 
@@ -55,6 +59,20 @@ constexpr size_t kSmallBytes = 64 + 64 * sizeof(int64_t);
 void *ibip_scratch(ibip_ctx *ctx, int slot, size_t bytes);
 
 #define IBIP_LAUNCH(ctx) ((ctx)->launches++)
+
+// One image of a batched invasion (internal form of ibip_job).
+struct IbipBatchItem {
+    const int32_t *dt2;
+    ibip_dims d;
+    int inlet;
+    int64_t max_steps;
+    int32_t *seq, *step_r2, *step_centre;
+    int64_t cap;
+    int64_t n_steps;   // out
+    int status;        // out
+};
+constexpr int kMaxBatch = 4096;   // two int64 per image fit the pinned readback buffer
+int ibip_invade_batch_run(ibip_ctx *ctx, int n, IbipBatchItem *items);
 
 // Status helpers.
 int ibip_cuda_status(cudaError_t e);

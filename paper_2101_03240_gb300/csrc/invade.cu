@@ -28,6 +28,7 @@
 //    committed ball covering it), covered candidates leave the bitmap, and
 //    new candidates (outside every committed ball) enter it.
 #include <algorithm>
+#include <vector>
 #include <climits>
 
 #include "common.cuh"
@@ -668,7 +669,8 @@ __device__ void tiny_loop(const Inv &a, Batch &B, u64 *s1, u64 *s2, u64 *s3, con
 }
 
 template <bool L1SMEM>
-__global__ void __launch_bounds__(kNT, 1) k_invade(Inv a, FastDiv fd_nyz, FastDiv fd_nz, int *gC, int *gD)
+__device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz, const FastDiv &fd_nz, int *gC,
+                                            int *gD)
 {
     extern __shared__ u64 s_fb[];
     __shared__ Batch B;
@@ -1105,36 +1107,90 @@ __global__ void __launch_bounds__(kNT, 1) k_invade(Inv a, FastDiv fd_nyz, FastDi
     }
 }
 
+template <bool L1SMEM>
+__global__ void __launch_bounds__(kNT, 1) k_invade(Inv a, FastDiv fd_nyz, FastDiv fd_nz, int *gC, int *gD)
+{
+    invade_body<L1SMEM>(a, fd_nyz, fd_nz, gC, gD);
+}
+
+// One image per CTA: many invasions in one launch (all with level 1 of the
+// rank bitmap in shared memory).
+struct InvJob {
+    Inv a;
+    FastDiv fd_nyz, fd_nz;
+    int *gC, *gD;
+};
+
+__global__ void __launch_bounds__(kNT, 1) k_invade_batch(const InvJob *__restrict__ jobs)
+{
+    const InvJob j = jobs[blockIdx.x];
+    invade_body<true>(j.a, j.fd_nyz, j.fd_nz, j.gC, j.gD);
+}
+
 }  // namespace
 
 // --------------------------------------------------------------- launcher --
 
-int ibip_invade_run(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, int64_t max_steps,
-                    int32_t *seq, int32_t *step_r2, int32_t *step_centre, int64_t cap, int64_t *h_out)
+namespace {
+
+// Device memory one invasion needs beyond its inputs and outputs.
+struct JobMem {
+    int32_t *rank;
+    int2 *okey;
+    uint32_t *avail, *added;
+    u64 *fb;
+    int *gl;
+    int64_t *out;
+};
+
+struct JobSizes {
+    size_t rank, okey, plane, fb, gl, out;
+    size_t total() const { return rank + okey + 2 * plane + fb + gl + out; }
+};
+
+size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+JobSizes job_sizes(ibip_dims d, int npore)
+{
+    JobSizes z;
+    const int64_t N = nvox(d);
+    const int NL0 = (npore + 63) / 64, NL1 = (NL0 + 63) / 64, NL2 = (NL1 + 63) / 64, NL3 = (NL2 + 63) / 64;
+    z.rank = up256((size_t)N * sizeof(int32_t));
+    z.okey = up256((size_t)npore * sizeof(int2));
+    z.plane = up256((size_t)d.nx * d.ny * ((d.nz + 31) / 32) * sizeof(uint32_t));
+    z.fb = up256(((size_t)NL0 + NL1 + NL2 + NL3) * sizeof(u64));
+    z.gl = up256((size_t)2 * npore * sizeof(int) + 64);
+    z.out = up256(kNOut * sizeof(int64_t));
+    return z;
+}
+
+JobMem carve(char *p, const JobSizes &z)
+{
+    JobMem m;
+    m.rank = (int32_t *)p; p += z.rank;
+    m.okey = (int2 *)p; p += z.okey;
+    m.avail = (uint32_t *)p; p += z.plane;
+    m.added = (uint32_t *)p; p += z.plane;
+    m.fb = (u64 *)p; p += z.fb;
+    m.gl = (int *)p; p += z.gl;
+    m.out = (int64_t *)p;
+    return m;
+}
+
+// Rank sort, sequence initialisation and bit-plane / bitmap set-up of one
+// invasion whose pore statistics (largest finite dt2, pore count, whether
+// dt2 is infinite) are known.  Queued on the context stream; synchronises
+// once (the number of distinct dt2 values sizes the counting sort).
+int invade_setup(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, int64_t max_steps, int32_t *seq,
+                 int32_t *step_r2, int32_t *step_centre, int64_t cap, int maxd, int npore, int hasinf,
+                 const JobMem &mem, Inv *out_a)
 {
     cudaStream_t s = ctx->stream;
     const int64_t N = nvox(d);
-    int *stats = (int *)ibip_scratch(ctx, SC_SMALL, kSmallBytes);
-    if (!stats) return IBIP_ERR_OOM;
+    const int gs = ctx->sm_count * 8;
     int *h = (int *)ctx->h_pinned;
-    ibip_prof_begin(ctx, IBIP_K_RANK);
-    cudaMemsetAsync(stats, 0, 3 * sizeof(int), s);
-    int gs = ctx->sm_count * 8;
-    k_stats<<<gs, 256, 0, s>>>(dt2, N, stats);
-    IBIP_LAUNCH(ctx);
-    cudaMemcpyAsync(h, stats, 3 * sizeof(int), cudaMemcpyDeviceToHost, s);
-    if (cudaStreamSynchronize(s) != cudaSuccess) return IBIP_ERR_CUDA;
-    const int maxd = h[0], npore = h[1], hasinf = h[2];
-
     k_seq_init<<<gs, 256, 0, s>>>(dt2, N, seq);
     IBIP_LAUNCH(ctx);
-    if (npore == 0) {
-        ibip_prof_end(ctx, IBIP_K_RANK);
-        for (int i = 0; i < kNOut; i++) h_out[i] = 0;
-        h_out[1] = IBIP_OK;
-        return ibip_cuda_status(cudaStreamSynchronize(s));
-    }
-
     // -- bucket ids by dt2 value
     int32_t *incl = (int32_t *)ibip_scratch(ctx, SC_PRES, ((size_t)maxd + 2) * sizeof(int32_t));
     if (!incl) return IBIP_ERR_OOM;
@@ -1150,28 +1206,24 @@ int ibip_invade_run(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, i
         B = h[0];
     }
     Bucket bk{incl, B, hasinf};
-
     // -- stable counting sort by bucket
     int64_t S = kChunk;
     while ((N + S - 1) / S * (int64_t)B > (1ll << 26)) S *= 2;
     const int C = (int)((N + S - 1) / S);
     int32_t *mat = (int32_t *)ibip_scratch(ctx, SC_MAT, (size_t)C * B * sizeof(int32_t));
-    int32_t *rank = (int32_t *)ibip_scratch(ctx, SC_RANK, (size_t)N * sizeof(int32_t));
-    int2 *okey = (int2 *)ibip_scratch(ctx, SC_OKEY, (size_t)npore * sizeof(int2));
-    if (!mat || !rank || !okey) return IBIP_ERR_OOM;
+    if (!mat) return IBIP_ERR_OOM;
     const bool smem = B <= 1024;
     const int wpb = 4;
-    size_t sm = smem ? (size_t)wpb * B * sizeof(int32_t) : 0;
-    int nb = (C + wpb - 1) / wpb;
+    const size_t sm = smem ? (size_t)wpb * B * sizeof(int32_t) : 0;
+    const int nb = (C + wpb - 1) / wpb;
     if (smem) k_chunk_hist<true><<<nb, wpb * 32, sm, s>>>(dt2, N, (int)S, C, bk, mat);
     else k_chunk_hist<false><<<nb, wpb * 32, 0, s>>>(dt2, N, (int)S, C, bk, mat);
     IBIP_LAUNCH(ctx);
     int st = ibip_scan_excl_i32(ctx, mat, mat, (int64_t)C * B);
     if (st) return st;
-    if (smem) k_chunk_scatter<true><<<nb, wpb * 32, sm, s>>>(dt2, N, (int)S, C, bk, mat, rank, okey);
-    else k_chunk_scatter<false><<<nb, wpb * 32, 0, s>>>(dt2, N, (int)S, C, bk, mat, rank, okey);
+    if (smem) k_chunk_scatter<true><<<nb, wpb * 32, sm, s>>>(dt2, N, (int)S, C, bk, mat, mem.rank, mem.okey);
+    else k_chunk_scatter<false><<<nb, wpb * 32, 0, s>>>(dt2, N, (int)S, C, bk, mat, mem.rank, mem.okey);
     IBIP_LAUNCH(ctx);
-
     // -- bit-planes and the candidate bitmap
     Inv a;
     a.nx = d.nx; a.ny = d.ny; a.nz = d.nz; a.NW = (d.nz + 31) / 32; a.inlet = inlet;
@@ -1182,42 +1234,174 @@ int ibip_invade_run(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, i
     a.max_steps = max_steps;
     a.cap = cap;
     a.npore = npore;
-    a.rank = rank; a.okey = okey; a.dt2 = dt2;
-    const int64_t nw = (int64_t)d.nx * d.ny * a.NW;
-    a.avail = (uint32_t *)ibip_scratch(ctx, SC_AVAIL, nw * sizeof(uint32_t));
-    a.added = (uint32_t *)ibip_scratch(ctx, SC_ADDED, nw * sizeof(uint32_t));
-    size_t nfb = (size_t)a.NL0 + a.NL1 + a.NL2 + a.NL3;
-    u64 *fb = (u64 *)ibip_scratch(ctx, SC_FB, nfb * sizeof(u64));
-    int64_t *out = (int64_t *)ibip_scratch(ctx, SC_SMALL, kSmallBytes);
-    if (!a.avail || !a.added || !fb || !out) return IBIP_ERR_OOM;
-    out += 8;
-    a.fb0 = fb; a.fb1 = fb + a.NL0; a.fb2 = a.fb1 + a.NL1; a.fb3 = a.fb2 + a.NL2;
-    a.seq = seq; a.step_r2 = step_r2; a.step_centre = step_centre; a.out = out;
-    cudaMemsetAsync(fb, 0, nfb * sizeof(u64), s);
+    a.rank = mem.rank; a.okey = mem.okey; a.dt2 = dt2;
+    a.avail = mem.avail; a.added = mem.added;
+    const size_t nfb = (size_t)a.NL0 + a.NL1 + a.NL2 + a.NL3;
+    a.fb0 = mem.fb; a.fb1 = mem.fb + a.NL0; a.fb2 = a.fb1 + a.NL1; a.fb3 = a.fb2 + a.NL2;
+    a.seq = seq; a.step_r2 = step_r2; a.step_centre = step_centre; a.out = mem.out;
+    a.isq_n = std::min(maxd + 1, 16384);
+    cudaMemsetAsync(mem.fb, 0, nfb * sizeof(u64), s);
     k_plane_init<<<gs, 256, 0, s>>>(a);
     IBIP_LAUNCH(ctx);
-    ibip_prof_end(ctx, IBIP_K_RANK);
+    *out_a = a;
+    return ibip_cuda_status(cudaGetLastError());
+}
 
-    int *gl = (int *)ibip_scratch(ctx, SC_LIST, (size_t)2 * npore * sizeof(int) + 64);
-    if (!gl) return IBIP_ERR_OOM;
+size_t invade_dyn_smem(const Inv &a, bool l1smem)
+{
+    return ((l1smem ? a.NL1 : 0) + (size_t)a.NL2 + a.NL3) * sizeof(u64) + (size_t)a.isq_n * sizeof(int);
+}
+
+}  // namespace
+
+int ibip_invade_run(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, int64_t max_steps,
+                    int32_t *seq, int32_t *step_r2, int32_t *step_centre, int64_t cap, int64_t *h_out)
+{
+    cudaStream_t s = ctx->stream;
+    const int64_t N = nvox(d);
+    int *stats = (int *)ibip_scratch(ctx, SC_SMALL, kSmallBytes);
+    if (!stats) return IBIP_ERR_OOM;
+    int *h = (int *)ctx->h_pinned;
+    ibip_prof_begin(ctx, IBIP_K_RANK);
+    cudaMemsetAsync(stats, 0, 3 * sizeof(int), s);
+    k_stats<<<ctx->sm_count * 8, 256, 0, s>>>(dt2, N, stats);
+    IBIP_LAUNCH(ctx);
+    cudaMemcpyAsync(h, stats, 3 * sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return IBIP_ERR_CUDA;
+    const int maxd = h[0], npore = h[1], hasinf = h[2];
+    if (npore == 0) {
+        k_seq_init<<<ctx->sm_count * 8, 256, 0, s>>>(dt2, N, seq);
+        IBIP_LAUNCH(ctx);
+        ibip_prof_end(ctx, IBIP_K_RANK);
+        for (int i = 0; i < kNOut; i++) h_out[i] = 0;
+        h_out[1] = IBIP_OK;
+        return ibip_cuda_status(cudaStreamSynchronize(s));
+    }
+    const JobSizes z = job_sizes(d, npore);
+    JobMem mem;
+    mem.rank = (int32_t *)ibip_scratch(ctx, SC_RANK, z.rank);
+    mem.okey = (int2 *)ibip_scratch(ctx, SC_OKEY, z.okey);
+    mem.avail = (uint32_t *)ibip_scratch(ctx, SC_AVAIL, z.plane);
+    mem.added = (uint32_t *)ibip_scratch(ctx, SC_ADDED, z.plane);
+    mem.fb = (u64 *)ibip_scratch(ctx, SC_FB, z.fb);
+    mem.gl = (int *)ibip_scratch(ctx, SC_LIST, z.gl);
+    int64_t *small = (int64_t *)ibip_scratch(ctx, SC_SMALL, kSmallBytes);
+    if (!mem.rank || !mem.okey || !mem.avail || !mem.added || !mem.fb || !mem.gl || !small) return IBIP_ERR_OOM;
+    mem.out = small + 8;
+    Inv a;
+    int st = invade_setup(ctx, dt2, d, inlet, max_steps, seq, step_r2, step_centre, cap, maxd, npore, hasinf, mem, &a);
+    if (st) return st;
+    ibip_prof_end(ctx, IBIP_K_RANK);
     const FastDiv fd_nyz = make_fastdiv((uint32_t)d.ny * (uint32_t)d.nz), fd_nz = make_fastdiv((uint32_t)d.nz);
     const bool l1smem = a.NL1 <= kSmemL1Max;
-    a.isq_n = std::min(maxd + 1, 16384);
-    size_t dyn = ((l1smem ? a.NL1 : 0) + (size_t)a.NL2 + a.NL3) * sizeof(u64) + (size_t)a.isq_n * sizeof(int);
+    const size_t dyn = invade_dyn_smem(a, l1smem);
     ibip_prof_begin(ctx, IBIP_K_INVADE);
     if (l1smem) {
         cudaFuncSetAttribute(k_invade<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn + 1024);
-        k_invade<true><<<1, kNT, dyn, s>>>(a, fd_nyz, fd_nz, gl, gl + npore);
+        k_invade<true><<<1, kNT, dyn, s>>>(a, fd_nyz, fd_nz, mem.gl, mem.gl + npore);
     } else {
         cudaFuncSetAttribute(k_invade<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn + 1024);
-        k_invade<false><<<1, kNT, dyn, s>>>(a, fd_nyz, fd_nz, gl, gl + npore);
+        k_invade<false><<<1, kNT, dyn, s>>>(a, fd_nyz, fd_nz, mem.gl, mem.gl + npore);
     }
     IBIP_LAUNCH(ctx);
     ibip_prof_end(ctx, IBIP_K_INVADE);
     int64_t *ho = (int64_t *)ctx->h_pinned;
-    cudaMemcpyAsync(ho, out, kNOut * sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(ho, mem.out, kNOut * sizeof(int64_t), cudaMemcpyDeviceToHost, s);
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return ibip_cuda_status(e);
     for (int i = 0; i < kNOut; i++) h_out[i] = ho[i];
+    return IBIP_OK;
+}
+
+// ------------------------------------------------------------- batched --
+
+int ibip_invade_batch_run(ibip_ctx *ctx, int n, IbipBatchItem *it)
+{
+    cudaStream_t s = ctx->stream;
+    if (n <= 0) return IBIP_OK;
+    if (n > kMaxBatch) return IBIP_ERR_ARG;
+    int *h = (int *)ctx->h_pinned;
+    // pore statistics of every image, one synchronisation
+    int *st3 = (int *)ibip_scratch(ctx, SC_BSTAT, (size_t)3 * n * sizeof(int));
+    if (!st3) return IBIP_ERR_OOM;
+    ibip_prof_begin(ctx, IBIP_K_RANK);
+    cudaMemsetAsync(st3, 0, (size_t)3 * n * sizeof(int), s);
+    for (int j = 0; j < n; j++) {
+        k_stats<<<ctx->sm_count * 2, 256, 0, s>>>(it[j].dt2, nvox(it[j].d), st3 + 3 * j);
+        IBIP_LAUNCH(ctx);
+    }
+    cudaMemcpyAsync(h, st3, (size_t)3 * n * sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return IBIP_ERR_CUDA;
+    std::vector<int> maxd(n), npore(n), hasinf(n);
+    size_t total = 0;
+    std::vector<JobSizes> z(n);
+    for (int j = 0; j < n; j++) {
+        maxd[j] = h[3 * j]; npore[j] = h[3 * j + 1]; hasinf[j] = h[3 * j + 2];
+        it[j].n_steps = 0;
+        it[j].status = IBIP_OK;
+        if (npore[j] == 0) continue;
+        z[j] = job_sizes(it[j].d, npore[j]);
+        if ((npore[j] + 63) / 64 > (int64_t)kSmemL1Max * 64) return IBIP_ERR_ARG;   // too large for one-CTA batching
+        total += z[j].total();
+    }
+    char *arena = (char *)ibip_scratch(ctx, SC_BARENA, total + 256);
+    if (!arena) return IBIP_ERR_OOM;
+    // per-image set-up, then one launch with the largest images first
+    std::vector<InvJob> jobs;
+    std::vector<int> idx;
+    std::vector<int64_t *> outs(n, nullptr);
+    size_t off = 0, dyn = 0;
+    for (int j = 0; j < n; j++) {
+        if (npore[j] == 0) {
+            k_seq_init<<<ctx->sm_count * 2, 256, 0, s>>>(it[j].dt2, nvox(it[j].d), it[j].seq);
+            IBIP_LAUNCH(ctx);
+            continue;
+        }
+        const JobMem mem = carve(arena + off, z[j]);
+        off += z[j].total();
+        InvJob J;
+        int st = invade_setup(ctx, it[j].dt2, it[j].d, it[j].inlet, it[j].max_steps, it[j].seq, it[j].step_r2,
+                              it[j].step_centre, it[j].cap, maxd[j], npore[j], hasinf[j], mem, &J.a);
+        if (st) return st;
+        J.fd_nyz = make_fastdiv((uint32_t)it[j].d.ny * (uint32_t)it[j].d.nz);
+        J.fd_nz = make_fastdiv((uint32_t)it[j].d.nz);
+        J.gC = mem.gl;
+        J.gD = mem.gl + npore[j];
+        dyn = std::max(dyn, invade_dyn_smem(J.a, true));
+        outs[j] = mem.out;
+        jobs.push_back(J);
+        idx.push_back(j);
+    }
+    ibip_prof_end(ctx, IBIP_K_RANK);
+    const int m = (int)jobs.size();
+    if (m > 0) {
+        std::vector<int> order(m);
+        for (int q = 0; q < m; q++) order[q] = q;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+            return nvox(it[idx[a]].d) > nvox(it[idx[b]].d);
+        });
+        std::vector<InvJob> sorted(m);
+        for (int q = 0; q < m; q++) sorted[q] = jobs[order[q]];
+        InvJob *djobs = (InvJob *)ibip_scratch(ctx, SC_BJOBS, (size_t)m * sizeof(InvJob));
+        if (!djobs) return IBIP_ERR_OOM;
+        cudaMemcpyAsync(djobs, sorted.data(), (size_t)m * sizeof(InvJob), cudaMemcpyHostToDevice, s);
+        ibip_prof_begin(ctx, IBIP_K_INVADE);
+        cudaFuncSetAttribute(k_invade_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn + 1024);
+        k_invade_batch<<<m, kNT, dyn, s>>>(djobs);
+        IBIP_LAUNCH(ctx);
+        ibip_prof_end(ctx, IBIP_K_INVADE);
+        // steps and status of every job
+        int64_t *ho = (int64_t *)ctx->h_pinned;
+        for (int q = 0; q < m; q++) cudaMemcpyAsync(ho + 2 * q, outs[idx[q]], 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return ibip_cuda_status(e);
+        for (int q = 0; q < m; q++) {
+            it[idx[q]].n_steps = ho[2 * q];
+            it[idx[q]].status = (int)ho[2 * q + 1];
+        }
+    } else {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return ibip_cuda_status(e);
+    }
     return IBIP_OK;
 }

@@ -30,6 +30,14 @@ class Dims(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32)]
 
 
+class Job(C.Structure):
+    _fields_ = [("image", C.c_void_p), ("dims", Dims), ("inlet", C.c_int32), ("outlet", C.c_int32),
+                ("dt2", C.c_void_p), ("seq", C.c_void_p), ("step_r2", C.c_void_p), ("step_centre", C.c_void_p),
+                ("capacity_steps", C.c_int64), ("trapped", C.c_void_p), ("seq_out", C.c_void_p),
+                ("sat_per_step", C.c_void_p), ("pc_per_step", C.c_void_p), ("voxel_m", C.c_double),
+                ("sigma", C.c_double), ("theta_deg", C.c_double), ("n_steps", C.c_int64), ("status", C.c_int32)]
+
+
 class IbipError(RuntimeError):
     def __init__(self, fn, status):
         self.status = status
@@ -66,6 +74,7 @@ def _lib():
                 "ibip_launch_count": (i64, [P]),
                 "ibip_status_string": (C.c_char_p, [C.c_int]),
                 "ibip_profile_enable": (C.c_int, [P, C.c_int]),
+                "ibip_invade_batched": (C.c_int, [P, i32, P]),
                 "ibip_invade_stats": (C.c_int, [P, C.POINTER(i64), C.c_int]),
                 "ibip_profile_read": (C.c_int, [P, C.c_int, C.POINTER(dbl), C.POINTER(i64)]),
             }
@@ -214,6 +223,54 @@ class Context:
         if st != OK:
             raise IbipError("ibip_morph_drainage", st)
         return lev, [int(c) for c in cnt[:len(levels)]]
+
+    def invade_batched(self, images, inlets=0, outlets=1, trapping=True, curve=True, voxel_m=5e-6, sigma=0.072,
+                       theta_deg=180.0, check=True):
+        """EDT, invasion, trapping and Pc curve of many images in one call.
+        `images`: list of 3-D CUDA uint8 tensors; `inlets` / `outlets`: a face
+        or a list of faces.  Returns one dict per image with seq, step_r2,
+        step_centre, K, status and (if requested) trapped, seq_out, S, Pc."""
+        n = len(images)
+        inl = inlets if isinstance(inlets, (list, tuple)) else [inlets] * n
+        outl = outlets if isinstance(outlets, (list, tuple)) else [outlets] * n
+        arr = (Job * n)()
+        res = []
+        for j, im in enumerate(images):
+            _need(im, torch.uint8, "image")
+            dev, N = im.device, im.numel()
+            r = {"seq": torch.empty(im.shape, dtype=torch.int32, device=dev),
+                 "step_r2": torch.empty(max(N, 1), dtype=torch.int32, device=dev),
+                 "step_centre": torch.empty(max(N, 1), dtype=torch.int32, device=dev)}
+            if trapping:
+                r["trapped"] = torch.empty(im.shape, dtype=torch.uint8, device=dev)
+                r["seq_out"] = torch.empty(im.shape, dtype=torch.int32, device=dev)
+            if curve:
+                r["S"] = torch.empty(max(N, 1), dtype=torch.float32, device=dev)
+                r["Pc"] = torch.empty(max(N, 1), dtype=torch.float32, device=dev)
+            J = arr[j]
+            J.image = im.data_ptr()
+            J.dims = _dims(im.shape)
+            J.inlet, J.outlet = int(inl[j]), int(outl[j]) if trapping else -1
+            J.dt2 = None
+            J.seq, J.step_r2, J.step_centre = r["seq"].data_ptr(), r["step_r2"].data_ptr(), r["step_centre"].data_ptr()
+            J.capacity_steps = N
+            J.trapped = r["trapped"].data_ptr() if trapping else None
+            J.seq_out = r["seq_out"].data_ptr() if trapping else None
+            J.sat_per_step = r["S"].data_ptr() if curve else None
+            J.pc_per_step = r["Pc"].data_ptr() if curve else None
+            J.voxel_m, J.sigma, J.theta_deg = float(voxel_m), float(sigma), float(theta_deg)
+            res.append(r)
+        self._stream()
+        st = _lib().ibip_invade_batched(self._h, n, arr)
+        if check and st != OK:
+            raise IbipError("ibip_invade_batched", st)
+        for j, r in enumerate(res):
+            K = int(arr[j].n_steps)
+            r["K"], r["status"] = K, int(arr[j].status)
+            for key in ("step_r2", "step_centre", "S", "Pc"):
+                if key in r:
+                    r[key] = r[key][:K]
+        return res
 
     def pc_curve(self, seq, step_r2, voxel_m=5e-6, sigma=0.072, theta_deg=180.0, sat_image=False):
         _need(seq, torch.int32, "seq")
