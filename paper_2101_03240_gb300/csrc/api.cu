@@ -343,21 +343,38 @@ int ibip_invade_batched(ibip_ctx *ctx, int32_t n, ibip_job *jobs)
     int st = ibip_invade_batch_run(ctx, n, it.data());
     if (st) return st;
     int first_bad = IBIP_OK;
+    // trapping: one widest-path propagation over every image that asks for it
+    std::vector<IbipMaximinJob> mj;
+    std::vector<int> mj_of;
+    int64_t mm_total = 0;
     for (int j = 0; j < n; j++) {
         ibip_job &J = jobs[j];
         J.n_steps = it[j].n_steps;
         J.status = it[j].status;
         if (J.status == IBIP_OK && J.n_steps > J.capacity_steps) J.status = IBIP_ERR_ARG;
         if (J.status != IBIP_OK) { if (first_bad == IBIP_OK) first_bad = J.status; continue; }
-        const int32_t *curve_seq = J.seq;
         if (J.trapped) {
-            int32_t *M = (int32_t *)ibip_scratch(ctx, SC_MM, (size_t)nvox(J.dims) * sizeof(int32_t));
-            if (!M) return IBIP_ERR_OOM;
-            st = ibip_maximin_launch(ctx, J.seq, J.dims, J.outlet, M, kMaxRounds);
-            if (!st) st = ibip_trap_finish(ctx, J.seq, M, J.dims, 0, J.trapped, J.seq_out);
-            if (st) { J.status = st; if (first_bad == IBIP_OK) first_bad = st; continue; }
-            if (J.seq_out) curve_seq = J.seq_out;
+            mj.push_back(IbipMaximinJob{J.seq, J.dims, J.outlet, nullptr});
+            mj_of.push_back(j);
+            mm_total += (nvox(J.dims) + 63) & ~(int64_t)63;
         }
+    }
+    if (!mj.empty()) {
+        int32_t *M = (int32_t *)ibip_scratch(ctx, SC_MM, (size_t)mm_total * sizeof(int32_t));
+        if (!M) return IBIP_ERR_OOM;
+        int64_t o = 0;
+        for (auto &m : mj) { m.M = M + o; o += (nvox(m.d) + 63) & ~(int64_t)63; }
+        st = ibip_maximin_multi(ctx, (int)mj.size(), mj.data(), kMaxRounds);
+        for (size_t q = 0; q < mj.size(); q++) {
+            ibip_job &J = jobs[mj_of[q]];
+            int sq = st ? st : ibip_trap_finish(ctx, J.seq, mj[q].M, J.dims, 0, J.trapped, J.seq_out);
+            if (sq) { J.status = sq; if (first_bad == IBIP_OK) first_bad = sq; }
+        }
+    }
+    for (int j = 0; j < n; j++) {
+        ibip_job &J = jobs[j];
+        if (J.status != IBIP_OK) continue;
+        const int32_t *curve_seq = (J.trapped && J.seq_out) ? J.seq_out : J.seq;
         if (J.sat_per_step) {
             const double pi = 3.14159265358979323846;
             st = ibip_pc_launch(ctx, curve_seq, J.dims, J.step_r2, J.n_steps, J.voxel_m, J.sigma,

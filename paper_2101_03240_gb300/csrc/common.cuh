@@ -96,6 +96,14 @@ int ibip_max_launch(ibip_ctx *ctx, const int32_t *a, int64_t n, int *h_max);
 // counts as +inf).  Writes M (-1 where unreachable).
 int ibip_maximin_launch(ibip_ctx *ctx, const int32_t *val, ibip_dims d, int face, int32_t *M,
                         int max_rounds);
+// The same for several images in one cooperative launch.
+struct IbipMaximinJob {
+    const int32_t *val;
+    ibip_dims d;
+    int face;
+    int32_t *M;
+};
+int ibip_maximin_multi(ibip_ctx *ctx, int n, const IbipMaximinJob *jobs, int max_rounds);
 // Scans.
 int ibip_scan_excl_i32(ibip_ctx *ctx, const int32_t *in, int32_t *out, int64_t n);
 int ibip_scan_incl_i32(ibip_ctx *ctx, const int32_t *in, int32_t *out, int64_t n);

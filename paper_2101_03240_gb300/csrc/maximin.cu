@@ -19,6 +19,8 @@
 // with L2-coherent loads: the SM's L1 may hold a line from an earlier round.
 #include <cooperative_groups.h>
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace cg = cooperative_groups;
@@ -45,33 +47,46 @@ __global__ void k_mm_init(const int32_t *__restrict__ val, int nx, int ny, int n
     }
 }
 
-// tiles touching the face start the first round's list
-__global__ void k_mm_seed(int tx, int ty, int tz, int face, int *list, int *count, int *mark)
+// One image of a (possibly batched) propagation; its tiles are numbered
+// tile0 .. tile0 + tx*ty*tz - 1 in the global tile space.
+struct MMJob {
+    const int32_t *val;
+    int32_t *M;
+    int nx, ny, nz, tx, ty, tz, face, tile0;
+};
+
+// tiles touching each image's face start the first round's list
+__global__ void k_mm_seed(const MMJob *__restrict__ jobs, int njobs, int ntot, int *list, int *count, int *mark)
 {
-    const int nt = tx * ty * tz;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
-        const int bz = t % tz, by = (t / tz) % ty, bx = t / (tz * ty);
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ntot; g += gridDim.x * blockDim.x) {
+        int lo = 0, hi = njobs;   // job: largest j with tile0 <= g
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (jobs[mid].tile0 <= g) lo = mid; else hi = mid;
+        }
+        const MMJob &J = jobs[lo];
+        const int t = g - J.tile0;
+        const int bz = t % J.tz, by = (t / J.tz) % J.ty, bx = t / (J.tz * J.ty);
         bool on = false;
-        switch (face) {
+        switch (J.face) {
         case 0: on = bx == 0; break;
-        case 1: on = bx == tx - 1; break;
+        case 1: on = bx == J.tx - 1; break;
         case 2: on = by == 0; break;
-        case 3: on = by == ty - 1; break;
+        case 3: on = by == J.ty - 1; break;
         case 4: on = bz == 0; break;
-        default: on = bz == tz - 1; break;
+        default: on = bz == J.tz - 1; break;
         }
         if (on) {
-            mark[t] = 0;
-            list[atomicAdd(count, 1)] = t;
+            mark[g] = 0;
+            list[atomicAdd(count, 1)] = g;
         }
     }
 }
 
 struct MMArgs {
-    const int32_t *val;
-    int32_t *M;
-    int nx, ny, nz, tx, ty, tz;
-    int *list0, *list1;   // work lists, alternating by round
+    const MMJob *jobs;
+    int njobs;
+    int *list0, *list1;   // work lists of global tile ids, alternating by round
     int *count, *head;    // per-round list sizes and take counters [max_rounds + 2]
     int *mark;            // per tile: last round it was queued for
     int *status;          // [0] rounds run, [1] 1 if the round cap was hit
@@ -95,16 +110,24 @@ __global__ void __launch_bounds__(kThreads) k_mm_persistent(MMArgs a)
                 s_tile = q < cnt ? __ldcg(list + q) : -1;
             }
             __syncthreads();
-            const int t = s_tile;
-            if (t < 0) break;
-            const int bz = t % a.tz, by = (t / a.tz) % a.ty, bx = t / (a.tz * a.ty);
+            const int g = s_tile;
+            if (g < 0) break;
+            int lo = 0, hi = a.njobs;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (__ldg(&a.jobs[mid].tile0) <= g) lo = mid; else hi = mid;
+            }
+            const MMJob J = a.jobs[lo];
+            const int t = g - J.tile0;
+            const int bz = t % J.tz, by = (t / J.tz) % J.ty, bx = t / (J.tz * J.ty);
             const int x0 = bx * TX, y0 = by * TY, z0 = bz * TZ;
             // tile + one-voxel halo of the field
             for (int i = threadIdx.x; i < (TX + 2) * (TY + 2) * (TZ + 2); i += kThreads) {
                 const int hz = i % (TZ + 2), hy = (i / (TZ + 2)) % (TY + 2), hx = i / ((TZ + 2) * (TY + 2));
                 const int x = x0 + hx - 1, y = y0 + hy - 1, z = z0 + hz - 1;
                 int m = -1;
-                if (x >= 0 && y >= 0 && z >= 0 && x < a.nx && y < a.ny && z < a.nz) m = __ldcg(a.M + d_lin(x, y, z, a.ny, a.nz));
+                if (x >= 0 && y >= 0 && z >= 0 && x < J.nx && y < J.ny && z < J.nz)
+                    m = __ldcg(J.M + d_lin(x, y, z, J.ny, J.nz));
                 sM[hx][hy][hz] = m;
             }
             int sval[kPer], lx[kPer], ly[kPer], lz[kPer];
@@ -113,7 +136,7 @@ __global__ void __launch_bounds__(kThreads) k_mm_persistent(MMArgs a)
                 const int i = threadIdx.x + k * kThreads;
                 lz[k] = i % TZ; ly[k] = (i / TZ) % TY; lx[k] = i / (TZ * TY);
                 const int x = x0 + lx[k], y = y0 + ly[k], z = z0 + lz[k];
-                sval[k] = (x < a.nx && y < a.ny && z < a.nz) ? as_val(a.val[d_lin(x, y, z, a.ny, a.nz)]) : 0;
+                sval[k] = (x < J.nx && y < J.ny && z < J.nz) ? as_val(J.val[d_lin(x, y, z, J.ny, J.nz)]) : 0;
             }
             __syncthreads();
             bool any = false, conv = false;
@@ -137,19 +160,19 @@ __global__ void __launch_bounds__(kThreads) k_mm_persistent(MMArgs a)
 #pragma unroll
                 for (int k = 0; k < kPer; k++) {
                     const int x = x0 + lx[k], y = y0 + ly[k], z = z0 + lz[k];
-                    if (x < a.nx && y < a.ny && z < a.nz && sval[k] != 0)
-                        a.M[d_lin(x, y, z, a.ny, a.nz)] = sM[lx[k] + 1][ly[k] + 1][lz[k] + 1];
+                    if (x < J.nx && y < J.ny && z < J.nz && sval[k] != 0)
+                        J.M[d_lin(x, y, z, J.ny, J.nz)] = sM[lx[k] + 1][ly[k] + 1][lz[k] + 1];
                 }
                 if (threadIdx.x == 0) {
                     const int nr = r + 1;
                     int nb[7] = {-1, -1, -1, -1, -1, -1, -1};
-                    if (bx > 0) nb[0] = t - a.tz * a.ty;
-                    if (bx < a.tx - 1) nb[1] = t + a.tz * a.ty;
-                    if (by > 0) nb[2] = t - a.tz;
-                    if (by < a.ty - 1) nb[3] = t + a.tz;
-                    if (bz > 0) nb[4] = t - 1;
-                    if (bz < a.tz - 1) nb[5] = t + 1;
-                    if (!conv) nb[6] = t;
+                    if (bx > 0) nb[0] = g - J.tz * J.ty;
+                    if (bx < J.tx - 1) nb[1] = g + J.tz * J.ty;
+                    if (by > 0) nb[2] = g - J.tz;
+                    if (by < J.ty - 1) nb[3] = g + J.tz;
+                    if (bz > 0) nb[4] = g - 1;
+                    if (bz < J.tz - 1) nb[5] = g + 1;
+                    if (!conv) nb[6] = g;
                     for (int q = 0; q < 7; q++) {
                         if (nb[q] < 0) continue;
                         if (atomicMax(&a.mark[nb[q]], nr) < nr) next[atomicAdd(&a.count[nr], 1)] = nb[q];
@@ -169,28 +192,45 @@ __global__ void __launch_bounds__(kThreads) k_mm_persistent(MMArgs a)
 
 }  // namespace
 
-int ibip_maximin_launch(ibip_ctx *ctx, const int32_t *val, ibip_dims d, int face, int32_t *M, int max_rounds)
+int ibip_maximin_multi(ibip_ctx *ctx, int n, const IbipMaximinJob *jobs, int max_rounds)
 {
     cudaStream_t s = ctx->stream;
-    const int tx = (d.nx + TX - 1) / TX, ty = (d.ny + TY - 1) / TY, tz = (d.nz + TZ - 1) / TZ;
-    const int nt = tx * ty * tz;
+    if (n <= 0) return IBIP_OK;
+    std::vector<MMJob> J(n);
+    int64_t ntot = 0;
+    for (int j = 0; j < n; j++) {
+        const ibip_dims d = jobs[j].d;
+        J[j].val = jobs[j].val; J[j].M = jobs[j].M;
+        J[j].nx = d.nx; J[j].ny = d.ny; J[j].nz = d.nz;
+        J[j].tx = (d.nx + TX - 1) / TX; J[j].ty = (d.ny + TY - 1) / TY; J[j].tz = (d.nz + TZ - 1) / TZ;
+        J[j].face = jobs[j].face;
+        J[j].tile0 = (int)ntot;
+        ntot += (int64_t)J[j].tx * J[j].ty * J[j].tz;
+    }
+    if (ntot >= (1ll << 30)) return IBIP_ERR_ARG;
+    const int nt = (int)ntot;
     const int rounds = max_rounds < kMaxRoundsDev ? max_rounds : kMaxRoundsDev;
-    // layout: list0[nt] list1[nt] mark[nt] count[rounds+2] head[rounds+2] status[4]
+    // layout: jobs | list0[nt] list1[nt] mark[nt] count[rounds+2] head[rounds+2] status[4]
+    const size_t jb = ((size_t)n * sizeof(MMJob) + 255) & ~(size_t)255;
     const size_t ints = (size_t)3 * nt + 2 * ((size_t)rounds + 2) + 4;
-    int *w = (int *)ibip_scratch(ctx, SC_TILE, ints * sizeof(int));
-    if (!w) return IBIP_ERR_OOM;
+    char *w0 = (char *)ibip_scratch(ctx, SC_TILE, jb + ints * sizeof(int));
+    if (!w0) return IBIP_ERR_OOM;
+    MMJob *djobs = (MMJob *)w0;
+    int *w = (int *)(w0 + jb);
     MMArgs a;
-    a.val = val; a.M = M;
-    a.nx = d.nx; a.ny = d.ny; a.nz = d.nz; a.tx = tx; a.ty = ty; a.tz = tz;
+    a.jobs = djobs; a.njobs = n;
     a.list0 = w; a.list1 = w + nt; a.mark = w + 2 * nt;
     a.count = w + 3 * nt; a.head = a.count + rounds + 2; a.status = a.head + rounds + 2;
     a.max_rounds = rounds;
     ibip_prof_begin(ctx, IBIP_K_MAXIMIN);
+    cudaMemcpyAsync(djobs, J.data(), (size_t)n * sizeof(MMJob), cudaMemcpyHostToDevice, s);
     cudaMemsetAsync(a.mark, 0xff, (size_t)nt * sizeof(int), s);   // -1: never queued
     cudaMemsetAsync(a.count, 0, (2 * ((size_t)rounds + 2) + 4) * sizeof(int), s);
-    k_mm_init<<<ctx->sm_count * 8, 256, 0, s>>>(val, d.nx, d.ny, d.nz, face, M);
-    IBIP_LAUNCH(ctx);
-    k_mm_seed<<<(nt + 255) / 256, 256, 0, s>>>(tx, ty, tz, face, a.list0, a.count, a.mark);
+    for (int j = 0; j < n; j++) {
+        k_mm_init<<<ctx->sm_count * 4, 256, 0, s>>>(J[j].val, J[j].nx, J[j].ny, J[j].nz, J[j].face, J[j].M);
+        IBIP_LAUNCH(ctx);
+    }
+    k_mm_seed<<<(nt + 255) / 256, 256, 0, s>>>(djobs, n, nt, a.list0, a.count, a.mark);
     IBIP_LAUNCH(ctx);
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mm_persistent, kThreads, 0) != cudaSuccess ||
@@ -210,4 +250,10 @@ int ibip_maximin_launch(ibip_ctx *ctx, const int32_t *val, ibip_dims d, int face
     ibip_prof_end(ctx, IBIP_K_MAXIMIN);
     if (e != cudaSuccess) return ibip_cuda_status(e);
     return h[1] ? IBIP_ERR_NOT_CONVERGED : IBIP_OK;
+}
+
+int ibip_maximin_launch(ibip_ctx *ctx, const int32_t *val, ibip_dims d, int face, int32_t *M, int max_rounds)
+{
+    IbipMaximinJob j{val, d, face, M};
+    return ibip_maximin_multi(ctx, 1, &j, max_rounds);
 }
