@@ -45,7 +45,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--config", choices=["spheres200", "blobs48", "blobs512", "batch256"], default="spheres200")
+    ap.add_argument("--config", choices=["spheres200", "blobs48", "blobs512", "batch256", "serve"],
+                    default="spheres200")
+    ap.add_argument("--requests", type=int, default=64, help="serve: requests in the Poisson stream")
+    ap.add_argument("--budget-gb", type=float, default=4.0, help="serve: device arena of the server")
+    ap.add_argument("--slots", type=int, default=16, help="serve: worker slots")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mio-levels", type=int, default=40)
     return ap.parse_args()
@@ -233,6 +237,149 @@ def run_batch(args, rank, world):
         t = time.perf_counter() - t0
         out["cpu_baseline"] = {"value": len(sample) / t, "unit": "images/s", "cores": os.cpu_count(),
                                "kind": "oracle", "sample": "the first 16 images of the batch, whole path each"}
+    return out
+
+
+# -------------------------------------------------------------- serve ----
+
+def _request_image(j):
+    from paper_2101_03240_gb300 import synth
+    return synth.mixed_image(j, 5000, 64, 384)
+
+
+def serve_images(n):
+    """The request stream's images (image j is mixed_image(j) of the
+    64^3..384^3 stream), generated by a spawn pool before any GPU call."""
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(min(n, os.cpu_count() or 1)) as pool:
+        return pool.map(_request_image, range(n))
+
+
+def run_serve(args, rank, world):
+    """Poisson request stream (20 requests/s, 64^3..384^3, half blobs, half
+    sphere packs), each request EDT + invasion + trapping + Pc, through the
+    continuous-batching server: p50/p99 latency at the offered load, and
+    images/s with every request queued at once."""
+    import numpy as np
+    from paper_2101_03240_gb300 import synth
+    reqs = synth.c5_requests(n=args.requests)
+    imgs_h = serve_images(len(reqs))
+    import torch
+    import torch.distributed as dist
+
+    from paper_2101_03240_gb300 import ibip
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    nvox_total = sum(a.size for a in imgs_h)
+    imgs = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in imgs_h]
+    ctx = ibip.Context(local)
+    budget = int(args.budget_gb * (1 << 30))
+    srv = ibip.Server(ctx, budget, max_slots=args.slots)
+    torch.cuda.synchronize()
+
+    def saturated(which):
+        ts = [srv.submit(imgs[j], inlet=0, outlet=1) for j in which]
+        return [srv.wait(t) for t in ts]
+
+    for _ in range(max(1, args.warmup)):
+        saturated(range(min(8, len(imgs))))
+    if world > 1:
+        dist.barrier()
+    clocks = Clocks(local) if rank == 0 else None
+    # capacity: every request queued at once
+    l0 = srv.stats()["launches"]
+    pass_s = []
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = saturated(range(len(imgs)))
+        torch.cuda.synchronize()
+        pass_s.append(time.perf_counter() - t0)
+    st_sat = srv.stats()
+    launches = (st_sat["launches"] - l0) // max(args.steps, 1)
+    # offered load: requests submitted at their Poisson arrival times
+    t0 = time.monotonic()
+    tick = []
+    for j, (ta, L, kind) in enumerate(reqs):
+        d = t0 + ta - time.monotonic()
+        if d > 0:
+            time.sleep(d)
+        tick.append(srv.submit(imgs[j], inlet=0, outlet=1))
+    lat = [srv.wait(t) for t in tick]
+    ck = clocks.stop() if clocks else None
+    st_off = srv.stats()
+    lat_ms = np.array([(r["t_end_ns"] - r["t_submit_ns"]) * 1e-6 for r in lat])
+    span_s = (max(r["t_end_ns"] for r in lat) - min(r["t_submit_ns"] for r in lat)) * 1e-9
+    Ks = [r["K"] for r in res]
+    assert all(r["status"] == 0 for r in res + lat) and Ks == [r["K"] for r in lat]
+    # end to end: host images in (pinned H2D), seq_out back to host
+    pins = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in imgs_h]
+    outs = [torch.empty(a.shape, dtype=torch.int32).pin_memory() for a in imgs_h]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ts = []
+    for d, p_ in zip(imgs, pins):
+        d.copy_(p_, non_blocking=True)
+        ts.append(srv.submit(d, inlet=0, outlet=1))
+    for o, t in zip(outs, ts):
+        o.copy_(srv.wait(t)["seq_out"])
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    srv.close()
+    # the plain one-image-per-call path on the same requests
+    t0 = time.perf_counter()
+    for j, im in enumerate(imgs):
+        dd = ctx.edt(im)
+        s_, r2, cen, K, st = ctx.invade(im, dd, inlet=0)
+        tr, so = ctx.trapping(s_, 1)
+        ctx.pc_curve(so, r2)
+        assert K == Ks[j]
+    torch.cuda.synchronize()
+    single_s = time.perf_counter() - t0
+    sat_s = sum(pass_s) / len(pass_s)
+    if world > 1:
+        t = torch.tensor([sat_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        sat_s = float(t.item())
+    if rank != 0:
+        return None
+    n = len(imgs)
+    out = {
+        "metric": "served images/s and p50/p99 latency (EDT+rank+invasion+trapping+Pc per request, bit-exact)",
+        "value": world * n / sat_s, "unit": "images/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": sat_s * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": "serve", "requests": n, "rate_per_s": 20.0, "voxels": int(nvox_total),
+                   "edge": "64..384 log-uniform", "mix": "half blobs, half sphere packs",
+                   "budget_bytes": budget, "slots": args.slots,
+                   "l2": "inputs larger than L2 (whole stream resident)", "parallelism": "replicas%d" % world,
+                   "timing": "host clock around device-synchronised passes (jobs span many streams)"},
+        "latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99)),
+                       "max": float(lat_ms.max()), "offered_images_per_s": n / reqs[-1][0],
+                       "achieved_images_per_s": n / span_s},
+        "server": {"saturated": st_sat, "offered": st_off},
+        "per_image_path_images_per_s": n / single_s,
+        "served_over_per_image": (n / sat_s) / (n / single_s),
+        "invasion_steps": int(sum(Ks)),
+        "e2e": {"value": world * n / e2e_s, "unit": "images/s", "h2d_bytes_per_step": int(nvox_total),
+                "d2h_bytes_per_step": int(4 * nvox_total)},
+        "gpu_launches": int(launches),
+        "clocks": ck,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle as O
+        sample = sorted(imgs_h, key=lambda a: a.size)[:4]
+        t = time.perf_counter()
+        for a in sample:
+            dd = O.edt(a)
+            sq = O.invade(a, dd, inlet=0)
+            so = O.trapping(sq[0], 1)[1]
+            O.pc_curve(so, sq[1])
+        t = time.perf_counter() - t
+        out["cpu_baseline"] = {"value": len(sample) / t, "unit": "images/s", "cores": os.cpu_count(),
+                               "kind": "oracle", "sample": "the 4 smallest request images, whole path each"}
     return out
 
 
@@ -465,7 +612,12 @@ def main():
         if world > 1:
             dist.barrier()
             __graft_entry__.build()
-        out = run_batch(args, rank, world) if args.config == "batch256" else run_ours(args, rank, world)
+        if args.config == "batch256":
+            out = run_batch(args, rank, world)
+        elif args.config == "serve":
+            out = run_serve(args, rank, world)
+        else:
+            out = run_ours(args, rank, world)
         if world > 1:
             dist.destroy_process_group()
     if out is not None:

@@ -221,6 +221,61 @@ typedef struct {
  * capacity_steps). */
 IBIP_API int ibip_invade_batched(ibip_ctx *ctx, int32_t n, ibip_job *h_jobs);
 
+/* ---- serving: a continuous-batching request loop ----------------------
+ * A server owns one device arena of mem_budget bytes and max_slots worker
+ * slots, each a host thread with its own non-blocking stream.  Submitted
+ * jobs wait in arrival order; the job at the head is admitted as soon as a
+ * slot is idle and a contiguous piece of the arena large enough for its
+ * scratch (ibip_job_footprint) is free.  An admitted job runs the same path
+ * as ibip_invade_batched does for one image (EDT, invasion, trapping when
+ * `trapped` is given, the curve when `sat_per_step` is given), on its
+ * slot's stream, so the jobs in flight overlap on the device; its results
+ * equal those of the one-image calls bit for bit.  Its scratch stays
+ * resident in the arena until it completes, then the piece is returned. */
+typedef struct ibip_server ibip_server;
+
+typedef struct {
+    int32_t status;          /* the job's ibip_status */
+    int32_t slot;            /* slot that ran it */
+    int64_t n_steps;         /* steps K */
+    int64_t t_submit_ns;     /* host steady-clock times: submitted, */
+    int64_t t_start_ns;      /*   admitted, */
+    int64_t t_end_ns;        /*   results complete on the device */
+    int64_t mem_reserved;    /* arena bytes held while it ran */
+    int64_t mem_used;        /* arena bytes its scratch actually took */
+} ibip_result;
+
+/* Upper bound of the scratch bytes one job of these dimensions takes
+ * (including a dt2 buffer when the job gives none). */
+IBIP_API int64_t ibip_job_footprint(ibip_dims dims, int with_dt2);
+
+/* Creates a server on ctx's device (ctx itself is not used afterwards).
+ * 1 <= max_slots <= 128.  Allocates the arena (IBIP_ERR_OOM if it cannot). */
+IBIP_API int ibip_server_create(ibip_server **out, ibip_ctx *ctx, size_t mem_budget, int max_slots);
+
+/* Waits for every submitted job, stops the slots and frees the arena. */
+IBIP_API int ibip_server_destroy(ibip_server *srv);
+
+/* Queues a job (validated as in ibip_invade_batched; a job whose footprint
+ * exceeds the whole arena is IBIP_ERR_OOM) and returns its ticket.  The
+ * job's buffers must stay valid until it completes.  Thread-safe. */
+IBIP_API int ibip_server_submit(ibip_server *srv, const ibip_job *job, uint64_t *h_ticket);
+
+/* *h_done = 1 and *h_result filled when the job has completed, else 0.
+ * A completed ticket can be polled again until the server is destroyed.
+ * Thread-safe. */
+IBIP_API int ibip_server_poll(ibip_server *srv, uint64_t ticket, int *h_done, ibip_result *h_result);
+
+/* As ibip_server_poll, waiting up to timeout_us microseconds (< 0: no
+ * limit) for the job to complete. */
+IBIP_API int ibip_server_wait(ibip_server *srv, uint64_t ticket, int64_t timeout_us, int *h_done,
+                              ibip_result *h_result);
+
+/* Counters: [submitted, completed, running, waiting, arena bytes in use,
+ * arena bytes, peak jobs running at once, peak arena bytes in use, kernel
+ * launches queued by the slots]; n <= 9. */
+IBIP_API int ibip_server_stats(ibip_server *srv, int64_t *h_stats, int n);
+
 /* Wait for everything queued on the context's stream; returns the first
  * error seen. */
 IBIP_API int ibip_synchronize(ibip_ctx *ctx);

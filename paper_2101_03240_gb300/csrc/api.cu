@@ -103,6 +103,14 @@ void *ibip_scratch(ibip_ctx *ctx, int slot, size_t bytes)
 {
     if (bytes == 0) bytes = 16;
     if (ctx->slot_bytes[slot] >= bytes) return ctx->slot[slot];
+    if (ctx->arena) {
+        const size_t b = (bytes + 255) & ~(size_t)255;
+        if (ctx->arena_used + b > ctx->arena_size) return nullptr;
+        ctx->slot[slot] = ctx->arena + ctx->arena_used;
+        ctx->slot_bytes[slot] = b;
+        ctx->arena_used += b;
+        return ctx->slot[slot];
+    }
     if (ctx->slot[slot]) {
         cudaStreamSynchronize(ctx->stream);
         cudaFree(ctx->slot[slot]);
@@ -118,6 +126,46 @@ void *ibip_scratch(ibip_ctx *ctx, int slot, size_t bytes)
     ctx->slot[slot] = p;
     ctx->slot_bytes[slot] = want;
     return p;
+}
+
+bool ibip_job_valid(const ibip_job &J)
+{
+    return J.image && J.seq && dims_ok(J.dims) && face_ok(J.inlet) && J.capacity_steps >= 0 &&
+           (J.capacity_steps == 0 || J.step_r2) && (!J.trapped || face_ok(J.outlet)) &&
+           ((J.sat_per_step != nullptr) == (J.pc_per_step != nullptr)) && (!J.sat_per_step || J.voxel_m > 0.0);
+}
+
+int ibip_run_job(ibip_ctx *ctx, ibip_job &J)
+{
+    J.n_steps = 0;
+    int32_t *d = J.dt2;
+    if (!d) d = (int32_t *)ibip_scratch(ctx, SC_DT2, (size_t)nvox(J.dims) * sizeof(int32_t));
+    if (!d) return IBIP_ERR_OOM;
+    int st = ibip_edt_launch(ctx, J.image, J.dims, d);
+    if (st) return st;
+    int64_t out[36] = {0};
+    st = ibip_invade_run(ctx, d, J.dims, J.inlet, nvox(J.dims), J.seq, J.step_r2, J.step_centre, J.capacity_steps,
+                         out);
+    if (st) return st;
+    J.n_steps = out[0];
+    if (out[1] != IBIP_OK) return (int)out[1];
+    if (out[0] > J.capacity_steps) return IBIP_ERR_ARG;
+    const int32_t *curve_seq = J.seq;
+    if (J.trapped) {
+        int32_t *M = (int32_t *)ibip_scratch(ctx, SC_MM, (size_t)nvox(J.dims) * sizeof(int32_t));
+        if (!M) return IBIP_ERR_OOM;
+        st = ibip_maximin_launch(ctx, J.seq, J.dims, J.outlet, M, kMaxRounds);
+        if (!st) st = ibip_trap_finish(ctx, J.seq, M, J.dims, 0, J.trapped, J.seq_out);
+        if (st) return st;
+        if (J.seq_out) curve_seq = J.seq_out;
+    }
+    if (J.sat_per_step) {
+        const double pi = 3.14159265358979323846;
+        st = ibip_pc_launch(ctx, curve_seq, J.dims, J.step_r2, J.n_steps, J.voxel_m, J.sigma,
+                            cos(J.theta_deg * pi / 180.0), J.sat_per_step, J.pc_per_step, nullptr);
+        if (st) return st;
+    }
+    return ibip_cuda_status(cudaStreamSynchronize(ctx->stream));
 }
 
 extern "C" {
@@ -154,7 +202,7 @@ int ibip_destroy(ibip_ctx *ctx)
     cudaStreamSynchronize(ctx->stream);
     delete (ProfLog *)ctx->prof;
     for (int i = 0; i < SC_NSLOTS; i++)
-        if (ctx->slot[i]) cudaFree(ctx->slot[i]);
+        if (ctx->slot[i] && !ctx->arena) cudaFree(ctx->slot[i]);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
     delete ctx;
     return IBIP_OK;
@@ -318,11 +366,7 @@ int ibip_invade_batched(ibip_ctx *ctx, int32_t n, ibip_job *jobs)
     int64_t need_dt2 = 0;
     for (int j = 0; j < n; j++) {
         const ibip_job &J = jobs[j];
-        if (!J.image || !J.seq || !dims_ok(J.dims) || !face_ok(J.inlet) || J.capacity_steps < 0 ||
-            (J.capacity_steps > 0 && !J.step_r2) || (J.trapped && !face_ok(J.outlet)) ||
-            ((J.sat_per_step != nullptr) != (J.pc_per_step != nullptr)) ||
-            (J.sat_per_step && !(J.voxel_m > 0.0)))
-            return IBIP_ERR_ARG;
+        if (!ibip_job_valid(J)) return IBIP_ERR_ARG;
         if (!J.dt2) need_dt2 += (nvox(J.dims) + 63) & ~(int64_t)63;
     }
     DeviceGuard g(ctx->device);

@@ -44,6 +44,12 @@ struct ibip_ctx {
     void *h_pinned;   // small pinned host buffer for scalar readback
     void *prof;       // event log when profiling is on (api.cu), else null
     int64_t inv_stats[36];   // counters of the last ibip_invade (ibip_invade_stats)
+    // Arena mode (server slots): scratch is carved from [arena, arena +
+    // arena_size) and never freed; a request that does not fit fails.
+    char *arena;
+    size_t arena_size, arena_used;
+    // Kernels share the device with other streams: no cooperative launches.
+    int no_coop;
 };
 
 // Profiling: CUDA-event pairs around each kernel class, on the context's
@@ -73,6 +79,12 @@ struct IbipBatchItem {
 };
 constexpr int kMaxBatch = 4096;   // two int64 per image fit the pinned readback buffer
 int ibip_invade_batch_run(ibip_ctx *ctx, int n, IbipBatchItem *items);
+
+// Argument checks of one ibip_job, and the whole one-image path for it
+// (EDT, invasion, trapping and curve as requested), synchronous on the
+// context's stream; fills n_steps and returns the job's status.
+bool ibip_job_valid(const ibip_job &J);
+int ibip_run_job(ibip_ctx *ctx, ibip_job &J);
 
 // Status helpers.
 int ibip_cuda_status(cudaError_t e);

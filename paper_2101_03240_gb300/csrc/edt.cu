@@ -5,7 +5,7 @@
 // The squared EDT is separable: dt2(x,y,z) = min over features (a,b,c) of
 // (x-a)^2 + (y-b)^2 + (z-c)^2.  Three passes:
 //   pass z: d1 = distance along z to the nearest feature in the row (uint16,
-//           0xFFFF = none), from warp ballots over 32-voxel chunks;
+//           0xFFFF = none), from warp scans over 16-voxel lane segments;
 //   pass y: g2(y) = min_j d1(j)^2 + (y-j)^2 over the y column;
 //   pass x: dt2(x) = min_j g2(j) + (x-j)^2 over the x column.
 // Passes y and x stage a column strip (32 consecutive z, all of the line) in
@@ -18,18 +18,54 @@
 namespace {
 
 constexpr int kZWarps = 8;          // rows per block in pass z
-constexpr int kMaxChunks = 512;     // nz <= 16384
 constexpr int kStripW = 32;         // z lanes per strip in passes y / x
-constexpr int kStripWarps = 8;
+constexpr int kStripWarps = 16;
 
+// bytes of w equal to zero (or <= a per-byte bound) as 4 bits, lowest
+// address first
+__device__ __forceinline__ uint32_t byte_bits(uint32_t x)
+{
+    return (x & 1u) | ((x >> 7) & 2u) | ((x >> 14) & 4u) | ((x >> 21) & 8u);
+}
+
+// The feature tests of a pass-z row: operator() for one voxel, bits16 for the
+// 16 voxels base+z0 .. base+z0+15 (bit k = voxel z0+k; none past nz).
 struct FeatSolid {
     const uint8_t *img;
     __device__ bool operator()(int64_t v) const { return __ldg(img + v) == 0; }
+    __device__ uint32_t bits16(int64_t base, int z0, int nz) const
+    {
+        const uint8_t *p = img + base + z0;
+        if (z0 + 16 <= nz && ((uintptr_t)p & 15) == 0) {
+            const uint4 v = __ldg((const uint4 *)p);
+            return byte_bits(__vcmpeq4(v.x, 0)) | byte_bits(__vcmpeq4(v.y, 0)) << 4 |
+                   byte_bits(__vcmpeq4(v.z, 0)) << 8 | byte_bits(__vcmpeq4(v.w, 0)) << 12;
+        }
+        uint32_t m = 0;
+        for (int k = 0; k < 16 && z0 + k < nz; k++) m |= (uint32_t)(__ldg(p + k) == 0) << k;
+        return m;
+    }
 };
 struct FeatAtLeast {
     const int32_t *w;
     int32_t t;
     __device__ bool operator()(int64_t v) const { return __ldg(w + v) >= t; }
+    __device__ uint32_t bits16(int64_t base, int z0, int nz) const
+    {
+        const int32_t *p = w + base + z0;
+        uint32_t m = 0;
+        if (z0 + 16 <= nz && ((uintptr_t)p & 15) == 0) {
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int4 v = __ldg((const int4 *)p + q);
+                m |= (uint32_t)(v.x >= t) << (4 * q) | (uint32_t)(v.y >= t) << (4 * q + 1) |
+                     (uint32_t)(v.z >= t) << (4 * q + 2) | (uint32_t)(v.w >= t) << (4 * q + 3);
+            }
+            return m;
+        }
+        for (int k = 0; k < 16 && z0 + k < nz; k++) m |= (uint32_t)(__ldg(p + k) >= t) << k;
+        return m;
+    }
 };
 // opening: voxel v belongs to the trimmed set of level i iff its first level
 // (the first radius index whose T it reaches) is <= i
@@ -37,6 +73,19 @@ struct FeatFirstLevel {
     const uint8_t *fl;
     int i;
     __device__ bool operator()(int64_t v) const { return __ldg(fl + v) <= i; }
+    __device__ uint32_t bits16(int64_t base, int z0, int nz) const
+    {
+        const uint8_t *p = fl + base + z0;
+        if (z0 + 16 <= nz && ((uintptr_t)p & 15) == 0) {
+            const uint4 v = __ldg((const uint4 *)p);
+            const uint32_t b = (uint32_t)i * 0x01010101u;   // i <= 254
+            return byte_bits(__vcmpleu4(v.x, b)) | byte_bits(__vcmpleu4(v.y, b)) << 4 |
+                   byte_bits(__vcmpleu4(v.z, b)) << 8 | byte_bits(__vcmpleu4(v.w, b)) << 12;
+        }
+        uint32_t m = 0;
+        for (int k = 0; k < 16 && z0 + k < nz; k++) m |= (uint32_t)(__ldg(p + k) <= i) << k;
+        return m;
+    }
 };
 
 // first level of every voxel: the smallest i with W >= T[i] (255 if none)
@@ -54,79 +103,109 @@ __global__ void k_first_level(const int32_t *__restrict__ W, int64_t N, const in
     }
 }
 
+// pass z: one warp per row.  A lane takes 16 consecutive voxels (one vector
+// load); rows are walked in tiles of 512 voxels, left to right to find each
+// lane's nearest feature on the left (warp max-scan, carried across tiles),
+// then right to left for the nearest on the right (min-scan), writing the
+// distances as packed 16-byte stores.
 template <class Feat>
 __global__ void __launch_bounds__(kZWarps * 32) k_edt_z(Feat feat, int nrows, int nz, int cap,
                                                         uint16_t *__restrict__ d1)
 {
-    __shared__ uint32_t s_mask[kZWarps][kMaxChunks];
-    __shared__ int s_left[kZWarps][kMaxChunks];
+    extern __shared__ unsigned char s_zraw[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t row = (int64_t)blockIdx.x * kZWarps + w;
-    if (row >= nrows) return;
+    if (row >= nrows) return;   // whole warps only; no block barrier follows
+    const int ntile = (nz + 511) >> 9;
+    uint16_t *s_m = (uint16_t *)s_zraw + (size_t)w * ntile * 32;
+    int *s_l = (int *)(s_zraw + (size_t)kZWarps * ntile * 64) + (size_t)w * ntile * 32;
     const int64_t base = row * nz;
-    const int nch = (nz + 31) >> 5;
     const int NONE = 1 << 29;
     int carry = -NONE;
-    // feature tests of eight chunks are issued before their ballots so the
-    // loads overlap
-    for (int c0 = 0; c0 < nch; c0 += 8) {
-        bool f[8];
+    for (int t = 0; t < ntile; t++) {
+        const int z0 = (t << 9) + (lane << 4);
+        const uint32_t m = z0 < nz ? feat.bits16(base, z0, nz) : 0u;
+        s_m[t * 32 + lane] = (uint16_t)m;
+        int last = m ? z0 + 31 - __clz(m) : -NONE;
 #pragma unroll
-        for (int q = 0; q < 8; q++) {
-            const int z = ((c0 + q) << 5) + lane;
-            f[q] = c0 + q < nch && z < nz && feat(base + z);
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, last, o);
+            if (lane >= o) last = max(last, v);
         }
-#pragma unroll
-        for (int q = 0; q < 8; q++) {
-            const int c = c0 + q;
-            if (c >= nch) break;
-            const uint32_t m = __ballot_sync(0xffffffffu, f[q]);
-            if (lane == 0) { s_mask[w][c] = m; s_left[w][c] = carry; }
-            if (m) carry = (c << 5) + 31 - __clz(m);
-        }
+        int before = __shfl_up_sync(0xffffffffu, last, 1);
+        if (lane == 0) before = -NONE;
+        s_l[t * 32 + lane] = max(carry, before);
+        carry = max(carry, __shfl_sync(0xffffffffu, last, 31));
     }
-    __syncwarp();
-    int right = NONE;
-    for (int c = nch - 1; c >= 0; c--) {
-        uint32_t m = s_mask[w][c];
-        int z = (c << 5) + lane;
-        uint32_t ml = m & (0xffffffffu >> (31 - lane));
-        int left = ml ? (c << 5) + 31 - __clz(ml) : s_left[w][c];
-        uint32_t mr = m & (0xffffffffu << lane);
-        int rt = mr ? (c << 5) + __ffs(mr) - 1 : right;
-        if (z < nz) {
-            int d = min(z - left, rt - z);
-            d1[base + z] = (d > cap) ? (uint16_t)0xffff : (uint16_t)d;
+    int carry_r = NONE;
+    for (int t = ntile - 1; t >= 0; t--) {
+        const int z0 = (t << 9) + (lane << 4);
+        const uint32_t m = s_m[t * 32 + lane];
+        const int lb = s_l[t * 32 + lane];
+        int first = m ? z0 + __ffs(m) - 1 : NONE;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_down_sync(0xffffffffu, first, o);
+            if (lane + o < 32) first = min(first, v);
         }
-        if (m) right = (c << 5) + __ffs(m) - 1;
+        int after = __shfl_down_sync(0xffffffffu, first, 1);
+        if (lane == 31) after = NONE;
+        const int ra = min(carry_r, after);
+        carry_r = min(carry_r, __shfl_sync(0xffffffffu, first, 0));
+        if (z0 >= nz) continue;
+        uint32_t packed[8];
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+            const int z = z0 + k;
+            const uint32_t ml = m & (0xffffu >> (15 - k));   // features at or left of z in this lane
+            const uint32_t mr = m >> k;                       // features at or right of z
+            const int left = ml ? z0 + 31 - __clz(ml) : lb;
+            const int right = mr ? z + __ffs(mr) - 1 : ra;
+            const int d = min(z - left, right - z);
+            const uint32_t v = d > cap ? 0xffffu : (uint32_t)d;
+            if (k & 1) packed[k >> 1] |= v << 16;
+            else packed[k >> 1] = v;
+        }
+        uint16_t *o = d1 + base + z0;
+        if (z0 + 16 <= nz && ((uintptr_t)o & 15) == 0) {
+            uint4 *o4 = (uint4 *)o;
+            o4[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+            o4[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+        } else {
+            for (int k = 0; k < 16 && z0 + k < nz; k++) o[k] = (uint16_t)(packed[k >> 1] >> ((k & 1) * 16));
+        }
     }
 }
 
-// One min-plus line search.  `g(j)` returns the squared partial distance or
-// IBIP_INF32.  Values >= cap2 are reported as IBIP_INF32.
+size_t edt_z_smem(int nz) { return (size_t)kZWarps * ((nz + 511) >> 9) * 32 * 6; }
+
+// Sentinel of the partial sums: larger than any squared distance of an image
+// within the dimension limits (3 * 16383^2 < 2^30), and small enough that
+// adding a squared offset (< 2^28) cannot overflow.
+constexpr int kNone = 1 << 30;
+
+// One min-plus line search: min over j of f(j) + (i - j)^2, where `g(j)`
+// returns f(j) or kNone.  The search widens from j = i and stops once the
+// squared offset alone reaches the best value so far (or `lim`).  Returns a
+// value >= lim when nothing below lim exists.
 template <class G>
-__device__ __forceinline__ int line_min(const G &g, int i, int n, int cap2)
+__device__ __forceinline__ int line_min(const G &g, int i, int n, int lim)
 {
-    int best = g(i);
-    int lim = best < cap2 ? best : cap2;
-    for (int d = 1;; d++) {
-        int64_t dd = (int64_t)d * d;
-        if (dd >= lim) break;
-        int j0 = i - d, j1 = i + d;
-        if (j0 < 0 && j1 >= n) break;
-        if (j0 >= 0) {
-            int v = g(j0);
-            if (v != IBIP_INF32 && v + dd < best) { best = v + (int)dd; lim = best < cap2 ? best : cap2; }
-        }
-        if (j1 < n) {
-            int v = g(j1);
-            if (v != IBIP_INF32 && v + dd < best) { best = v + (int)dd; lim = best < cap2 ? best : cap2; }
-        }
+    int best = min(g(i), lim);
+    const int dmax = max(i, n - 1 - i);
+    int dd = 1;
+#pragma unroll 2
+    for (int d = 1; d <= dmax && dd < best; d++) {
+        const int vl = i - d >= 0 ? g(i - d) : kNone;
+        const int vr = i + d < n ? g(i + d) : kNone;
+        best = min(best, min(vl, vr) + dd);
+        dd += 2 * d + 1;
     }
-    return best >= cap2 ? IBIP_INF32 : best;
+    return best;
 }
 
 // pass y: strip = (x, all y, 32 z).  blockIdx.x = z strip, blockIdx.y = x.
+// Output: partial sums < cap2, kNone elsewhere.
 template <bool SMEM>
 __global__ void __launch_bounds__(kStripWarps * 32) k_edt_y(const uint16_t *__restrict__ d1, int ny,
                                                             int nz, int cap2, int32_t *__restrict__ g2)
@@ -143,10 +222,14 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_edt_y(const uint16_t *__re
     }
     if (!ok) return;
     auto g = [&](int j) -> int {
-        uint16_t v = SMEM ? s_col[j * kStripW + lane] : __ldg(d1 + b + (int64_t)j * nz);
-        return v == 0xffff ? IBIP_INF32 : (int)v * (int)v;
+        const int v = SMEM ? s_col[j * kStripW + lane] : __ldg(d1 + b + (int64_t)j * nz);
+        return v == 0xffff ? kNone : v * v;
     };
-    for (int y = w; y < ny; y += kStripWarps) g2[b + (int64_t)y * nz] = line_min(g, y, ny, cap2);
+    const int lim = min(cap2, kNone);
+    for (int y = w; y < ny; y += kStripWarps) {
+        const int v = line_min(g, y, ny, lim);
+        g2[b + (int64_t)y * nz] = v >= lim ? kNone : v;
+    }
 }
 
 struct EpiStore {
@@ -164,6 +247,7 @@ struct EpiLevel {
 };
 
 // pass x: strip = (y, all x, 32 z).  blockIdx.x = z strip, blockIdx.y = y.
+// Final values >= cap2 (or no feature at all) are reported as IBIP_INF32.
 template <bool SMEM, class Epi>
 __global__ void __launch_bounds__(kStripWarps * 32) k_edt_x(const int32_t *__restrict__ g2, int nx,
                                                             int ny, int nz, int cap2, Epi epi)
@@ -176,12 +260,16 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_edt_x(const int32_t *__res
     const int64_t b = (int64_t)y * nz + z;
     if (SMEM) {
 #pragma unroll 8
-        for (int x = w; x < nx; x += kStripWarps) s_colx[x * kStripW + lane] = ok ? __ldg(g2 + b + x * st) : IBIP_INF32;
+        for (int x = w; x < nx; x += kStripWarps) s_colx[x * kStripW + lane] = ok ? __ldg(g2 + b + x * st) : kNone;
         __syncthreads();
     }
     if (!ok) return;
     auto g = [&](int j) -> int { return SMEM ? s_colx[j * kStripW + lane] : __ldg(g2 + b + j * st); };
-    for (int x = w; x < nx; x += kStripWarps) epi(b + x * st, line_min(g, x, nx, cap2));
+    const int lim = min(cap2, kNone);
+    for (int x = w; x < nx; x += kStripWarps) {
+        const int v = line_min(g, x, nx, lim);
+        epi(b + x * st, v >= lim ? IBIP_INF32 : v);
+    }
 }
 
 constexpr size_t kSmemBudget = 200 * 1024;
@@ -196,7 +284,7 @@ int edt_passes(ibip_ctx *ctx, Feat feat, ibip_dims d, int cap, int cap2, Epi epi
     cudaStream_t s = ctx->stream;
     int nrows = d.nx * d.ny;
     ibip_prof_begin(ctx, cls);
-    k_edt_z<Feat><<<(nrows + kZWarps - 1) / kZWarps, kZWarps * 32, 0, s>>>(feat, nrows, d.nz, cap, d1);
+    k_edt_z<Feat><<<(nrows + kZWarps - 1) / kZWarps, kZWarps * 32, edt_z_smem(d.nz), s>>>(feat, nrows, d.nz, cap, d1);
     IBIP_LAUNCH(ctx);
     dim3 gy((d.nz + kStripW - 1) / kStripW, d.nx);
     size_t sy = (size_t)d.ny * kStripW * sizeof(uint16_t);
@@ -303,7 +391,8 @@ extern "C" int ibip_edt_noalloc(const uint8_t *image, ibip_dims d, int32_t *dt2,
     cudaStream_t s = (cudaStream_t)cuda_stream;
     uint16_t *d1 = (uint16_t *)dt2;   // 2 bytes per voxel inside the 4-byte output
     const int nrows = d.nx * d.ny;
-    k_edt_z<FeatSolid><<<(nrows + kZWarps - 1) / kZWarps, kZWarps * 32, 0, s>>>(FeatSolid{image}, nrows, d.nz, 0xfffe, d1);
+    k_edt_z<FeatSolid><<<(nrows + kZWarps - 1) / kZWarps, kZWarps * 32, edt_z_smem(d.nz), s>>>(FeatSolid{image}, nrows,
+                                                                                              d.nz, 0xfffe, d1);
     dim3 gy((d.nz + kStripW - 1) / kStripW, d.nx);
     const size_t sy = (size_t)d.ny * kStripW * sizeof(uint16_t);
     if (sy <= kSmemBudget) {

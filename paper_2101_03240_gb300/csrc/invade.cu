@@ -1150,6 +1150,22 @@ struct JobSizes {
 
 size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
 
+// Lets the kernel take all the dynamic shared memory the device allows.  The
+// value is the same on every call, so threads driving different contexts can
+// set it concurrently.
+void allow_max_dyn_smem(const void *func)
+{
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, func) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+}
+
 JobSizes job_sizes(ibip_dims d, int npore)
 {
     JobSizes z;
@@ -1207,8 +1223,11 @@ int invade_setup(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, int6
     }
     Bucket bk{incl, B, hasinf};
     // -- stable counting sort by bucket
+    // chunks of S voxels; the (bucket, chunk) count matrix is kept to at most
+    // max(N/4, 2^20) entries (one byte per voxel) by widening the chunks
     int64_t S = kChunk;
-    while ((N + S - 1) / S * (int64_t)B > (1ll << 26)) S *= 2;
+    const int64_t mat_lim = std::max(N / 4, (int64_t)1 << 20);
+    while (S < N && (N + S - 1) / S * (int64_t)B > mat_lim) S *= 2;
     const int C = (int)((N + S - 1) / S);
     int32_t *mat = (int32_t *)ibip_scratch(ctx, SC_MAT, (size_t)C * B * sizeof(int32_t));
     if (!mat) return IBIP_ERR_OOM;
@@ -1297,10 +1316,10 @@ int ibip_invade_run(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, i
     const size_t dyn = invade_dyn_smem(a, l1smem);
     ibip_prof_begin(ctx, IBIP_K_INVADE);
     if (l1smem) {
-        cudaFuncSetAttribute(k_invade<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn + 1024);
+        allow_max_dyn_smem((const void *)k_invade<true>);
         k_invade<true><<<1, kNT, dyn, s>>>(a, fd_nyz, fd_nz, mem.gl, mem.gl + npore);
     } else {
-        cudaFuncSetAttribute(k_invade<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn + 1024);
+        allow_max_dyn_smem((const void *)k_invade<false>);
         k_invade<false><<<1, kNT, dyn, s>>>(a, fd_nyz, fd_nz, mem.gl, mem.gl + npore);
     }
     IBIP_LAUNCH(ctx);
@@ -1386,7 +1405,7 @@ int ibip_invade_batch_run(ibip_ctx *ctx, int n, IbipBatchItem *it)
         if (!djobs) return IBIP_ERR_OOM;
         cudaMemcpyAsync(djobs, sorted.data(), (size_t)m * sizeof(InvJob), cudaMemcpyHostToDevice, s);
         ibip_prof_begin(ctx, IBIP_K_INVADE);
-        cudaFuncSetAttribute(k_invade_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn + 1024);
+        allow_max_dyn_smem((const void *)k_invade_batch);
         k_invade_batch<<<m, kNT, dyn, s>>>(djobs);
         IBIP_LAUNCH(ctx);
         ibip_prof_end(ctx, IBIP_K_INVADE);

@@ -15,6 +15,8 @@
 // shared memory and relaxes it until it stops changing.  A tile that changed
 // puts its six neighbours on the next round's work list; rounds are separated
 // by a grid-wide barrier and end when a list is empty (or at the round cap).
+// Contexts that share the device with other streams run the same rounds as
+// one ordinary launch each instead.
 // Everything other blocks write (the field, the lists, the counters) is read
 // with L2-coherent loads: the SM's L1 may hold a line from an earlier round.
 #include <cooperative_groups.h>
@@ -93,6 +95,93 @@ struct MMArgs {
     int max_rounds;
 };
 
+// Claims and relaxes the tiles of round r's list until the list is drained.
+// Tiles that changed queue their neighbours for round r + 1.
+__device__ void mm_round(const MMArgs &a, int r, int32_t (*sM)[TY + 2][TZ + 2], int *s_tile)
+{
+    const int cnt = __ldcg(a.count + r);
+    const int *list = (r & 1) ? a.list1 : a.list0;
+    int *next = (r & 1) ? a.list0 : a.list1;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int q = atomicAdd(&a.head[r], 1);
+            *s_tile = q < cnt ? __ldcg(list + q) : -1;
+        }
+        __syncthreads();
+        const int g = *s_tile;
+        if (g < 0) break;
+        int lo = 0, hi = a.njobs;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (__ldg(&a.jobs[mid].tile0) <= g) lo = mid; else hi = mid;
+        }
+        const MMJob J = a.jobs[lo];
+        const int t = g - J.tile0;
+        const int bz = t % J.tz, by = (t / J.tz) % J.ty, bx = t / (J.tz * J.ty);
+        const int x0 = bx * TX, y0 = by * TY, z0 = bz * TZ;
+        // tile + one-voxel halo of the field
+        for (int i = threadIdx.x; i < (TX + 2) * (TY + 2) * (TZ + 2); i += kThreads) {
+            const int hz = i % (TZ + 2), hy = (i / (TZ + 2)) % (TY + 2), hx = i / ((TZ + 2) * (TY + 2));
+            const int x = x0 + hx - 1, y = y0 + hy - 1, z = z0 + hz - 1;
+            int m = -1;
+            if (x >= 0 && y >= 0 && z >= 0 && x < J.nx && y < J.ny && z < J.nz)
+                m = __ldcg(J.M + d_lin(x, y, z, J.ny, J.nz));
+            sM[hx][hy][hz] = m;
+        }
+        int sval[kPer], lx[kPer], ly[kPer], lz[kPer];
+#pragma unroll
+        for (int k = 0; k < kPer; k++) {
+            const int i = threadIdx.x + k * kThreads;
+            lz[k] = i % TZ; ly[k] = (i / TZ) % TY; lx[k] = i / (TZ * TY);
+            const int x = x0 + lx[k], y = y0 + ly[k], z = z0 + lz[k];
+            sval[k] = (x < J.nx && y < J.ny && z < J.nz) ? as_val(J.val[d_lin(x, y, z, J.ny, J.nz)]) : 0;
+        }
+        __syncthreads();
+        bool any = false, conv = false;
+        for (int it = 0; it < kInner; it++) {
+            int ch = 0;
+#pragma unroll
+            for (int k = 0; k < kPer; k++) {
+                if (sval[k] == 0) continue;
+                const int hx = lx[k] + 1, hy = ly[k] + 1, hz = lz[k] + 1;
+                const int b = max(max(max(sM[hx - 1][hy][hz], sM[hx + 1][hy][hz]), max(sM[hx][hy - 1][hz], sM[hx][hy + 1][hz])),
+                                  max(sM[hx][hy][hz - 1], sM[hx][hy][hz + 1]));
+                const int nv = min(b, sval[k]);
+                if (nv > sM[hx][hy][hz]) { sM[hx][hy][hz] = nv; ch = 1; }
+            }
+            if (!__syncthreads_or(ch)) { conv = true; break; }
+            any = true;
+        }
+        // the first round's tiles hold the seeds: they always wake their
+        // neighbours (a tile that is only the face layer does not change)
+        if (any || r == 0) {
+#pragma unroll
+            for (int k = 0; k < kPer; k++) {
+                const int x = x0 + lx[k], y = y0 + ly[k], z = z0 + lz[k];
+                if (x < J.nx && y < J.ny && z < J.nz && sval[k] != 0)
+                    J.M[d_lin(x, y, z, J.ny, J.nz)] = sM[lx[k] + 1][ly[k] + 1][lz[k] + 1];
+            }
+            if (threadIdx.x == 0) {
+                const int nr = r + 1;
+                int nb[7] = {-1, -1, -1, -1, -1, -1, -1};
+                if (bx > 0) nb[0] = g - J.tz * J.ty;
+                if (bx < J.tx - 1) nb[1] = g + J.tz * J.ty;
+                if (by > 0) nb[2] = g - J.tz;
+                if (by < J.ty - 1) nb[3] = g + J.tz;
+                if (bz > 0) nb[4] = g - 1;
+                if (bz < J.tz - 1) nb[5] = g + 1;
+                if (!conv) nb[6] = g;
+                for (int q = 0; q < 7; q++) {
+                    if (nb[q] < 0) continue;
+                    if (atomicMax(&a.mark[nb[q]], nr) < nr) next[atomicAdd(&a.count[nr], 1)] = nb[q];
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// All rounds in one cooperative launch, a grid barrier between rounds.
 __global__ void __launch_bounds__(kThreads) k_mm_persistent(MMArgs a)
 {
     cg::grid_group grid = cg::this_grid();
@@ -100,87 +189,8 @@ __global__ void __launch_bounds__(kThreads) k_mm_persistent(MMArgs a)
     __shared__ int s_tile;
     int r = 0;
     for (;; r++) {
-        const int cnt = *(volatile int *)&a.count[r];
-        if (cnt == 0 || r >= a.max_rounds) break;
-        const int *list = (r & 1) ? a.list1 : a.list0;
-        int *next = (r & 1) ? a.list0 : a.list1;
-        for (;;) {
-            if (threadIdx.x == 0) {
-                const int q = atomicAdd(&a.head[r], 1);
-                s_tile = q < cnt ? __ldcg(list + q) : -1;
-            }
-            __syncthreads();
-            const int g = s_tile;
-            if (g < 0) break;
-            int lo = 0, hi = a.njobs;
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (__ldg(&a.jobs[mid].tile0) <= g) lo = mid; else hi = mid;
-            }
-            const MMJob J = a.jobs[lo];
-            const int t = g - J.tile0;
-            const int bz = t % J.tz, by = (t / J.tz) % J.ty, bx = t / (J.tz * J.ty);
-            const int x0 = bx * TX, y0 = by * TY, z0 = bz * TZ;
-            // tile + one-voxel halo of the field
-            for (int i = threadIdx.x; i < (TX + 2) * (TY + 2) * (TZ + 2); i += kThreads) {
-                const int hz = i % (TZ + 2), hy = (i / (TZ + 2)) % (TY + 2), hx = i / ((TZ + 2) * (TY + 2));
-                const int x = x0 + hx - 1, y = y0 + hy - 1, z = z0 + hz - 1;
-                int m = -1;
-                if (x >= 0 && y >= 0 && z >= 0 && x < J.nx && y < J.ny && z < J.nz)
-                    m = __ldcg(J.M + d_lin(x, y, z, J.ny, J.nz));
-                sM[hx][hy][hz] = m;
-            }
-            int sval[kPer], lx[kPer], ly[kPer], lz[kPer];
-#pragma unroll
-            for (int k = 0; k < kPer; k++) {
-                const int i = threadIdx.x + k * kThreads;
-                lz[k] = i % TZ; ly[k] = (i / TZ) % TY; lx[k] = i / (TZ * TY);
-                const int x = x0 + lx[k], y = y0 + ly[k], z = z0 + lz[k];
-                sval[k] = (x < J.nx && y < J.ny && z < J.nz) ? as_val(J.val[d_lin(x, y, z, J.ny, J.nz)]) : 0;
-            }
-            __syncthreads();
-            bool any = false, conv = false;
-            for (int it = 0; it < kInner; it++) {
-                int ch = 0;
-#pragma unroll
-                for (int k = 0; k < kPer; k++) {
-                    if (sval[k] == 0) continue;
-                    const int hx = lx[k] + 1, hy = ly[k] + 1, hz = lz[k] + 1;
-                    const int b = max(max(max(sM[hx - 1][hy][hz], sM[hx + 1][hy][hz]), max(sM[hx][hy - 1][hz], sM[hx][hy + 1][hz])),
-                                      max(sM[hx][hy][hz - 1], sM[hx][hy][hz + 1]));
-                    const int nv = min(b, sval[k]);
-                    if (nv > sM[hx][hy][hz]) { sM[hx][hy][hz] = nv; ch = 1; }
-                }
-                if (!__syncthreads_or(ch)) { conv = true; break; }
-                any = true;
-            }
-            // the first round's tiles hold the seeds: they always wake their
-            // neighbours (a tile that is only the face layer does not change)
-            if (any || r == 0) {
-#pragma unroll
-                for (int k = 0; k < kPer; k++) {
-                    const int x = x0 + lx[k], y = y0 + ly[k], z = z0 + lz[k];
-                    if (x < J.nx && y < J.ny && z < J.nz && sval[k] != 0)
-                        J.M[d_lin(x, y, z, J.ny, J.nz)] = sM[lx[k] + 1][ly[k] + 1][lz[k] + 1];
-                }
-                if (threadIdx.x == 0) {
-                    const int nr = r + 1;
-                    int nb[7] = {-1, -1, -1, -1, -1, -1, -1};
-                    if (bx > 0) nb[0] = g - J.tz * J.ty;
-                    if (bx < J.tx - 1) nb[1] = g + J.tz * J.ty;
-                    if (by > 0) nb[2] = g - J.tz;
-                    if (by < J.ty - 1) nb[3] = g + J.tz;
-                    if (bz > 0) nb[4] = g - 1;
-                    if (bz < J.tz - 1) nb[5] = g + 1;
-                    if (!conv) nb[6] = g;
-                    for (int q = 0; q < 7; q++) {
-                        if (nb[q] < 0) continue;
-                        if (atomicMax(&a.mark[nb[q]], nr) < nr) next[atomicAdd(&a.count[nr], 1)] = nb[q];
-                    }
-                }
-            }
-            __syncthreads();
-        }
+        if (__ldcg(a.count + r) == 0 || r >= a.max_rounds) break;
+        mm_round(a, r, sM, &s_tile);
         __threadfence();
         grid.sync();
     }
@@ -188,6 +198,16 @@ __global__ void __launch_bounds__(kThreads) k_mm_persistent(MMArgs a)
         a.status[0] = r;
         a.status[1] = (r >= a.max_rounds && __ldcg(a.count + r) != 0) ? 1 : 0;
     }
+}
+
+// One round per launch: for contexts whose kernels share the device with
+// other streams (a cooperative grid could not be made resident beside them).
+__global__ void __launch_bounds__(kThreads) k_mm_round(MMArgs a, int r)
+{
+    __shared__ int32_t sM[TX + 2][TY + 2][TZ + 2];
+    __shared__ int s_tile;
+    if (r >= a.max_rounds || __ldcg(a.count + r) == 0) return;
+    mm_round(a, r, sM, &s_tile);
 }
 
 }  // namespace
@@ -232,6 +252,30 @@ int ibip_maximin_multi(ibip_ctx *ctx, int n, const IbipMaximinJob *jobs, int max
     }
     k_mm_seed<<<(nt + 255) / 256, 256, 0, s>>>(djobs, n, nt, a.list0, a.count, a.mark);
     IBIP_LAUNCH(ctx);
+    int *h = (int *)ctx->h_pinned;
+    if (ctx->no_coop) {
+        // rounds in chunks; the next round's list size is read back after
+        // each chunk (an empty round's launch returns at once)
+        constexpr int kChunkRounds = 16;
+        const int grid = ctx->sm_count;
+        int r = 0;
+        for (;;) {
+            for (int q = 0; q < kChunkRounds && r < rounds; q++, r++) {
+                k_mm_round<<<grid, kThreads, 0, s>>>(a, r);
+                IBIP_LAUNCH(ctx);
+            }
+            cudaMemcpyAsync(h, a.count + r, sizeof(int), cudaMemcpyDeviceToHost, s);
+            cudaError_t e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) return ibip_cuda_status(e);
+            if (h[0] == 0) break;
+            if (r >= rounds) {
+                ibip_prof_end(ctx, IBIP_K_MAXIMIN);
+                return IBIP_ERR_NOT_CONVERGED;
+            }
+        }
+        ibip_prof_end(ctx, IBIP_K_MAXIMIN);
+        return IBIP_OK;
+    }
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mm_persistent, kThreads, 0) != cudaSuccess ||
         per_sm < 1) {
@@ -244,7 +288,6 @@ int ibip_maximin_multi(ibip_ctx *ctx, int n, const IbipMaximinJob *jobs, int max
     cudaError_t e = cudaLaunchCooperativeKernel((void *)k_mm_persistent, grid, kThreads, args, 0, s);
     IBIP_LAUNCH(ctx);
     if (e != cudaSuccess) return ibip_cuda_status(e);
-    int *h = (int *)ctx->h_pinned;
     cudaMemcpyAsync(h, a.status, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
     e = cudaStreamSynchronize(s);
     ibip_prof_end(ctx, IBIP_K_MAXIMIN);

@@ -38,6 +38,12 @@ class Job(C.Structure):
                 ("sigma", C.c_double), ("theta_deg", C.c_double), ("n_steps", C.c_int64), ("status", C.c_int32)]
 
 
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("slot", C.c_int32), ("n_steps", C.c_int64), ("t_submit_ns", C.c_int64),
+                ("t_start_ns", C.c_int64), ("t_end_ns", C.c_int64), ("mem_reserved", C.c_int64),
+                ("mem_used", C.c_int64)]
+
+
 class IbipError(RuntimeError):
     def __init__(self, fn, status):
         self.status = status
@@ -77,6 +83,13 @@ def _lib():
                 "ibip_invade_batched": (C.c_int, [P, i32, P]),
                 "ibip_invade_stats": (C.c_int, [P, C.POINTER(i64), C.c_int]),
                 "ibip_profile_read": (C.c_int, [P, C.c_int, C.POINTER(dbl), C.POINTER(i64)]),
+                "ibip_job_footprint": (i64, [Dims, C.c_int]),
+                "ibip_server_create": (C.c_int, [C.POINTER(P), P, C.c_size_t, C.c_int]),
+                "ibip_server_destroy": (C.c_int, [P]),
+                "ibip_server_submit": (C.c_int, [P, C.POINTER(Job), C.POINTER(C.c_uint64)]),
+                "ibip_server_poll": (C.c_int, [P, C.c_uint64, C.POINTER(C.c_int), C.POINTER(Result)]),
+                "ibip_server_wait": (C.c_int, [P, C.c_uint64, i64, C.POINTER(C.c_int), C.POINTER(Result)]),
+                "ibip_server_stats": (C.c_int, [P, C.POINTER(i64), C.c_int]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -98,6 +111,46 @@ def _dims(shape):
 def _need(t, dtype, name):
     if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous() and t.dim() == 3):
         raise ValueError("%s must be a contiguous 3-D CUDA %s tensor" % (name, dtype))
+
+
+def _fill_job(J, im, inlet, outlet, trapping, curve, voxel_m, sigma, theta_deg):
+    """Allocates the outputs of one image and fills its ibip_job."""
+    _need(im, torch.uint8, "image")
+    dev, N = im.device, im.numel()
+    r = {"seq": torch.empty(im.shape, dtype=torch.int32, device=dev),
+         "step_r2": torch.empty(max(N, 1), dtype=torch.int32, device=dev),
+         "step_centre": torch.empty(max(N, 1), dtype=torch.int32, device=dev)}
+    if trapping:
+        r["trapped"] = torch.empty(im.shape, dtype=torch.uint8, device=dev)
+        r["seq_out"] = torch.empty(im.shape, dtype=torch.int32, device=dev)
+    if curve:
+        r["S"] = torch.empty(max(N, 1), dtype=torch.float32, device=dev)
+        r["Pc"] = torch.empty(max(N, 1), dtype=torch.float32, device=dev)
+    J.image = im.data_ptr()
+    J.dims = _dims(im.shape)
+    J.inlet, J.outlet = inlet, outlet if trapping else -1
+    J.dt2 = None
+    J.seq, J.step_r2, J.step_centre = r["seq"].data_ptr(), r["step_r2"].data_ptr(), r["step_centre"].data_ptr()
+    J.capacity_steps = N
+    J.trapped = r["trapped"].data_ptr() if trapping else None
+    J.seq_out = r["seq_out"].data_ptr() if trapping else None
+    J.sat_per_step = r["S"].data_ptr() if curve else None
+    J.pc_per_step = r["Pc"].data_ptr() if curve else None
+    J.voxel_m, J.sigma, J.theta_deg = float(voxel_m), float(sigma), float(theta_deg)
+    return r
+
+
+def _trim(r, K):
+    for key in ("step_r2", "step_centre", "S", "Pc"):
+        if key in r:
+            r[key] = r[key][:K]
+    return r
+
+
+def job_footprint(shape, with_dt2=True) -> int:
+    """Upper bound of the device scratch bytes one served job of this shape
+    takes (ibip_job_footprint)."""
+    return int(_lib().ibip_job_footprint(_dims(shape), 1 if with_dt2 else 0))
 
 
 class Context:
@@ -236,30 +289,7 @@ class Context:
         arr = (Job * n)()
         res = []
         for j, im in enumerate(images):
-            _need(im, torch.uint8, "image")
-            dev, N = im.device, im.numel()
-            r = {"seq": torch.empty(im.shape, dtype=torch.int32, device=dev),
-                 "step_r2": torch.empty(max(N, 1), dtype=torch.int32, device=dev),
-                 "step_centre": torch.empty(max(N, 1), dtype=torch.int32, device=dev)}
-            if trapping:
-                r["trapped"] = torch.empty(im.shape, dtype=torch.uint8, device=dev)
-                r["seq_out"] = torch.empty(im.shape, dtype=torch.int32, device=dev)
-            if curve:
-                r["S"] = torch.empty(max(N, 1), dtype=torch.float32, device=dev)
-                r["Pc"] = torch.empty(max(N, 1), dtype=torch.float32, device=dev)
-            J = arr[j]
-            J.image = im.data_ptr()
-            J.dims = _dims(im.shape)
-            J.inlet, J.outlet = int(inl[j]), int(outl[j]) if trapping else -1
-            J.dt2 = None
-            J.seq, J.step_r2, J.step_centre = r["seq"].data_ptr(), r["step_r2"].data_ptr(), r["step_centre"].data_ptr()
-            J.capacity_steps = N
-            J.trapped = r["trapped"].data_ptr() if trapping else None
-            J.seq_out = r["seq_out"].data_ptr() if trapping else None
-            J.sat_per_step = r["S"].data_ptr() if curve else None
-            J.pc_per_step = r["Pc"].data_ptr() if curve else None
-            J.voxel_m, J.sigma, J.theta_deg = float(voxel_m), float(sigma), float(theta_deg)
-            res.append(r)
+            res.append(_fill_job(arr[j], im, int(inl[j]), int(outl[j]), trapping, curve, voxel_m, sigma, theta_deg))
         self._stream()
         st = _lib().ibip_invade_batched(self._h, n, arr)
         if check and st != OK:
@@ -267,9 +297,7 @@ class Context:
         for j, r in enumerate(res):
             K = int(arr[j].n_steps)
             r["K"], r["status"] = K, int(arr[j].status)
-            for key in ("step_r2", "step_centre", "S", "Pc"):
-                if key in r:
-                    r[key] = r[key][:K]
+            _trim(r, K)
         return res
 
     def pc_curve(self, seq, step_r2, voxel_m=5e-6, sigma=0.072, theta_deg=180.0, sat_image=False):
@@ -286,6 +314,83 @@ class Context:
         if st != OK:
             raise IbipError("ibip_pc_curve", st)
         return S[:K], P[:K], img
+
+
+class Server:
+    """Continuous-batching request loop (ibip_server_*): jobs are admitted in
+    arrival order as slots and arena memory free up, and run concurrently on
+    the slots' streams.  `mem_budget` bytes of device memory are allocated
+    up front."""
+
+    def __init__(self, ctx: Context, mem_budget: int, max_slots: int = 16):
+        h = C.c_void_p()
+        st = _lib().ibip_server_create(C.byref(h), ctx._h, int(mem_budget), int(max_slots))
+        if st != OK:
+            raise IbipError("ibip_server_create", st)
+        self._h = h
+        self.device = ctx.device
+        self._live = {}   # ticket -> (job, image, outputs): kept alive until collected
+
+    def submit(self, image, inlet=0, outlet=1, trapping=True, curve=True, voxel_m=5e-6, sigma=0.072,
+               theta_deg=180.0) -> int:
+        """Queues the whole path for one image; returns its ticket.  The
+        image and the outputs are read and written on a slot's stream, so
+        the current stream is synchronised first (the image must be ready)."""
+        J = Job()
+        r = _fill_job(J, image, int(inlet), int(outlet), trapping, curve, voxel_m, sigma, theta_deg)
+        torch.cuda.current_stream(image.device).synchronize()
+        t = C.c_uint64()
+        st = _lib().ibip_server_submit(self._h, C.byref(J), C.byref(t))
+        if st != OK:
+            raise IbipError("ibip_server_submit", st)
+        self._live[t.value] = (J, image, r)
+        return t.value
+
+    def _collect(self, ticket, done, res):
+        if not done.value:
+            return None
+        _, _, r = self._live.pop(ticket)
+        K = int(res.n_steps)
+        r.update(K=K, status=int(res.status), slot=int(res.slot), t_submit_ns=int(res.t_submit_ns),
+                 t_start_ns=int(res.t_start_ns), t_end_ns=int(res.t_end_ns), mem_reserved=int(res.mem_reserved),
+                 mem_used=int(res.mem_used))
+        return _trim(r, K)
+
+    def poll(self, ticket):
+        """The job's result dict if it has completed (collected once), else None."""
+        done, res = C.c_int(), Result()
+        st = _lib().ibip_server_poll(self._h, int(ticket), C.byref(done), C.byref(res))
+        if st != OK:
+            raise IbipError("ibip_server_poll", st)
+        return self._collect(ticket, done, res)
+
+    def wait(self, ticket, timeout=None):
+        """Blocks until the job completes (or `timeout` seconds pass: None)."""
+        done, res = C.c_int(), Result()
+        us = -1 if timeout is None else int(timeout * 1e6)
+        st = _lib().ibip_server_wait(self._h, int(ticket), us, C.byref(done), C.byref(res))
+        if st != OK:
+            raise IbipError("ibip_server_wait", st)
+        return self._collect(ticket, done, res)
+
+    def stats(self) -> dict:
+        v = (C.c_int64 * 9)()
+        _lib().ibip_server_stats(self._h, v, 9)
+        keys = ("submitted", "completed", "running", "waiting", "arena_used", "arena_bytes", "peak_running",
+                "peak_arena_used", "launches")
+        return dict(zip(keys, (int(x) for x in v)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib().ibip_server_destroy(self._h)
+            self._h = None
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 _default = {}
