@@ -204,28 +204,63 @@ __device__ __forceinline__ int line_min(const G &g, int i, int n, int lim)
     return best;
 }
 
+// The same search over a staged column in shared memory (`col` points at
+// entry 0 of this lane's column, entries kStripW apart): both sides while
+// both are inside the line, then the remaining side alone.
+__device__ __forceinline__ int line_min_smem(const int32_t *col, int i, int n, int lim)
+{
+    const int32_t *c = col + i * kStripW;
+    int best = min(c[0], lim);
+    const int both = min(i, n - 1 - i);
+    int d = 1, dd = 1;
+#pragma unroll 2
+    for (; d <= both && dd < best; d++) {
+        best = min(best, min(c[-d * kStripW], c[d * kStripW]) + dd);
+        dd += 2 * d + 1;
+    }
+    if (dd < best) {
+        const int step = i - d >= 0 ? -kStripW : kStripW;   // the side still inside
+        const int end = step < 0 ? i : n - 1 - i;
+        for (; d <= end && dd < best; d++) {
+            best = min(best, c[d * step] + dd);
+            dd += 2 * d + 1;
+        }
+    }
+    return best;
+}
+
 // pass y: strip = (x, all y, 32 z).  blockIdx.x = z strip, blockIdx.y = x.
-// Output: partial sums < cap2, kNone elsewhere.
+// Output: partial sums < cap2, kNone elsewhere.  The staged column holds
+// the squared pass-z distances.
 template <bool SMEM>
 __global__ void __launch_bounds__(kStripWarps * 32) k_edt_y(const uint16_t *__restrict__ d1, int ny,
                                                             int nz, int cap2, int32_t *__restrict__ g2)
 {
-    extern __shared__ uint16_t s_col[];
+    extern __shared__ int32_t s_col[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int x = blockIdx.y, z = blockIdx.x * kStripW + lane;
     const bool ok = z < nz;
     const int64_t b = (int64_t)x * ny * nz + z;
+    const int lim = min(cap2, kNone);
     if (SMEM) {
 #pragma unroll 8
-        for (int y = w; y < ny; y += kStripWarps) s_col[y * kStripW + lane] = ok ? __ldg(d1 + b + (int64_t)y * nz) : 0xffff;
+        for (int y = w; y < ny; y += kStripWarps) {
+            const int v = ok ? __ldg(d1 + b + (int64_t)y * nz) : 0xffff;
+            s_col[y * kStripW + lane] = v == 0xffff ? kNone : v * v;
+        }
         __syncthreads();
+        if (!ok) return;
+        for (int y = w; y < ny; y += kStripWarps) {
+            const int v = line_min_smem(s_col + lane, y, ny, lim);
+            g2[b + (int64_t)y * nz] = v >= lim ? kNone : v;
+        }
+        return;
     }
     if (!ok) return;
     auto g = [&](int j) -> int {
-        const int v = SMEM ? s_col[j * kStripW + lane] : __ldg(d1 + b + (int64_t)j * nz);
+        const int v = __ldg(d1 + b + (int64_t)j * nz);
         return v == 0xffff ? kNone : v * v;
     };
-    const int lim = min(cap2, kNone);
     for (int y = w; y < ny; y += kStripWarps) {
         const int v = line_min(g, y, ny, lim);
         g2[b + (int64_t)y * nz] = v >= lim ? kNone : v;
@@ -258,14 +293,20 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_edt_x(const int32_t *__res
     const bool ok = z < nz;
     const int64_t st = (int64_t)ny * nz;
     const int64_t b = (int64_t)y * nz + z;
+    const int lim = min(cap2, kNone);
     if (SMEM) {
 #pragma unroll 8
         for (int x = w; x < nx; x += kStripWarps) s_colx[x * kStripW + lane] = ok ? __ldg(g2 + b + x * st) : kNone;
         __syncthreads();
+        if (!ok) return;
+        for (int x = w; x < nx; x += kStripWarps) {
+            const int v = line_min_smem(s_colx + lane, x, nx, lim);
+            epi(b + x * st, v >= lim ? IBIP_INF32 : v);
+        }
+        return;
     }
     if (!ok) return;
-    auto g = [&](int j) -> int { return SMEM ? s_colx[j * kStripW + lane] : __ldg(g2 + b + j * st); };
-    const int lim = min(cap2, kNone);
+    auto g = [&](int j) -> int { return __ldg(g2 + b + j * st); };
     for (int x = w; x < nx; x += kStripWarps) {
         const int v = line_min(g, x, nx, lim);
         epi(b + x * st, v >= lim ? IBIP_INF32 : v);
@@ -287,7 +328,7 @@ int edt_passes(ibip_ctx *ctx, Feat feat, ibip_dims d, int cap, int cap2, Epi epi
     k_edt_z<Feat><<<(nrows + kZWarps - 1) / kZWarps, kZWarps * 32, edt_z_smem(d.nz), s>>>(feat, nrows, d.nz, cap, d1);
     IBIP_LAUNCH(ctx);
     dim3 gy((d.nz + kStripW - 1) / kStripW, d.nx);
-    size_t sy = (size_t)d.ny * kStripW * sizeof(uint16_t);
+    size_t sy = (size_t)d.ny * kStripW * sizeof(int32_t);
     if (sy <= kSmemBudget) {
         cudaFuncSetAttribute(k_edt_y<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget);
         k_edt_y<true><<<gy, kStripWarps * 32, sy, s>>>(d1, d.ny, d.nz, cap2, g2);
@@ -394,7 +435,7 @@ extern "C" int ibip_edt_noalloc(const uint8_t *image, ibip_dims d, int32_t *dt2,
     k_edt_z<FeatSolid><<<(nrows + kZWarps - 1) / kZWarps, kZWarps * 32, edt_z_smem(d.nz), s>>>(FeatSolid{image}, nrows,
                                                                                               d.nz, 0xfffe, d1);
     dim3 gy((d.nz + kStripW - 1) / kStripW, d.nx);
-    const size_t sy = (size_t)d.ny * kStripW * sizeof(uint16_t);
+    const size_t sy = (size_t)d.ny * kStripW * sizeof(int32_t);
     if (sy <= kSmemBudget) {
         cudaFuncSetAttribute(k_edt_y<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget);
         k_edt_y<true><<<gy, kStripWarps * 32, sy, s>>>(d1, d.ny, d.nz, IBIP_INF32, g2);

@@ -776,12 +776,20 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
                       ((u64)__ballot_sync(0xffffffffu, cont[1] != 0) << 32);
             u64 valid = m == 64 ? ~0ull : ((1ull << m) - 1);
             u64 keep = valid & ~has;
-            u64 pend = has & valid;
-            while (pend) {
-                int j = __ffsll(pend) - 1;
-                pend &= pend - 1;
-                u64 cj = __shfl_sync(0xffffffffu, j < 32 ? cont[0] : cont[1], j & 31);
-                if (!(cj & keep)) keep |= 1ull << j;
+            // An item is kept iff no kept earlier item's ball contains it.
+            // Containers come earlier, so rounds that settle every item whose
+            // containers are all settled reach the sequential answer.
+            u64 decided = ~(has & valid);
+            while (~decided) {
+                bool rd[2], kp[2];
+#pragma unroll
+                for (int q = 0; q < 2; q++) {
+                    const int j = lane + 32 * q;
+                    rd[q] = !((decided >> j) & 1) && (cont[q] & ~decided) == 0;
+                    kp[q] = rd[q] && (cont[q] & keep) == 0;
+                }
+                decided |= (u64)__ballot_sync(0xffffffffu, rd[0]) | ((u64)__ballot_sync(0xffffffffu, rd[1]) << 32);
+                keep |= (u64)__ballot_sync(0xffffffffu, kp[0]) | ((u64)__ballot_sync(0xffffffffu, kp[1]) << 32);
             }
             const long long tc2 = clock64();
             if (tid == 0) c_sub[4] += tc2 - tc;
@@ -818,23 +826,26 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
             }
             mcap = min(mcap, cut);
             if (tid == 0) c_sub[5] += clock64() - tc2;
+            // prefix through item mcap - 1, carried by every later item
+            const bool odd = (mcap - 1) & 1;
+            int last = __shfl_sync(0xffffffffu, odd ? inc : ex + r0, max(mcap - 1, 0) >> 1);
+            int dlast = __shfl_sync(0xffffffffu, odd ? dinc : dex + d0, max(mcap - 1, 0) >> 1);
+            if (mcap == 0) { last = 0; dlast = 0; }
             __syncwarp();
             if (j0 < m) {
                 B.step[j0] = ((keep >> j0) & 1) ? __popcll(keep & ((1ull << j0) - 1)) : -1;
-                B.upre[j0 + 1] = j0 < mcap ? ex + r0 : 0;
-                B.dpre[j0 + 1] = j0 < mcap ? dex + d0 : 0;
+                B.upre[j0 + 1] = j0 < mcap ? ex + r0 : last;
+                B.dpre[j0 + 1] = j0 < mcap ? dex + d0 : dlast;
             }
             if (j1 < m) {
                 B.step[j1] = ((keep >> j1) & 1) ? __popcll(keep & ((1ull << j1) - 1)) : -1;
-                B.upre[j1 + 1] = j1 < mcap ? ex + r0 + r1 : 0;
-                B.dpre[j1 + 1] = j1 < mcap ? dex + d0 + d1 : 0;
+                B.upre[j1 + 1] = j1 < mcap ? ex + r0 + r1 : last;
+                B.dpre[j1 + 1] = j1 < mcap ? dex + d0 + d1 : dlast;
             }
             __syncwarp();
             if (lane == 0) {
                 B.upre[0] = 0;
                 B.dpre[0] = 0;
-                const int last = mcap > 0 ? B.upre[mcap] : 0, dlast = mcap > 0 ? B.dpre[mcap] : 0;
-                for (int j = mcap; j < m; j++) { B.upre[j + 1] = last; B.dpre[j + 1] = dlast; }
                 B.mcap = mcap;
                 B.J = mcap;
                 B.keep = keep;
