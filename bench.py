@@ -39,6 +39,24 @@ L2_BYTES = 129 * 1024 * 1024
 CLASS_NAMES = ["edt", "rank", "invade", "maximin", "trap", "pc", "dilate"]
 
 
+def max_over_ranks(x, world, device):
+    """The largest x over all ranks: a replica job takes as long as its
+    slowest rank.  Works on any process group (NCCL on GPUs, gloo on CPU)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, seconds):
+    """Whole-job throughput of `world` independent replicas that each
+    processed `units_per_rank` units, the slowest in `seconds`."""
+    return world * units_per_rank / seconds
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -170,10 +188,7 @@ def run_batch(args, rank, world):
     ctx.profile(False)
     ck = clocks.stop() if clocks else None
     ms_step = sum(ms) / len(ms)
-    if world > 1:
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks(ms_step, world, dev)
     # plain per-image path, one pass (same outputs)
     single()
     torch.cuda.synchronize()
@@ -193,7 +208,7 @@ def run_batch(args, rank, world):
     for o, r in zip(outs, res):
         o.copy_(r["seq_out"], non_blocking=True)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
     if rank != 0:
         return None
     tot = sum(v[0] for v in prof.values()) or 1.0
@@ -207,7 +222,7 @@ def run_batch(args, rank, world):
     achieved = alg / (inv_ms * 1e-3) / 1e9
     out = {
         "metric": "batched images/s (EDT+rank+invasion+trapping+Pc per image, bit-exact vs oracle)",
-        "value": world * nimg / (ms_step * 1e-3), "unit": "images/s", "n_gpus": world, "steps": args.steps,
+        "value": job_rate(nimg, world, ms_step * 1e-3), "unit": "images/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": "batch256", "images": nimg, "voxels": nvox_total, "edge": "32..160 log-uniform",
@@ -216,7 +231,7 @@ def run_batch(args, rank, world):
         "per_image_path_images_per_s": nimg / single_s,
         "batched_over_per_image": (nimg / (ms_step * 1e-3)) / (nimg / single_s),
         "invasion_steps": steps_total,
-        "e2e": {"value": world * nimg / e2e_s, "unit": "images/s", "h2d_bytes_per_step": int(nvox_total),
+        "e2e": {"value": job_rate(nimg, world, e2e_s), "unit": "images/s", "h2d_bytes_per_step": int(nvox_total),
                 "d2h_bytes_per_step": int(4 * nvox_total)},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "kernel": "invade (batched)", "achieved": round(achieved, 3), "peak": hbm_peak,
@@ -326,7 +341,7 @@ def run_serve(args, rank, world):
     for o, t in zip(outs, ts):
         o.copy_(srv.wait(t)["seq_out"])
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
     srv.close()
     # the plain one-image-per-call path on the same requests
     alone_s = []
@@ -343,16 +358,13 @@ def run_serve(args, rank, world):
     single_s = sum(alone_s)
     service_s = [(r["t_end_ns"] - r["t_start_ns"]) * 1e-9 for r in res]
     sat_s = sum(pass_s) / len(pass_s)
-    if world > 1:
-        t = torch.tensor([sat_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        sat_s = float(t.item())
+    sat_s = max_over_ranks(sat_s, world, dev)
     if rank != 0:
         return None
     n = len(imgs)
     out = {
         "metric": "served images/s and p50/p99 latency (EDT+rank+invasion+trapping+Pc per request, bit-exact)",
-        "value": world * n / sat_s, "unit": "images/s", "n_gpus": world, "steps": args.steps,
+        "value": job_rate(n, world, sat_s), "unit": "images/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": sat_s * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": "serve", "requests": n, "rate_per_s": 20.0, "voxels": int(nvox_total),
@@ -371,7 +383,7 @@ def run_serve(args, rank, world):
                  "largest_edge": max(a.shape[0] for a in imgs_h),
                  "note": "a served pass cannot end before its longest job; alone_s_max bounds it from below"},
         "invasion_steps": int(sum(Ks)),
-        "e2e": {"value": world * n / e2e_s, "unit": "images/s", "h2d_bytes_per_step": int(nvox_total),
+        "e2e": {"value": job_rate(n, world, e2e_s), "unit": "images/s", "h2d_bytes_per_step": int(nvox_total),
                 "d2h_bytes_per_step": int(4 * nvox_total)},
         "gpu_launches": int(launches),
         "clocks": ck,
@@ -454,10 +466,8 @@ def run_ours(args, rank, world):
     ck = clocks.stop() if clocks else None
     ms = [a.elapsed_time(b) for a, b in ev]
     ms_step = sum(ms) / len(ms)
+    ms_step = max_over_ranks(ms_step, world, dev)
     if world > 1:
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
         dist.barrier()
 
     # ---- end to end through the public API (host image in, seq_out + Pc out)
@@ -479,10 +489,7 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
         e2e_ms.append(a.elapsed_time(b))
     e2e_step = sum(e2e_ms) / len(e2e_ms)
-    if world > 1:
-        t = torch.tensor([e2e_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_step = float(t.item())
+    e2e_step = max_over_ranks(e2e_step, world, dev)
 
     if rank != 0:
         return None
@@ -519,7 +526,7 @@ def run_ours(args, rank, world):
                         "algorithmic minimum (dt2 read + seq write + step arrays)"}
     us_per_step = prof["invade"][0] / max(args.steps, 1) * 1e3 / max(K, 1)
 
-    value = world * N / (ms_step * 1e-3)
+    value = job_rate(N, world, ms_step * 1e-3)
     out = {
         "metric": "invasion voxels/s (EDT+rank+invasion+trapping+Pc+opening, bit-exact vs oracle)",
         "value": value,
@@ -539,7 +546,7 @@ def run_ours(args, rank, world):
         "invasion_steps": K,
         "invasion_steps_per_s": K / (prof["invade"][0] / args.steps * 1e-3) if prof["invade"][1] else None,
         "invasion_us_per_step": us_per_step,
-        "e2e": {"value": world * N / (e2e_step * 1e-3), "unit": "voxels/s",
+        "e2e": {"value": job_rate(N, world, e2e_step * 1e-3), "unit": "voxels/s",
                 "h2d_bytes_per_step": int(img_h.nbytes),
                 "d2h_bytes_per_step": int(out_seq.numel() * 4 + K * 4)},
         "gpu_launches": int(launches),
@@ -576,9 +583,55 @@ def cpu_baseline(args, w, levels):
             "seconds": t}
 
 
+def run_reference_images(args, world):
+    """The oracle on a bounded sample of the batch / request-stream images:
+    whole path per image (EDT, invasion, trapping, Pc), images/s."""
+    import oracle as O
+    from paper_2101_03240_gb300 import synth
+    if args.config == "batch256":
+        imgs = [synth.mixed_image(i, 4000, 32, 160) for i in range(8)]
+        sample = "the first 8 images of the 256-image batch, whole path each"
+        cfg = {"workload": "batch256", "images": 256, "edge": "32..160 log-uniform",
+               "mix": "half blobs, half sphere packs"}
+        metric = "batched images/s (EDT+rank+invasion+trapping+Pc per image, bit-exact vs oracle)"
+    else:
+        reqs = synth.c5_requests(n=args.requests)
+        small = sorted(range(min(32, len(reqs))), key=lambda j: reqs[j][1])[:4]
+        imgs = [synth.mixed_image(j, 5000, 64, 384) for j in small]
+        sample = "the 4 smallest of the first 32 requests, whole path each"
+        cfg = {"workload": "serve", "requests": len(reqs), "rate_per_s": 20.0, "edge": "64..384 log-uniform",
+               "mix": "half blobs, half sphere packs"}
+        metric = "served images/s and p50/p99 latency (EDT+rank+invasion+trapping+Pc per request, bit-exact)"
+
+    def one_pass():
+        for a in imgs:
+            d = O.edt(a)
+            sq = O.invade(a, d, inlet=0)
+            so = O.trapping(sq[0], 1)[1]
+            O.pc_curve(so, sq[1])
+
+    for _ in range(args.warmup):
+        one_pass()
+    ts = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        one_pass()
+        ts.append(time.perf_counter() - t)
+    s = sum(ts) / len(ts)
+    v = len(imgs) / s
+    return {"impl": "reference", "metric": metric, "value": v, "unit": "images/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": s * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": v, "unit": "images/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "images/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return None
+    if args.config in ("batch256", "serve"):
+        return run_reference_images(args, world)
     import oracle as O
     from paper_2101_03240_gb300 import synth
     w = workload(args.config)
