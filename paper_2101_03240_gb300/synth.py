@@ -149,6 +149,12 @@ def c3_blobs512(seed=3) -> Workload:
                     0, 1, mio_levels=40)
 
 
+def mixed_edge(i, seed_base, lo, hi):
+    """Edge length of mixed_image(i, seed_base, lo, hi) without building it."""
+    rng = np.random.default_rng(seed_base + i)
+    return int(round(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
+
+
 def mixed_image(i, seed_base, lo, hi):
     """Image `i` of a mixed batch: edge log-uniform in [lo, hi]; even i are
     blobs (sigma U(2,6), porosity U(0.5,0.7)), odd i are sphere packs
