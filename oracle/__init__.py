@@ -52,6 +52,8 @@ def lib():
                 "or_edt_sep": (None, [P, i32, i32, i32, P]),
                 "or_invade_scan": (i64, [P, P, i32, i32, i32, i32, i64, P, P, P, i64, P]),
                 "or_invade_heap": (i64, [P, P, i32, i32, i32, i32, i64, P, P, P, i64, P]),
+                "or_invade_literal_scan": (i64, [P, P, i32, i32, i32, i32, i64, P, P, P, P, i64, P]),
+                "or_invade_literal_queue": (i64, [P, P, i32, i32, i32, i32, i64, P, P, P, P, i64, P]),
                 "or_trap_bfs": (None, [P, i32, i32, i32, i32, i32, P, P]),
                 "or_trap_uf": (None, [P, i32, i32, i32, i32, i32, P, P]),
                 "or_count_unconnected": (i64, [P, i32, i32, i32, i32]),
@@ -115,6 +117,33 @@ def invade(image, dt2, inlet=0, max_steps=None, method="heap", capacity=None):
     kk = min(k, cap)
     del n
     return seq, r2[:kk].copy(), cen[:kk].copy(), int(st.value), k
+
+
+def invade_literal(image, dt2, inlet=0, max_steps=None, method="queue", capacity=None):
+    """The invasion exactly as Section 2.1 prints it: candidates are the
+    inlets plus their face neighbours, every candidate holding the largest
+    value is an insertion point of the step, spheres have the truncated
+    integer radius, insertion points join the inlets with their value set to
+    zero.  Returns (seq, cstep, step_r2, step_count, status, K): cstep[v] is
+    the step at which v was an insertion point (0 never), step_r2 the squared
+    integer radius of each step, step_count its number of insertion points.
+    method: "queue" (each voxel queued once) or "scan" (the definition)."""
+    a = _img(image)
+    d = np.ascontiguousarray(dt2, dtype=np.int32)
+    npore = int(np.count_nonzero(a))
+    if max_steps is None:
+        max_steps = npore
+    cap = npore if capacity is None else int(capacity)
+    seq = np.empty(a.shape, np.int32)
+    cstep = np.empty(a.shape, np.int32)
+    r2 = np.zeros(max(cap, 1), np.int32)
+    cnt = np.zeros(max(cap, 1), np.int32)
+    st = C.c_int(0)
+    f = lib().or_invade_literal_queue if method == "queue" else lib().or_invade_literal_scan
+    k = int(f(_p(a), _p(d), *a.shape, int(inlet), int(max_steps), _p(seq), _p(cstep), _p(r2), _p(cnt), cap,
+              C.addressof(st)))
+    kk = min(k, cap)
+    return seq, cstep, r2[:kk].copy(), cnt[:kk].copy(), int(st.value), k
 
 
 def trapping(seq, outlet=1, rerank=False, method="uf"):

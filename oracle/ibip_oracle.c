@@ -656,4 +656,187 @@ void or_pc_curve(const int32_t *seq, int64_t N, const int32_t *step_r2, int64_t 
     free(cnt);
 }
 
+/* ------------------------------------------------------------------------
+ * Invasion exactly as Section 2.1 prints it (the paper-literal rule; the
+ * functions above use the frontier rule instead).  The state is an inlets
+ * image and a working copy of the distance values:
+ *   1. the candidates are the inlets plus their face neighbours (dilation by
+ *      a cross, i.e. a structuring element of radius 1);
+ *   2. the largest distance value over the candidates is found, and every
+ *      candidate holding it is an insertion point of this step (all tied
+ *      maxima at once);
+ *   3. at each insertion point c a sphere of integer radius R = trunc(dt)
+ *      (footnote 1; dt = sqrt(dt2)) is inserted: every pore voxel p with
+ *      |p - c|^2 <= R^2 not invaded before gets the step number;
+ *   4. the insertion points join the inlets and their distance values are
+ *      set to zero, so they are not chosen again.
+ * The loop ends when the largest candidate value is zero.
+ * Readings where the text is silent: the inlets start as every voxel of the
+ * inlet face; a sphere is the set of voxels within distance R (a ball
+ * structuring element of radius R), written only into pore voxels (when dt
+ * is an integer the ball reaches the nearest solid voxel); steps whose
+ * spheres meet no uninvaded voxel still count.
+ * Outputs: seq; cstep[v] = the step at which v was an insertion point (0 if
+ * never); per step the squared radius R^2 and the number of insertion
+ * points.
+ * ---------------------------------------------------------------------- */
+
+/* floor(sqrt(v)) for 0 <= v < 2^31, exact */
+static int64_t isqrt_floor(int64_t v)
+{
+    int64_t r = (int64_t)sqrt((double)v);
+    while (r > 0 && r * r > v) r--;
+    while ((r + 1) * (r + 1) <= v) r++;
+    return r;
+}
+
+/* step k's sphere of squared radius rr at c, pore voxels only */
+static void stamp_literal(const uint8_t *img, int32_t *seq, int nx, int ny, int nz, int64_t c, int64_t rr,
+                          int32_t k)
+{
+    int64_t cx, cy, cz;
+    coords(c, ny, nz, &cx, &cy, &cz);
+    int64_t r = isqrt_floor(rr);
+    int64_t x0 = cx - r < 0 ? 0 : cx - r, x1 = cx + r > nx - 1 ? nx - 1 : cx + r;
+    int64_t y0 = cy - r < 0 ? 0 : cy - r, y1 = cy + r > ny - 1 ? ny - 1 : cy + r;
+    int64_t z0 = cz - r < 0 ? 0 : cz - r, z1 = cz + r > nz - 1 ? nz - 1 : cz + r;
+    for (int64_t x = x0; x <= x1; x++)
+        for (int64_t y = y0; y <= y1; y++)
+            for (int64_t z = z0; z <= z1; z++) {
+                int64_t d = (x - cx) * (x - cx) + (y - cy) * (y - cy) + (z - cz) * (z - cz);
+                if (d > rr) continue;
+                int64_t p = lin(x, y, z, ny, nz);
+                if (img[p] && seq[p] == -1) seq[p] = k;
+            }
+}
+
+/* Literal-scan: the steps above with the candidate set rebuilt from the
+ * inlets image over the whole image every step.  O(steps * N). */
+int64_t or_invade_literal_scan(const uint8_t *img, const int32_t *dt2, int nx, int ny, int nz, int inlet,
+                               int64_t max_steps, int32_t *seq, int32_t *cstep, int32_t *step_r2,
+                               int32_t *step_count, int64_t cap, int *status)
+{
+    int64_t N = (int64_t)nx * ny * nz, k = 0;
+    uint8_t *inl = calloc(N ? N : 1, 1), *cand = calloc(N ? N : 1, 1);
+    int32_t *dt = malloc(sizeof(int32_t) * (N ? N : 1));
+    for (int64_t v = 0; v < N; v++) {
+        int64_t x, y, z;
+        coords(v, ny, nz, &x, &y, &z);
+        seq[v] = img[v] ? -1 : 0;
+        cstep[v] = 0;
+        dt[v] = dt2[v];
+        inl[v] = (uint8_t)on_face(x, y, z, nx, ny, nz, inlet);
+    }
+    *status = OR_OK;
+    for (;;) {
+        /* 1: inlets dilated by a cross */
+        for (int64_t v = 0; v < N; v++) {
+            int64_t x, y, z;
+            coords(v, ny, nz, &x, &y, &z);
+            int c = inl[v];
+            for (int d = 0; d < 6 && !c; d++) {
+                int64_t a = x + NB[d][0], b = y + NB[d][1], e = z + NB[d][2];
+                if (a < 0 || b < 0 || e < 0 || a >= nx || b >= ny || e >= nz) continue;
+                c = inl[lin(a, b, e, ny, nz)];
+            }
+            cand[v] = (uint8_t)c;
+        }
+        /* 2: the largest value under the candidates */
+        int32_t best = 0;
+        for (int64_t v = 0; v < N; v++)
+            if (cand[v] && dt[v] > best) best = dt[v];
+        if (best == 0) break;
+        if (k >= max_steps) { *status = OR_STEP_LIMIT; break; }
+        k++;
+        int64_t R = isqrt_floor(best), count = 0;
+        /* 3: a sphere at every maximum */
+        for (int64_t v = 0; v < N; v++) {
+            if (!cand[v] || dt[v] != best) continue;
+            stamp_literal(img, seq, nx, ny, nz, v, R * R, (int32_t)k);
+            cstep[v] = (int32_t)k;
+            count++;
+        }
+        /* 4: the insertion points join the inlets; their values drop to 0 */
+        for (int64_t v = 0; v < N; v++)
+            if (cstep[v] == k) { inl[v] = 1; dt[v] = 0; }
+        if (k <= cap) {
+            step_r2[k - 1] = (int32_t)(R * R);
+            step_count[k - 1] = (int32_t)count;
+        }
+    }
+    free(inl);
+    free(cand);
+    free(dt);
+    return k;
+}
+
+/* Literal-queue: the same process with every voxel queued once, when it
+ * first becomes a candidate, in a max-heap on its distance value.  A step
+ * pops every queued voxel holding the largest value before it queues the
+ * neighbours of its insertion points, so voxels that become candidates
+ * during step k are first examined at step k + 1, as in the scan. */
+int64_t or_invade_literal_queue(const uint8_t *img, const int32_t *dt2, int nx, int ny, int nz, int inlet,
+                                int64_t max_steps, int32_t *seq, int32_t *cstep, int32_t *step_r2,
+                                int32_t *step_count, int64_t cap, int *status)
+{
+    int64_t N = (int64_t)nx * ny * nz, k = 0;
+    uint8_t *queued = calloc(N ? N : 1, 1);
+    int64_t *pts = malloc(sizeof(int64_t) * (N ? N : 1));
+    heap_t h = {0};
+    for (int64_t v = 0; v < N; v++) {
+        seq[v] = img[v] ? -1 : 0;
+        cstep[v] = 0;
+    }
+    /* the inlet face and its face neighbours; zero values never win */
+    for (int64_t v = 0; v < N; v++) {
+        int64_t x, y, z;
+        coords(v, ny, nz, &x, &y, &z);
+        if (!on_face(x, y, z, nx, ny, nz, inlet)) continue;
+        for (int d = -1; d < 6; d++) {
+            int64_t a = x, b = y, e = z;
+            if (d >= 0) { a += NB[d][0]; b += NB[d][1]; e += NB[d][2]; }
+            if (a < 0 || b < 0 || e < 0 || a >= nx || b >= ny || e >= nz) continue;
+            int64_t u = lin(a, b, e, ny, nz);
+            if (queued[u] || dt2[u] == 0) continue;
+            queued[u] = 1;
+            hpush(&h, hkey(dt2[u], u));
+        }
+    }
+    *status = OR_OK;
+    while (h.n > 0) {
+        int32_t best = (int32_t)(h.a[0] >> 32);
+        if (k >= max_steps) { *status = OR_STEP_LIMIT; break; }
+        k++;
+        int64_t R = isqrt_floor(best), n = 0;
+        while (h.n > 0 && (int32_t)(h.a[0] >> 32) == best) {
+            uint64_t key = hpop(&h);
+            pts[n++] = (int64_t)(0xffffffffu - (uint32_t)(key & 0xffffffffu));
+        }
+        for (int64_t q = 0; q < n; q++) {
+            stamp_literal(img, seq, nx, ny, nz, pts[q], R * R, (int32_t)k);
+            cstep[pts[q]] = (int32_t)k;
+        }
+        for (int64_t q = 0; q < n; q++) {
+            int64_t x, y, z;
+            coords(pts[q], ny, nz, &x, &y, &z);
+            for (int d = 0; d < 6; d++) {
+                int64_t a = x + NB[d][0], b = y + NB[d][1], e = z + NB[d][2];
+                if (a < 0 || b < 0 || e < 0 || a >= nx || b >= ny || e >= nz) continue;
+                int64_t u = lin(a, b, e, ny, nz);
+                if (queued[u] || dt2[u] == 0) continue;
+                queued[u] = 1;
+                hpush(&h, hkey(dt2[u], u));
+            }
+        }
+        if (k <= cap) {
+            step_r2[k - 1] = (int32_t)(R * R);
+            step_count[k - 1] = (int32_t)n;
+        }
+    }
+    free(h.a);
+    free(queued);
+    free(pts);
+    return k;
+}
+
 int or_abi_version(void) { return 1; }
