@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--budget-gb", type=float, default=64.0, help="serve: device arena of the server")
     ap.add_argument("--slots", type=int, default=64, help="serve: worker slots")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rule", choices=["frontier", "paper"], default="frontier",
+                    help="invasion rule: the frontier rule, or Section 2.1 as printed (all ties, trunc radius)")
     ap.add_argument("--mio-levels", type=int, default=40)
     return ap.parse_args()
 
@@ -439,7 +441,10 @@ def run_ours(args, rank, world):
 
     def step(image):
         d = ctx.edt(image, out=dt2)
-        s, rr, cc, K, st = ctx.invade(image, d, inlet=w.inlet, seq=seq, step_r2=r2, step_centre=cen)
+        if args.rule == "paper":
+            s, _, rr, _, K, st = ctx.invade_literal(image, d, inlet=w.inlet)
+        else:
+            s, rr, cc, K, st = ctx.invade(image, d, inlet=w.inlet, seq=seq, step_r2=r2, step_centre=cen)
         so = ctx.trapping(s, w.outlet)[1] if w.outlet is not None else s
         S, P, _ = ctx.pc_curve(so, rr, w.voxel_m, w.sigma, w.theta_deg)
         lev, cnt = ctx.morph_drainage(image, d, levels, inlet=w.inlet)
@@ -545,7 +550,8 @@ def run_ours(args, rank, world):
         "vs_baseline": None,
         "dtype": "int32",
         "data": "synthetic",
-        "config": {"workload": w.name, "shape": list(img_h.shape), "porosity": float(npore / N),
+        "config": {"workload": w.name if args.rule == "frontier" else w.name + "_paper_rule",
+                   "shape": list(img_h.shape), "porosity": float(npore / N),
                    "inlet": "x0", "outlet": "x1" if w.outlet is not None else None, "mio_levels": len(levels),
                    "l2": "flushed between steps (256 MB write)", "parallelism": "replicas%d" % world},
         "invasion_steps": K,
@@ -567,10 +573,13 @@ def run_ours(args, rank, world):
 
 # ------------------------------------------------------------ oracle ----
 
-def oracle_pass(w, levels):
+def oracle_pass(w, levels, rule="frontier"):
     import oracle as O
     d = O.edt(w.image)
-    seq, r2, cen, st, K = O.invade(w.image, d, inlet=w.inlet)
+    if rule == "paper":
+        seq, _, r2, _, st, K = O.invade_literal(w.image, d, inlet=w.inlet)
+    else:
+        seq, r2, cen, st, K = O.invade(w.image, d, inlet=w.inlet)
     so = O.trapping(seq, w.outlet)[1] if w.outlet is not None else seq
     O.pc_curve(so, r2, w.voxel_m, w.sigma, w.theta_deg)
     O.morph_drainage(w.image, d, levels, inlet=w.inlet)
@@ -579,12 +588,12 @@ def oracle_pass(w, levels):
 
 def cpu_baseline(args, w, levels):
     t = time.perf_counter()
-    oracle_pass(w, levels)
+    oracle_pass(w, levels, args.rule)
     t = time.perf_counter() - t
     return {"value": w.image.size / t, "unit": "voxels/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": "one full pass of the %s workload (EDT-sep, invade-heap, trap-UF, Pc, "
-                      "opening by EDT at %d radii); invade-heap and trap-UF are single-threaded, "
-                      "the EDT passes use OpenMP on all cores" % (w.name, len(levels)),
+            "sample": "one full pass of the %s workload (EDT-sep, %s, trap-UF, Pc, "
+                      "opening by EDT at %d radii); the invasion and trap-UF are single-threaded, "
+                      "the EDT passes use OpenMP on all cores" % (w.name, "literal-queue" if args.rule == "paper" else "invade-heap", len(levels)),
             "seconds": t}
 
 
@@ -647,11 +656,11 @@ def run_reference(args, rank, world):
     maxd = int(O.edt(w.image)[w.image == 1].max())
     levels = synth.mio_levels(maxd, args.mio_levels)
     for _ in range(args.warmup):
-        oracle_pass(w, levels)
+        oracle_pass(w, levels, args.rule)
     ts = []
     for _ in range(args.steps):
         t = time.perf_counter()
-        K = oracle_pass(w, levels)
+        K = oracle_pass(w, levels, args.rule)
         ts.append(time.perf_counter() - t)
     s = sum(ts) / len(ts)
     v = w.image.size / s
@@ -659,7 +668,8 @@ def run_reference(args, rank, world):
             "bit-exact vs oracle)", "value": v, "unit": "voxels/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": s * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": w.name, "shape": list(w.image.shape), "mio_levels": len(levels)},
+            "config": {"workload": w.name if args.rule == "frontier" else w.name + "_paper_rule",
+                       "shape": list(w.image.shape), "mio_levels": len(levels)},
             "invasion_steps": K,
             "cpu_baseline": {"value": v, "unit": "voxels/s", "cores": os.cpu_count(), "kind": "oracle",
                              "sample": "one full pass of the %s workload per step" % w.name},

@@ -137,6 +137,28 @@ IBIP_API int ibip_invade(ibip_ctx *ctx, const uint8_t *image, const int32_t *dt2
                 int inlet, int64_t max_steps, int32_t *seq, int32_t *step_r2,
                 int32_t *step_centre, int64_t capacity_steps, int64_t *h_n_steps);
 
+/* The invasion exactly as Section 2.1 prints it (the "paper-literal" rule;
+ * ibip_invade uses the frontier rule instead).  The inlets start as every
+ * voxel of the `inlet` face.  Step k = 1, 2, ...: the candidates are the
+ * inlets plus their face neighbours; every candidate holding the largest
+ * dt2 is an insertion point of step k (all tied maxima at once); around each
+ * one, every pore voxel p with |p - c|^2 <= R^2, R = floor(sqrt(dt2)) (the
+ * truncated integer radius of footnote 1), that no earlier step invaded
+ * gets k; the insertion points then join the inlets and their value is set
+ * to zero.  Stops when the largest candidate value is zero, or after
+ * max_steps steps.
+ *   image, dt2, dims, inlet, max_steps, seq: as in ibip_invade.
+ *   cstep:       int32[N] output: the step at which each voxel was an
+ *                insertion point, 0 if never.
+ *   step_r2:     int32[capacity_steps] output: R^2 of each step.
+ *   step_count:  int32[capacity_steps] output: insertion points of each step.
+ *   h_n_steps:   host int64 output: steps K.
+ * Synchronous.  Status conventions as ibip_invade (capacity_steps = number
+ * of pore voxels is always enough). */
+IBIP_API int ibip_invade_literal(ibip_ctx *ctx, const uint8_t *image, const int32_t *dt2, ibip_dims dims,
+                                 int inlet, int64_t max_steps, int32_t *seq, int32_t *cstep, int32_t *step_r2,
+                                 int32_t *step_count, int64_t capacity_steps, int64_t *h_n_steps);
+
 /* Defending-phase trapping (Section 2.2.3).  A voxel invaded at step k is
  * trapped when no 6-path through pore voxels whose sequence value is >= k
  * (never-invaded pore counting as +infinity) joins it to a pore voxel on the

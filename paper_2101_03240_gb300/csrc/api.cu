@@ -301,6 +301,32 @@ int ibip_invade(ibip_ctx *ctx, const uint8_t *image, const int32_t *dt2, ibip_di
     return IBIP_OK;
 }
 
+int ibip_invade_literal(ibip_ctx *ctx, const uint8_t *image, const int32_t *dt2, ibip_dims dims, int inlet,
+                        int64_t max_steps, int32_t *seq, int32_t *cstep, int32_t *step_r2, int32_t *step_count,
+                        int64_t capacity_steps, int64_t *h_n_steps)
+{
+    if (!ctx || !image || !seq || !cstep || !h_n_steps || !dims_ok(dims) || !face_ok(inlet) || max_steps < 0 ||
+        capacity_steps < 0 || (capacity_steps > 0 && (!step_r2 || !step_count)))
+        return IBIP_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    *h_n_steps = 0;
+    const int32_t *d = dt2;
+    if (!d) {
+        int32_t *t = (int32_t *)ibip_scratch(ctx, SC_DT2, (size_t)nvox(dims) * sizeof(int32_t));
+        if (!t) return IBIP_ERR_OOM;
+        int st = ibip_edt_launch(ctx, image, dims, t);
+        if (st) return st;
+        d = t;
+    }
+    int64_t out[2] = {0, 0};
+    int st = ibip_literal_run(ctx, d, dims, inlet, max_steps, seq, cstep, step_r2, step_count, capacity_steps, out);
+    if (st) return st;
+    *h_n_steps = out[0];
+    if (out[1] != IBIP_OK) return (int)out[1];
+    if (out[0] > capacity_steps) return IBIP_ERR_ARG;
+    return IBIP_OK;
+}
+
 int ibip_trapping(ibip_ctx *ctx, const int32_t *seq, ibip_dims dims, int outlet, int rerank, uint8_t *trapped,
                   int32_t *seq_out)
 {

@@ -31,6 +31,7 @@ enum ScratchSlot {
     SC_BARENA,    // batched invasion: per-image ranks, bit-planes, bitmaps
     SC_BJOBS,     // batched invasion: job table
     SC_BDT2,      // batched invasion: EDTs of images given without one
+    SC_LIT,       // paper-literal invasion: bucket lists, counters, bit-plane
     SC_NSLOTS
 };
 
@@ -116,6 +117,12 @@ struct IbipMaximinJob {
     int32_t *M;
 };
 int ibip_maximin_multi(ibip_ctx *ctx, int n, const IbipMaximinJob *jobs, int max_rounds);
+// Pore statistics of a dt2 image: stats[0] = largest finite value, [1] =
+// pore voxels, [2] = 1 if any value is infinite (stats zeroed by the caller).
+int ibip_stats_launch(ibip_ctx *ctx, const int32_t *dt2, int64_t N, int *stats);
+// Paper-literal invasion (literal.cu); h_out = [steps, status].
+int ibip_literal_run(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, int64_t max_steps, int32_t *seq,
+                     int32_t *cstep, int32_t *step_r2, int32_t *step_count, int64_t cap, int64_t *h_out);
 // Scans.
 int ibip_scan_excl_i32(ibip_ctx *ctx, const int32_t *in, int32_t *out, int64_t n);
 int ibip_scan_incl_i32(ibip_ctx *ctx, const int32_t *in, int32_t *out, int64_t n);

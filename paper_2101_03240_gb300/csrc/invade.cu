@@ -1343,6 +1343,13 @@ int ibip_invade_run(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, i
     return IBIP_OK;
 }
 
+int ibip_stats_launch(ibip_ctx *ctx, const int32_t *dt2, int64_t N, int *stats)
+{
+    k_stats<<<ctx->sm_count * 8, 256, 0, ctx->stream>>>(dt2, N, stats);
+    IBIP_LAUNCH(ctx);
+    return IBIP_OK;
+}
+
 // ------------------------------------------------------------- batched --
 
 int ibip_invade_batch_run(ibip_ctx *ctx, int n, IbipBatchItem *it)

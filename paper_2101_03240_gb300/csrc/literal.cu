@@ -1,0 +1,354 @@
+// literal.cu -- the invasion exactly as Section 2.1 prints it (the
+// paper-literal rule of ibip_invade_literal):
+//   candidates = the inlets plus their face neighbours; every candidate
+//   holding the largest distance value is an insertion point of the step
+//   (all tied maxima at once); a sphere of integer radius R = trunc(dt)
+//   (footnote 1) is written, step number k, into every pore voxel within
+//   distance R that no earlier step invaded; the insertion points join the
+//   inlets and their value drops to zero.
+//
+// GPU design.  Each pore voxel is queued once, when it first becomes a
+// candidate, into the list of its distance value ("bucket"; buckets are
+// numbered by decreasing value and own consecutive ranges of one list array
+// sized by a histogram).  A step takes the highest non-empty bucket, and
+// every entry queued there before the step is an insertion point: the step
+// consumes the bucket's whole pending range, stamps the spheres of all its
+// points in parallel, then queues their uninvaded face neighbours (entries
+// queued now are examined from the next step on, as in the definition).
+// One persistent CTA of 1024 threads runs the steps, with the buckets'
+// counters and a bitmap of non-empty buckets in shared memory (up to ~10k
+// distinct values); spheres are written with fire-and-forget atomic minima,
+// so a step never waits on a read of the sequence image.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace {
+
+constexpr int kLT = 1024;                 // threads of the step kernel
+constexpr size_t kLitSmem = 160 * 1024;   // bucket bookkeeping kept in shared memory up to this
+
+struct Lit {
+    int nx, ny, nz, inlet;
+    int64_t N;
+    const int32_t *dt2;
+    int32_t *seq, *cstep, *step_r2, *step_count;
+    int64_t cap, max_steps;
+    int npore;
+    uint32_t *queued;      // one bit per voxel: ever queued
+    int32_t *list;         // [npore]: bucket b owns [bstart[b], bstart[b] + size of b)
+    const int32_t *bstart; // [B]
+    const int32_t *bval;   // [B] distance value of bucket b (decreasing in b)
+    int32_t *tail;         // [B] entries queued so far
+    int32_t *head;         // [B] entries consumed so far
+    unsigned long long *ne;   // [ceil(B / 64)] non-empty buckets
+    const int32_t *incl;   // incl[v] = number of present values <= v (bucket of v = B - incl[v])
+    int B, hasinf;
+    int64_t *out;          // [0] steps, [1] status
+};
+
+__device__ __forceinline__ int bucket_of(const Lit &a, int v) { return a.hasinf ? 0 : a.B - __ldg(a.incl + v); }
+
+// Bucket bookkeeping: in shared memory when the buckets fit (SMEM), else in
+// the global arrays of Lit.
+struct Book {
+    int32_t *tail, *head;
+    const int32_t *bstart, *bval;
+    unsigned long long *ne;
+};
+
+// queue voxel u if it is pore and was never queued
+__device__ __forceinline__ void enqueue(const Lit &a, const Book &k, int64_t u)
+{
+    const int v = __ldg(a.dt2 + u);
+    if (v == 0) return;
+    const uint32_t bit = 1u << (u & 31);
+    if (atomicOr(a.queued + (u >> 5), bit) & bit) return;
+    const int b = bucket_of(a, v);
+    const int pos = atomicAdd(k.tail + b, 1);
+    a.list[k.bstart[b] + pos] = (int32_t)u;
+    atomicOr(k.ne + (b >> 6), 1ull << (b & 63));
+}
+
+__device__ __forceinline__ void coords(const Lit &a, uint32_t v, int &x, int &y, int &z)
+{
+    z = (int)(v % (uint32_t)a.nz);
+    const uint32_t r = v / (uint32_t)a.nz;
+    y = (int)(r % (uint32_t)a.ny);
+    x = (int)(r / (uint32_t)a.ny);
+}
+
+// the inlet face and its face neighbours are the first candidates
+__global__ void k_lit_seed(Lit a)
+{
+    const Book bk{a.tail, a.head, a.bstart, a.bval, a.ne};
+    const int f = a.inlet, ax = f >> 1;
+    const int n0 = ax == 0 ? a.ny : a.nx, n1 = ax == 2 ? a.ny : a.nz;   // the face's two extents
+    const int fixed = (f & 1) ? (ax == 0 ? a.nx : ax == 1 ? a.ny : a.nz) - 1 : 0;
+    const int64_t nf = (int64_t)n0 * n1;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += (int64_t)gridDim.x * blockDim.x) {
+        const int p = (int)(i / n1), q = (int)(i % n1);
+        int x, y, z;
+        if (ax == 0) { x = fixed; y = p; z = q; }
+        else if (ax == 1) { x = p; y = fixed; z = q; }
+        else { x = p; y = q; z = fixed; }
+        const int dx[7] = {0, -1, 1, 0, 0, 0, 0}, dy[7] = {0, 0, 0, -1, 1, 0, 0}, dz[7] = {0, 0, 0, 0, 0, -1, 1};
+        for (int d = 0; d < 7; d++) {
+            const int u0 = x + dx[d], u1 = y + dy[d], u2 = z + dz[d];
+            if (u0 < 0 || u1 < 0 || u2 < 0 || u0 >= a.nx || u1 >= a.ny || u2 >= a.nz) continue;
+            enqueue(a, bk, d_lin(u0, u1, u2, a.ny, a.nz));
+        }
+    }
+}
+
+// The steps.  During the run an uninvaded pore voxel holds INT32_MAX, so a
+// sphere writes min(seq, k) with fire-and-forget atomics (steps only grow,
+// so the minimum is the first step that covered the voxel); k_lit_final
+// turns the remaining INT32_MAX back into -1.
+template <bool SMEM>
+__global__ void __launch_bounds__(kLT, 1) k_lit_steps(Lit a)
+{
+    extern __shared__ unsigned long long s_lit[];
+    __shared__ int s_b, s_h, s_n, s_stop;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int nw = (a.B + 63) >> 6;
+    Book bk{a.tail, a.head, a.bstart, a.bval, a.ne};
+    if (SMEM) {
+        unsigned long long *ne = s_lit;
+        int32_t *t = (int32_t *)(s_lit + nw);
+        for (int i = tid; i < nw; i += kLT) ne[i] = a.ne[i];
+        for (int i = tid; i < a.B; i += kLT) {
+            t[i] = a.tail[i];
+            t[a.B + i] = a.head[i];
+            t[2 * a.B + i] = a.bstart[i];
+            t[3 * a.B + i] = a.bval[i];
+        }
+        bk = Book{t, t + a.B, t + 2 * a.B, t + 3 * a.B, ne};
+        __syncthreads();
+    }
+    int64_t k = 0;
+    for (;;) {
+        if (tid < 32) {
+            // highest non-empty bucket: first set bit of the bitmap
+            int b = -1;
+            for (int w0 = 0; w0 < nw && b < 0; w0 += 32) {
+                const int w = w0 + lane;
+                const unsigned long long m = w < nw ? *(volatile unsigned long long *)(bk.ne + w) : 0ull;
+                const unsigned bal = __ballot_sync(0xffffffffu, m != 0ull);
+                if (bal) {
+                    const int l = __ffs(bal) - 1;
+                    const unsigned long long ml = __shfl_sync(0xffffffffu, m, l);
+                    b = ((w0 + l) << 6) + __ffsll((long long)ml) - 1;
+                }
+            }
+            if (lane == 0) {
+                int stop = 0;
+                if (b < 0) stop = 1;
+                else if (k >= a.max_steps) stop = 2;
+                else if (k >= a.npore) stop = 3;   // every step consumes a queued voxel: cannot happen
+                s_stop = stop;
+                if (!stop) {
+                    const int h = bk.head[b], t = *(volatile int *)(bk.tail + b);
+                    bk.head[b] = t;
+                    // consumed: the bucket is empty until this step queues into it
+                    atomicAnd(bk.ne + (b >> 6), ~(1ull << (b & 63)));
+                    s_b = b; s_h = h; s_n = t - h;
+                }
+            }
+        }
+        __syncthreads();
+        if (s_stop) break;
+        k++;
+        const int b = s_b, n = s_n;
+        const int32_t *pts = a.list + bk.bstart[b] + s_h;
+        const int v = bk.bval[b];
+        const int R = d_isqrt(v);                              // trunc(dt)
+        const int64_t RR = (int64_t)R * R;
+        const int Re = min(R, max(a.nx, max(a.ny, a.nz)));     // reach inside the image
+        const int side = 2 * Re + 1;
+        const int64_t rows = (int64_t)side * side;
+        // spheres: one item per (point, row of the bounding square)
+        for (int64_t it = tid; it < (int64_t)n * rows; it += kLT) {
+            const int q = (int)(it / rows);
+            const int r = (int)(it - (int64_t)q * rows);
+            const int ddx = r / side - Re, ddy = r % side - Re;
+            const int64_t rem = RR - (int64_t)ddx * ddx - (int64_t)ddy * ddy;
+            if (rem < 0) continue;
+            int cx, cy, cz;
+            coords(a, (uint32_t)pts[q], cx, cy, cz);
+            const int x = cx + ddx, y = cy + ddy;
+            if (x < 0 || y < 0 || x >= a.nx || y >= a.ny) continue;
+            const int hz = d_isqrt((int)min(rem, (int64_t)IBIP_INF32));
+            const int z0 = max(0, cz - hz), z1 = min(a.nz - 1, cz + hz);
+            int32_t *row = a.seq + d_lin(x, y, 0, a.ny, a.nz);
+            for (int z = z0; z <= z1; z++) atomicMin(row + z, (int32_t)k);
+        }
+        // the points join the inlets: mark them, queue their neighbours
+        for (int64_t it = tid; it < (int64_t)n * 6; it += kLT) {
+            const int q = (int)(it / 6), d = (int)(it - (int64_t)q * 6);
+            const uint32_t c = (uint32_t)pts[q];
+            int x, y, z;
+            coords(a, c, x, y, z);
+            if (d == 0) a.cstep[c] = (int32_t)k;
+            x += d == 0 ? -1 : d == 1 ? 1 : 0;
+            y += d == 2 ? -1 : d == 3 ? 1 : 0;
+            z += d == 4 ? -1 : d == 5 ? 1 : 0;
+            if (x < 0 || y < 0 || z < 0 || x >= a.nx || y >= a.ny || z >= a.nz) continue;
+            enqueue(a, bk, d_lin(x, y, z, a.ny, a.nz));
+        }
+        if (tid == 0 && k <= a.cap) {
+            a.step_r2[k - 1] = (int32_t)RR;
+            a.step_count[k - 1] = n;
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        a.out[0] = k;
+        a.out[1] = s_stop == 2 ? IBIP_ERR_STEP_LIMIT : (s_stop == 3 ? IBIP_ERR_BOUNDS : IBIP_OK);
+    }
+}
+
+__global__ void k_lit_final(int32_t *seq, int64_t N)
+{
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (int64_t)gridDim.x * blockDim.x)
+        if (seq[v] == IBIP_INF32) seq[v] = -1;
+}
+
+__global__ void k_lit_init(const int32_t *__restrict__ dt2, int64_t N, int32_t *seq, int32_t *cstep)
+{
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (int64_t)gridDim.x * blockDim.x) {
+        seq[v] = dt2[v] ? IBIP_INF32 : 0;   // uninvaded pore: see k_lit_steps
+        cstep[v] = 0;
+    }
+}
+
+// presence of each distance value among pore voxels
+__global__ void k_lit_presence(const int32_t *__restrict__ dt2, int64_t N, int32_t *pres)
+{
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (int64_t)gridDim.x * blockDim.x) {
+        const int d = dt2[v];
+        if (d > 0 && d != IBIP_INF32 && pres[d] == 0) pres[d] = 1;
+    }
+}
+
+// voxels per bucket
+__global__ void k_lit_hist(const int32_t *__restrict__ dt2, int64_t N, const int32_t *incl, int B, int hasinf,
+                           int32_t *cnt)
+{
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (int64_t)gridDim.x * blockDim.x) {
+        const int d = dt2[v];
+        if (d == 0) continue;
+        atomicAdd(cnt + (hasinf ? 0 : B - incl[d]), 1);
+    }
+}
+
+// value of each bucket
+__global__ void k_lit_bval(const int32_t *incl, int maxd, int B, int hasinf, int32_t *bval)
+{
+    if (hasinf) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) bval[0] = IBIP_INF32;
+        return;
+    }
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x + 1; v <= maxd; v += gridDim.x * blockDim.x)
+        if (incl[v] != incl[v - 1]) bval[B - incl[v]] = v;
+}
+
+}  // namespace
+
+int ibip_literal_run(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, int64_t max_steps, int32_t *seq,
+                     int32_t *cstep, int32_t *step_r2, int32_t *step_count, int64_t cap, int64_t *h_out)
+{
+    cudaStream_t s = ctx->stream;
+    const int64_t N = nvox(d);
+    const int gs = ctx->sm_count * 8;
+    int *stats = (int *)ibip_scratch(ctx, SC_SMALL, kSmallBytes);
+    if (!stats) return IBIP_ERR_OOM;
+    int *h = (int *)ctx->h_pinned;
+    ibip_prof_begin(ctx, IBIP_K_RANK);
+    // largest finite value, pore count, whether values are infinite
+    cudaMemsetAsync(stats, 0, 3 * sizeof(int), s);
+    ibip_stats_launch(ctx, dt2, N, stats);
+    cudaMemcpyAsync(h, stats, 3 * sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return IBIP_ERR_CUDA;
+    const int maxd = h[0], npore = h[1], hasinf = h[2];
+    k_lit_init<<<gs, 256, 0, s>>>(dt2, N, seq, cstep);
+    IBIP_LAUNCH(ctx);
+    if (npore == 0) {
+        ibip_prof_end(ctx, IBIP_K_RANK);
+        h_out[0] = 0;
+        h_out[1] = IBIP_OK;
+        return ibip_cuda_status(cudaStreamSynchronize(s));
+    }
+    // buckets: distinct values in decreasing order
+    int32_t *incl = (int32_t *)ibip_scratch(ctx, SC_PRES, ((size_t)maxd + 2) * sizeof(int32_t));
+    if (!incl) return IBIP_ERR_OOM;
+    int B = 1;
+    if (!hasinf) {
+        cudaMemsetAsync(incl, 0, ((size_t)maxd + 1) * sizeof(int32_t), s);
+        k_lit_presence<<<gs, 256, 0, s>>>(dt2, N, incl);
+        IBIP_LAUNCH(ctx);
+        int st = ibip_scan_incl_i32(ctx, incl, incl, (int64_t)maxd + 1);
+        if (st) return st;
+        cudaMemcpyAsync(h, incl + maxd, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) return IBIP_ERR_CUDA;
+        B = h[0];
+    }
+    const int nw = (B + 63) / 64;
+    // one arena: list | bstart | bval | tail | head | cnt | ne | queued | out
+    const size_t planes = ((size_t)N + 31) / 32;
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t o_list = 0, o_bstart = o_list + up((size_t)npore * 4), o_bval = o_bstart + up((size_t)B * 4),
+                 o_tail = o_bval + up((size_t)B * 4), o_head = o_tail + up((size_t)B * 4),
+                 o_cnt = o_head + up((size_t)B * 4), o_ne = o_cnt + up((size_t)B * 4),
+                 o_q = o_ne + up((size_t)nw * 8), o_out = o_q + up(planes * 4), total = o_out + up(64);
+    char *w = (char *)ibip_scratch(ctx, SC_LIT, total);
+    if (!w) return IBIP_ERR_OOM;
+    Lit a;
+    a.nx = d.nx; a.ny = d.ny; a.nz = d.nz; a.inlet = inlet; a.N = N;
+    a.dt2 = dt2; a.seq = seq; a.cstep = cstep; a.step_r2 = step_r2; a.step_count = step_count;
+    a.cap = cap; a.max_steps = max_steps; a.npore = npore;
+    a.list = (int32_t *)(w + o_list);
+    a.bstart = (const int32_t *)(w + o_bstart);
+    a.bval = (const int32_t *)(w + o_bval);
+    a.tail = (int32_t *)(w + o_tail);
+    a.head = (int32_t *)(w + o_head);
+    a.ne = (unsigned long long *)(w + o_ne);
+    a.queued = (uint32_t *)(w + o_q);
+    a.incl = incl;
+    a.B = B; a.hasinf = hasinf;
+    a.out = (int64_t *)(w + o_out);
+    int32_t *cnt = (int32_t *)(w + o_cnt);
+    // tail, head, cnt and ne are contiguous: clear them at once, and the plane
+    cudaMemsetAsync(w + o_tail, 0, o_q - o_tail, s);
+    cudaMemsetAsync(w + o_q, 0, planes * 4, s);
+    k_lit_hist<<<gs, 256, 0, s>>>(dt2, N, incl, B, hasinf, cnt);
+    IBIP_LAUNCH(ctx);
+    int st = ibip_scan_excl_i32(ctx, cnt, (int32_t *)a.bstart, B);
+    if (st) return st;
+    k_lit_bval<<<std::max(1, std::min(gs, (maxd + 255) / 256)), 256, 0, s>>>(incl, maxd, B, hasinf,
+                                                                             (int32_t *)a.bval);
+    IBIP_LAUNCH(ctx);
+    const int nface = (inlet >> 1) == 0 ? d.ny * d.nz : (inlet >> 1) == 1 ? d.nx * d.nz : d.nx * d.ny;
+    k_lit_seed<<<std::max(1, std::min(gs, (nface + 255) / 256)), 256, 0, s>>>(a);
+    IBIP_LAUNCH(ctx);
+    ibip_prof_end(ctx, IBIP_K_RANK);
+    ibip_prof_begin(ctx, IBIP_K_INVADE);
+    const size_t book = (size_t)nw * 8 + (size_t)B * 16;
+    if (book <= kLitSmem) {
+        cudaFuncSetAttribute(k_lit_steps<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLitSmem);
+        k_lit_steps<true><<<1, kLT, book, s>>>(a);
+    } else {
+        k_lit_steps<false><<<1, kLT, 0, s>>>(a);
+    }
+    IBIP_LAUNCH(ctx);
+    k_lit_final<<<gs, 256, 0, s>>>(seq, N);
+    IBIP_LAUNCH(ctx);
+    ibip_prof_end(ctx, IBIP_K_INVADE);
+    int64_t *ho = (int64_t *)ctx->h_pinned;
+    cudaMemcpyAsync(ho, a.out, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return ibip_cuda_status(e);
+    h_out[0] = ho[0];
+    h_out[1] = ho[1];
+    return IBIP_OK;
+}

@@ -84,6 +84,7 @@ def _lib():
                 "ibip_invade_stats": (C.c_int, [P, C.POINTER(i64), C.c_int]),
                 "ibip_profile_read": (C.c_int, [P, C.c_int, C.POINTER(dbl), C.POINTER(i64)]),
                 "ibip_job_footprint": (i64, [Dims, C.c_int]),
+                "ibip_invade_literal": (C.c_int, [P, P, P, Dims, C.c_int, i64, P, P, P, P, i64, C.POINTER(i64)]),
                 "ibip_server_create": (C.c_int, [C.POINTER(P), P, C.c_size_t, C.c_int]),
                 "ibip_server_destroy": (C.c_int, [P]),
                 "ibip_server_submit": (C.c_int, [P, C.POINTER(Job), C.POINTER(C.c_uint64)]),
@@ -252,6 +253,28 @@ class Context:
         k = int(K.value)
         kk = min(k, capacity)
         return seq, step_r2[:kk], (step_centre[:kk] if centres else None), k, st
+
+    def invade_literal(self, image, dt2=None, inlet=0, max_steps=None, capacity=None):
+        """The invasion exactly as Section 2.1 prints it (ibip_invade_literal).
+        Returns (seq, cstep, step_r2, step_count, K, status)."""
+        _need(image, torch.uint8, "image")
+        if dt2 is not None:
+            _need(dt2, torch.int32, "dt2")
+        dev, N = image.device, image.numel()
+        cap = N if capacity is None else int(capacity)
+        seq = torch.empty(image.shape, dtype=torch.int32, device=dev)
+        cstep = torch.empty(image.shape, dtype=torch.int32, device=dev)
+        r2 = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+        cnt = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+        k = C.c_int64(0)
+        self._stream()
+        st = _lib().ibip_invade_literal(self._h, _ptr(image), _ptr(dt2), _dims(image.shape), int(inlet),
+                                        N if max_steps is None else int(max_steps), _ptr(seq), _ptr(cstep),
+                                        _ptr(r2), _ptr(cnt), cap, C.byref(k))
+        if st not in (OK, ERR_STEP_LIMIT):
+            raise IbipError("ibip_invade_literal", st)
+        K = int(k.value)
+        return seq, cstep, r2[:min(K, cap)], cnt[:min(K, cap)], K, st
 
     def trapping(self, seq, outlet=1, rerank=False, seq_out=True):
         _need(seq, torch.int32, "seq")
