@@ -439,6 +439,8 @@ def run_ours(args, rank, world):
     cen = torch.empty(N, dtype=torch.int32, device=dev)
     dt2 = torch.empty(img_d.shape, dtype=torch.int32, device=dev)
 
+    eq = [None, None, None]
+
     def step(image):
         d = ctx.edt(image, out=dt2)
         if args.rule == "paper":
@@ -448,6 +450,7 @@ def run_ours(args, rank, world):
         so = ctx.trapping(s, w.outlet)[1] if w.outlet is not None else s
         S, P, _ = ctx.pc_curve(so, rr, w.voxel_m, w.sigma, w.theta_deg)
         lev, cnt = ctx.morph_drainage(image, d, levels, inlet=w.inlet)
+        eq[:] = ctx.equal_saturation(s, lev, K, len(levels))   # Section 3.1.1 check, by counts
         return K, so, S, P
 
     for _ in range(args.warmup):
@@ -555,6 +558,10 @@ def run_ours(args, rank, world):
                    "inlet": "x0", "outlet": "x1" if w.outlet is not None else None, "mio_levels": len(levels),
                    "l2": "flushed between steps (256 MB write)", "parallelism": "replicas%d" % world},
         "invasion_steps": K,
+        "equal_saturation": {"levels": len(levels), "max_diff_frac": max(eq[1]) / npore,
+                             "mean_diff_frac": sum(eq[1]) / len(eq[1]) / npore,
+                             "note": "voxels in exactly one of the opening's level set and the invasion's "
+                                     "matched-count set, over all pore voxels (Section 3.1.1)"},
         "invasion_steps_per_s": K / (prof["invade"][0] / args.steps * 1e-3) if prof["invade"][1] else None,
         "invasion_us_per_step": us_per_step,
         "e2e": {"value": job_rate(N, world, e2e_step * 1e-3), "unit": "voxels/s",

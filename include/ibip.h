@@ -191,6 +191,22 @@ IBIP_API int ibip_morph_drainage(ibip_ctx *ctx, const uint8_t *image, const int3
                         int inlet, const int32_t *h_r2_levels, int32_t n_levels, int32_t *level,
                         int64_t *h_counts);
 
+/* Equal-saturation comparison of an invasion with morphological-opening
+ * drainage (Section 3.1.1, Figure 8), by integer counts.  For opening level
+ * i (0-based): n_i = voxels with 1 <= level <= i + 1; k_i = the smallest
+ * step with #(1 <= seq <= k_i) >= n_i (n_steps if none); diff_i = the number
+ * of voxels in exactly one of {1 <= level <= i + 1} and {1 <= seq <= k_i}.
+ *   seq:      int32[N] sequence image (ibip_invade, ibip_invade_literal, or a
+ *             trapping-corrected seq_out); values above n_steps are ignored.
+ *   level:    int32[N] from ibip_morph_drainage (-1 none, 0 solid, i + 1).
+ *   n_levels: 1..254.
+ *   h_steps, h_count: host int64[n_levels] outputs k_i and n_i, or NULL.
+ *   h_diff:   host int64[n_levels] output diff_i.
+ * Synchronous. */
+IBIP_API int ibip_equal_saturation(ibip_ctx *ctx, const int32_t *seq, const int32_t *level, ibip_dims dims,
+                                   int64_t n_steps, int32_t n_levels, int64_t *h_steps, int64_t *h_diff,
+                                   int64_t *h_count);
+
 /* Saturation and capillary pressure after each step (Sections 2.2.1 and
  * 2.2.2; Washburn relation Pc = -2 sigma cos(theta) / R, Section 2.4.1).
  *   S_k  = (voxels with 1 <= seq <= k) / (all pore voxels, seq != 0);

@@ -189,3 +189,30 @@ def pc_curve(seq, step_r2, voxel_m=5e-6, sigma=0.072, theta_deg=180.0, sat_image
     lib().or_pc_curve(_p(s), s.size, _p(r2), K, float(voxel_m), float(sigma), float(theta_deg),
                       _p(S), _p(P), _p(img))
     return S[:K].copy(), P[:K].copy(), img
+
+
+def equal_saturation(seq, level, n_levels):
+    """Equal-saturation comparison of an invasion with morphological-opening
+    drainage (Section 3.1.1, Figure 8), by integer counts: for opening level
+    i (0-based), n_i = voxels with 1 <= level <= i + 1; k_i = the smallest
+    invasion step whose cumulative invaded count reaches n_i (the last step
+    if none does); diff_i = size of the symmetric difference of
+    {1 <= level <= i + 1} and {1 <= seq <= k_i}.  `level` uses the encoding
+    of morph_drainage (-1 none, 0 solid, i + 1 first level).  Returns
+    (k, diff, n) as int64 arrays of length n_levels."""
+    s = np.asarray(seq).ravel()
+    lv = np.asarray(level).ravel()
+    K = int(s.max()) if s.size else 0
+    K = max(K, 0)
+    cum = np.cumsum(np.bincount(s[s >= 1], minlength=K + 1))   # cum[k] = voxels with 1 <= seq <= k
+    ks, diffs, ns = [], [], []
+    for i in range(n_levels):
+        in_mio = (lv >= 1) & (lv <= i + 1)
+        n = int(in_mio.sum())
+        hit = np.nonzero(cum >= n)[0]
+        k = int(hit[0]) if hit.size else K
+        in_ibip = (s >= 1) & (s <= k)
+        ks.append(k)
+        ns.append(n)
+        diffs.append(int(np.count_nonzero(in_mio != in_ibip)))
+    return np.array(ks, np.int64), np.array(diffs, np.int64), np.array(ns, np.int64)

@@ -457,6 +457,16 @@ int ibip_invade_batched(ibip_ctx *ctx, int32_t n, ibip_job *jobs)
     return first_bad;
 }
 
+int ibip_equal_saturation(ibip_ctx *ctx, const int32_t *seq, const int32_t *level, ibip_dims dims,
+                          int64_t n_steps, int32_t n_levels, int64_t *h_steps, int64_t *h_diff, int64_t *h_count)
+{
+    if (!ctx || !seq || !level || !h_diff || !dims_ok(dims) || n_steps < 0 || n_steps >= (1ll << 31) ||
+        n_levels < 1 || n_levels > 254)
+        return IBIP_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    return ibip_eqsat_launch(ctx, seq, level, dims, n_steps, n_levels, h_steps, h_diff, h_count);
+}
+
 int ibip_pc_curve(ibip_ctx *ctx, const int32_t *seq, ibip_dims dims, const int32_t *step_r2, int64_t n_steps,
                   double voxel_m, double sigma, double theta_deg, float *sat_per_step, float *pc_per_step,
                   float *sat_image)

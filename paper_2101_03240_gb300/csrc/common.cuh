@@ -123,6 +123,9 @@ int ibip_stats_launch(ibip_ctx *ctx, const int32_t *dt2, int64_t N, int *stats);
 // Paper-literal invasion (literal.cu); h_out = [steps, status].
 int ibip_literal_run(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, int64_t max_steps, int32_t *seq,
                      int32_t *cstep, int32_t *step_r2, int32_t *step_count, int64_t cap, int64_t *h_out);
+// Equal-saturation comparison of a sequence image with opening levels.
+int ibip_eqsat_launch(ibip_ctx *ctx, const int32_t *seq, const int32_t *level, ibip_dims d, int64_t K, int L,
+                      int64_t *h_steps, int64_t *h_diff, int64_t *h_count);
 // Scans.
 int ibip_scan_excl_i32(ibip_ctx *ctx, const int32_t *in, int32_t *out, int64_t n);
 int ibip_scan_incl_i32(ibip_ctx *ctx, const int32_t *in, int32_t *out, int64_t n);

@@ -95,6 +95,59 @@ __global__ void k_level_hist(const int32_t *__restrict__ level, int64_t N, int L
     }
 }
 
+// Equal-saturation comparison with the opening (Section 3.1.1, by integer
+// counts).  k_i = the smallest step whose cumulative count cum[k] reaches
+// n_i (cum[K] if none does); one thread per level.
+__global__ void k_eqsat_steps(const int32_t *__restrict__ cum, int64_t K, const int32_t *__restrict__ n, int L,
+                              int32_t *kq)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= L) return;
+    const int32_t want = n[i];
+    int64_t lo = 0, hi = K;   // cum is non-decreasing; cum[0] = 0
+    if (cum[K] < want) { kq[i] = (int32_t)K; return; }
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (cum[mid] >= want) hi = mid; else lo = mid + 1;
+    }
+    kq[i] = (int32_t)lo;
+}
+
+// A voxel is in the opening's set of level i from i = level - 1 on, and in
+// the invasion's matched set from the first i with k_i >= seq on: the two
+// differ on the levels between those two starts.  Difference array over
+// levels, per block in shared memory.
+constexpr int kMaxEqLevels = 256;
+__global__ void k_eqsat(const int32_t *__restrict__ seq, const int32_t *__restrict__ level, int64_t N,
+                        const int32_t *__restrict__ kq, int L, int32_t *dh)
+{
+    __shared__ int32_t s_k[kMaxEqLevels];
+    __shared__ int32_t s_h[kMaxEqLevels + 1];
+    for (int i = threadIdx.x; i < L; i += blockDim.x) s_k[i] = kq[i];
+    for (int i = threadIdx.x; i <= L; i += blockDim.x) s_h[i] = 0;
+    __syncthreads();
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (int64_t)gridDim.x * blockDim.x) {
+        const int lv = level[v], sq = seq[v];
+        const int a = lv >= 1 ? lv - 1 : L;
+        int b = L;
+        if (sq >= 1) {
+            int lo = 0, hi = L;   // first i with k_i >= seq (k is non-decreasing)
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (s_k[mid] >= sq) hi = mid; else lo = mid + 1;
+            }
+            b = lo;
+        }
+        if (a != b) {
+            atomicAdd(s_h + min(a, b), 1);
+            atomicAdd(s_h + max(a, b), -1);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i <= L; i += blockDim.x)
+        if (s_h[i]) atomicAdd(dh + i, s_h[i]);
+}
+
 }  // namespace
 
 int ibip_pc_launch(ibip_ctx *ctx, const int32_t *seq, ibip_dims d, const int32_t *r2, int64_t K, double voxel,
@@ -201,5 +254,45 @@ int ibip_level_counts(ibip_ctx *ctx, const int32_t *level, ibip_dims d, int L, i
     if (e != cudaSuccess) return ibip_cuda_status(e);
     int64_t run = 0;
     for (int i = 0; i < L; i++) { run += h[i + 1]; h_counts[i] = run; }
+    return IBIP_OK;
+}
+
+int ibip_eqsat_launch(ibip_ctx *ctx, const int32_t *seq, const int32_t *level, ibip_dims d, int64_t K, int L,
+                      int64_t *h_steps, int64_t *h_diff, int64_t *h_count)
+{
+    cudaStream_t s = ctx->stream;
+    const int64_t N = nvox(d);
+    const int gs = ctx->sm_count * 8;
+    // layout: cum[K + 2] | lv[L + 2] | kq[L] | dh[L + 1] | npore
+    const size_t words = (size_t)K + 2 + (L + 2) + L + (L + 1) + 1;
+    int32_t *w = (int32_t *)ibip_scratch(ctx, SC_HIST, words * sizeof(int32_t));
+    if (!w) return IBIP_ERR_OOM;
+    int32_t *cum = w, *lv = cum + K + 2, *kq = lv + L + 2, *dh = kq + L, *np = dh + L + 1;
+    cudaMemsetAsync(w, 0, words * sizeof(int32_t), s);
+    k_hist_seq<<<gs, 256, 0, s>>>(seq, N, K, cum, np);
+    IBIP_LAUNCH(ctx);
+    int st = ibip_scan_incl_i32(ctx, cum, cum, K + 1);
+    if (st) return st;
+    k_level_hist<<<gs, 256, 0, s>>>(level, N, L, lv);
+    IBIP_LAUNCH(ctx);
+    st = ibip_scan_incl_i32(ctx, lv + 1, lv + 1, L);   // lv[1 + i] = voxels with 1 <= level <= i + 1
+    if (st) return st;
+    k_eqsat_steps<<<(L + 127) / 128, 128, 0, s>>>(cum, K, lv + 1, L, kq);
+    IBIP_LAUNCH(ctx);
+    k_eqsat<<<gs, 256, 0, s>>>(seq, level, N, kq, L, dh);
+    IBIP_LAUNCH(ctx);
+    int32_t *h = (int32_t *)ctx->h_pinned;   // L <= 254: 3L + 1 words fit the pinned buffer
+    cudaMemcpyAsync(h, lv + 1, (size_t)L * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(h + L, kq, (size_t)L * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(h + 2 * L, dh, ((size_t)L + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return ibip_cuda_status(e);
+    int64_t run = 0;
+    for (int i = 0; i < L; i++) {
+        run += h[2 * L + i];
+        if (h_count) h_count[i] = h[i];
+        if (h_steps) h_steps[i] = h[L + i];
+        h_diff[i] = run;
+    }
     return IBIP_OK;
 }

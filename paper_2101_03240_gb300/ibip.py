@@ -84,6 +84,8 @@ def _lib():
                 "ibip_invade_stats": (C.c_int, [P, C.POINTER(i64), C.c_int]),
                 "ibip_profile_read": (C.c_int, [P, C.c_int, C.POINTER(dbl), C.POINTER(i64)]),
                 "ibip_job_footprint": (i64, [Dims, C.c_int]),
+                "ibip_equal_saturation": (C.c_int, [P, P, P, Dims, i64, i32, C.POINTER(i64), C.POINTER(i64),
+                                                    C.POINTER(i64)]),
                 "ibip_invade_literal": (C.c_int, [P, P, P, Dims, C.c_int, i64, P, P, P, P, i64, C.POINTER(i64)]),
                 "ibip_server_create": (C.c_int, [C.POINTER(P), P, C.c_size_t, C.c_int]),
                 "ibip_server_destroy": (C.c_int, [P]),
@@ -322,6 +324,20 @@ class Context:
             r["K"], r["status"] = K, int(arr[j].status)
             _trim(r, K)
         return res
+
+    def equal_saturation(self, seq, level, n_steps, n_levels):
+        """Equal-saturation comparison with opening levels (Section 3.1.1):
+        returns (k, diff, n) as lists, one entry per level."""
+        _need(seq, torch.int32, "seq")
+        _need(level, torch.int32, "level")
+        L = int(n_levels)
+        k, d, n = (C.c_int64 * L)(), (C.c_int64 * L)(), (C.c_int64 * L)()
+        self._stream()
+        st = _lib().ibip_equal_saturation(self._h, _ptr(seq), _ptr(level), _dims(seq.shape), int(n_steps), L,
+                                          k, d, n)
+        if st != OK:
+            raise IbipError("ibip_equal_saturation", st)
+        return list(k), list(d), list(n)
 
     def pc_curve(self, seq, step_r2, voxel_m=5e-6, sigma=0.072, theta_deg=180.0, sat_image=False):
         _need(seq, torch.int32, "seq")

@@ -1,0 +1,68 @@
+"""Equal-saturation comparison (ibip_equal_saturation) against the oracle's
+definition, on invasions of both rules and their opening levels."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2101_03240_gb300 import synth as S
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2101_03240_gb300 import ibip
+    return ibip.Context(0)
+
+
+def compare(ctx, img, inlet, n_levels, rule):
+    dev = torch.from_numpy(np.ascontiguousarray(img)).cuda()
+    d = ctx.edt(dev)
+    if rule == "paper":
+        seq, _, r2, _, K, st = ctx.invade_literal(dev, d, inlet=inlet)
+    else:
+        seq, r2, cen, K, st = ctx.invade(dev, d, inlet=inlet)
+    dmax = int(d[dev > 0].max().item()) if bool((dev > 0).any()) else 1
+    T = S.mio_levels(min(dmax, 1 << 30), n_levels)
+    lev, cnt = ctx.morph_drainage(dev, d, T, inlet=inlet)
+    k, diff, n = ctx.equal_saturation(seq, lev, K, len(T))
+    rk, rdiff, rn = O.equal_saturation(seq.cpu().numpy(), lev.cpu().numpy(), len(T))
+    assert list(rk) == k and list(rdiff) == diff and list(rn) == n
+    assert n == cnt
+    return k, diff, n
+
+
+@pytest.mark.parametrize("seed", range(10))
+@pytest.mark.parametrize("rule", ["frontier", "paper"])
+def test_equal_saturation_random(ctx, seed, rule):
+    rng = np.random.default_rng(700 + seed)
+    shape = tuple(int(x) for x in rng.integers(6, 40, 3))
+    img = S.blobs(shape, rng.uniform(1.5, 3.0), rng.uniform(0.5, 0.75), rng) if seed % 2 else \
+        S.sphere_pack(shape, int(rng.integers(2, 5)), rng.uniform(0.35, 0.5), rng)
+    compare(ctx, img, seed % 6, int(rng.integers(1, 60)), rule)
+
+
+def test_equal_saturation_blobs48_against_oracle_inputs(ctx):
+    w = S.c1_blobs48()
+    d = O.edt(w.image)
+    seq = O.invade(w.image, d, inlet=0)[0]
+    T = S.mio_levels(int(d[w.image > 0].max()), 40)
+    level = O.morph_drainage(w.image, d, T, inlet=0)[0]
+    k, diff, n = ctx.equal_saturation(torch.from_numpy(seq).cuda(), torch.from_numpy(level).cuda(),
+                                      int(seq.max()), len(T))
+    rk, rdiff, rn = O.equal_saturation(seq, level, len(T))
+    assert list(rk) == k and list(rdiff) == diff and list(rn) == n
+
+
+def test_equal_saturation_edges(ctx):
+    z = np.zeros((4, 5, 6), np.uint8)
+    dev = torch.from_numpy(z).cuda()
+    seq = torch.zeros(z.shape, dtype=torch.int32, device="cuda")
+    k, diff, n = ctx.equal_saturation(seq, seq.clone(), 0, 3)
+    assert k == [0, 0, 0] and diff == [0, 0, 0] and n == [0, 0, 0]
+    compare(ctx, np.ones((5, 4, 7), np.uint8), 0, 5, "frontier")
