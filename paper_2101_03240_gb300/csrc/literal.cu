@@ -19,9 +19,13 @@
 // counters and a bitmap of non-empty buckets in shared memory (up to ~10k
 // distinct values); spheres are written with fire-and-forget atomic minima,
 // so a step never waits on a read of the sequence image.
+#include <cooperative_groups.h>
+
 #include <algorithm>
 
 #include "common.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -41,7 +45,7 @@ struct Lit {
     const int32_t *bval;   // [B] distance value of bucket b (decreasing in b)
     int32_t *tail;         // [B] entries queued so far
     int32_t *head;         // [B] entries consumed so far
-    unsigned long long *ne;   // [ceil(B / 64)] non-empty buckets
+    uint32_t *ne;          // [ceil(B / 32)] non-empty buckets
     const int32_t *incl;   // incl[v] = number of present values <= v (bucket of v = B - incl[v])
     int B, hasinf;
     int64_t *out;          // [0] steps, [1] status
@@ -54,7 +58,7 @@ __device__ __forceinline__ int bucket_of(const Lit &a, int v) { return a.hasinf 
 struct Book {
     int32_t *tail, *head;
     const int32_t *bstart, *bval;
-    unsigned long long *ne;
+    uint32_t *ne;
 };
 
 // queue voxel u if it is pore and was never queued
@@ -67,7 +71,7 @@ __device__ __forceinline__ void enqueue(const Lit &a, const Book &k, int64_t u)
     const int b = bucket_of(a, v);
     const int pos = atomicAdd(k.tail + b, 1);
     a.list[k.bstart[b] + pos] = (int32_t)u;
-    atomicOr(k.ne + (b >> 6), 1ull << (b & 63));
+    atomicOr(k.ne + (b >> 5), 1u << (b & 31));
 }
 
 __device__ __forceinline__ void coords(const Lit &a, uint32_t v, int &x, int &y, int &z)
@@ -108,13 +112,13 @@ __global__ void k_lit_seed(Lit a)
 template <bool SMEM>
 __global__ void __launch_bounds__(kLT, 1) k_lit_steps(Lit a)
 {
-    extern __shared__ unsigned long long s_lit[];
+    extern __shared__ uint32_t s_lit[];
     __shared__ int s_b, s_h, s_n, s_stop;
     const int tid = threadIdx.x, lane = tid & 31;
-    const int nw = (a.B + 63) >> 6;
+    const int nw = (a.B + 31) >> 5;
     Book bk{a.tail, a.head, a.bstart, a.bval, a.ne};
     if (SMEM) {
-        unsigned long long *ne = s_lit;
+        uint32_t *ne = s_lit;
         int32_t *t = (int32_t *)(s_lit + nw);
         for (int i = tid; i < nw; i += kLT) ne[i] = a.ne[i];
         for (int i = tid; i < a.B; i += kLT) {
@@ -133,12 +137,12 @@ __global__ void __launch_bounds__(kLT, 1) k_lit_steps(Lit a)
             int b = -1;
             for (int w0 = 0; w0 < nw && b < 0; w0 += 32) {
                 const int w = w0 + lane;
-                const unsigned long long m = w < nw ? *(volatile unsigned long long *)(bk.ne + w) : 0ull;
-                const unsigned bal = __ballot_sync(0xffffffffu, m != 0ull);
+                const uint32_t m = w < nw ? *(volatile uint32_t *)(bk.ne + w) : 0u;
+                const unsigned bal = __ballot_sync(0xffffffffu, m != 0u);
                 if (bal) {
                     const int l = __ffs(bal) - 1;
-                    const unsigned long long ml = __shfl_sync(0xffffffffu, m, l);
-                    b = ((w0 + l) << 6) + __ffsll((long long)ml) - 1;
+                    const uint32_t ml = __shfl_sync(0xffffffffu, m, l);
+                    b = ((w0 + l) << 5) + __ffs(ml) - 1;
                 }
             }
             if (lane == 0) {
@@ -151,7 +155,7 @@ __global__ void __launch_bounds__(kLT, 1) k_lit_steps(Lit a)
                     const int h = bk.head[b], t = *(volatile int *)(bk.tail + b);
                     bk.head[b] = t;
                     // consumed: the bucket is empty until this step queues into it
-                    atomicAnd(bk.ne + (b >> 6), ~(1ull << (b & 63)));
+                    atomicAnd(bk.ne + (b >> 5), ~(1u << (b & 31)));
                     s_b = b; s_h = h; s_n = t - h;
                 }
             }
@@ -208,6 +212,121 @@ __global__ void __launch_bounds__(kLT, 1) k_lit_steps(Lit a)
     }
 }
 
+// The same steps on a thread-block cluster: CTA 0 keeps the bucket
+// bookkeeping in its shared memory and picks each step's bucket; every CTA
+// of the cluster stamps a share of the spheres and queues a share of the
+// neighbours, reaching CTA 0's counters through distributed shared memory.
+// Two cluster barriers per step: after the pick, and after the step's work.
+// List entries written by other SMs are read with L2-coherent loads.
+__global__ void __launch_bounds__(kLT, 1) k_lit_cluster(Lit a)
+{
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ uint32_t s_litc[];
+    __shared__ int s_step[6];   // CTA 0: bucket, first entry, count, stop, list start, value
+    __shared__ int s_loc[6];    // every CTA: its copy of CTA 0's s_step
+    const unsigned rank = cl.block_rank(), ncta = cl.num_blocks();
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int gtid = (int)rank * kLT + tid, gstride = (int)ncta * kLT;
+    const int nw = (a.B + 31) >> 5;
+    uint32_t *const s_lit = s_litc;
+    uint32_t *ne0 = cl.map_shared_rank(s_lit, 0);
+    int32_t *t0 = (int32_t *)(ne0 + nw);
+    const Book bk0{t0, t0 + a.B, t0 + 2 * a.B, t0 + 3 * a.B, ne0};   // CTA 0's book, from any CTA
+    const int *step0 = cl.map_shared_rank(s_step, 0);
+    if (rank == 0) {
+        int32_t *t = (int32_t *)(s_lit + nw);
+        for (int i = tid; i < nw; i += kLT) s_lit[i] = a.ne[i];
+        for (int i = tid; i < a.B; i += kLT) {
+            t[i] = a.tail[i];
+            t[a.B + i] = a.head[i];
+            t[2 * a.B + i] = a.bstart[i];
+            t[3 * a.B + i] = a.bval[i];
+        }
+    }
+    cl.sync();
+    int64_t k = 0;
+    for (;;) {
+        if (rank == 0 && tid < 32) {
+            int b = -1;
+            for (int w0 = 0; w0 < nw && b < 0; w0 += 32) {
+                const int w = w0 + lane;
+                const uint32_t m = w < nw ? *(volatile uint32_t *)(s_lit + w) : 0u;
+                const unsigned bal = __ballot_sync(0xffffffffu, m != 0u);
+                if (bal) {
+                    const int l = __ffs(bal) - 1;
+                    const uint32_t ml = __shfl_sync(0xffffffffu, m, l);
+                    b = ((w0 + l) << 5) + __ffs(ml) - 1;
+                }
+            }
+            if (lane == 0) {
+                int stop = 0;
+                if (b < 0) stop = 1;
+                else if (k >= a.max_steps) stop = 2;
+                else if (k >= a.npore) stop = 3;
+                s_step[3] = stop;
+                if (!stop) {
+                    int32_t *t = (int32_t *)(s_lit + nw);
+                    const int h = t[a.B + b], tl = *(volatile int *)(t + b);
+                    t[a.B + b] = tl;
+                    atomicAnd(s_lit + (b >> 5), ~(1u << (b & 31)));
+                    s_step[0] = b; s_step[1] = h; s_step[2] = tl - h;
+                    s_step[4] = t[2 * a.B + b]; s_step[5] = t[3 * a.B + b];
+                }
+            }
+        }
+        cl.sync();
+        if (tid < 6) s_loc[tid] = step0[tid];
+        __syncthreads();
+        if (s_loc[3]) break;
+        k++;
+        const int n = s_loc[2];
+        const int32_t *pts = a.list + s_loc[4] + s_loc[1];
+        const int v = s_loc[5];
+        const int R = d_isqrt(v);
+        const int64_t RR = (int64_t)R * R;
+        const int Re = min(R, max(a.nx, max(a.ny, a.nz)));
+        const int side = 2 * Re + 1;
+        const int64_t rows = (int64_t)side * side;
+        for (int64_t it = gtid; it < (int64_t)n * rows; it += gstride) {
+            const int q = (int)(it / rows);
+            const int r = (int)(it - (int64_t)q * rows);
+            const int ddx = r / side - Re, ddy = r % side - Re;
+            const int64_t rem = RR - (int64_t)ddx * ddx - (int64_t)ddy * ddy;
+            if (rem < 0) continue;
+            int cx, cy, cz;
+            coords(a, (uint32_t)__ldcg(pts + q), cx, cy, cz);
+            const int x = cx + ddx, y = cy + ddy;
+            if (x < 0 || y < 0 || x >= a.nx || y >= a.ny) continue;
+            const int hz = d_isqrt((int)min(rem, (int64_t)IBIP_INF32));
+            const int z0 = max(0, cz - hz), z1 = min(a.nz - 1, cz + hz);
+            int32_t *row = a.seq + d_lin(x, y, 0, a.ny, a.nz);
+            for (int z = z0; z <= z1; z++) atomicMin(row + z, (int32_t)k);
+        }
+        for (int64_t it = gtid; it < (int64_t)n * 6; it += gstride) {
+            const int q = (int)(it / 6), d = (int)(it - (int64_t)q * 6);
+            const uint32_t c = (uint32_t)__ldcg(pts + q);
+            int x, y, z;
+            coords(a, c, x, y, z);
+            if (d == 0) a.cstep[c] = (int32_t)k;
+            x += d == 0 ? -1 : d == 1 ? 1 : 0;
+            y += d == 2 ? -1 : d == 3 ? 1 : 0;
+            z += d == 4 ? -1 : d == 5 ? 1 : 0;
+            if (x < 0 || y < 0 || z < 0 || x >= a.nx || y >= a.ny || z >= a.nz) continue;
+            enqueue(a, bk0, d_lin(x, y, z, a.ny, a.nz));
+        }
+        if (rank == 0 && tid == 0 && k <= a.cap) {
+            a.step_r2[k - 1] = (int32_t)RR;
+            a.step_count[k - 1] = n;
+        }
+        cl.sync();
+    }
+    if (rank == 0 && tid == 0) {
+        a.out[0] = k;
+        a.out[1] = s_loc[3] == 2 ? IBIP_ERR_STEP_LIMIT : (s_loc[3] == 3 ? IBIP_ERR_BOUNDS : IBIP_OK);
+    }
+    cl.sync();   // CTA 0's shared memory stays alive until every CTA has read it
+}
+
 __global__ void k_lit_final(int32_t *seq, int64_t N)
 {
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (int64_t)gridDim.x * blockDim.x)
@@ -255,6 +374,31 @@ __global__ void k_lit_bval(const int32_t *incl, int maxd, int B, int hasinf, int
 
 }  // namespace
 
+// Largest cluster (16, 8, 4 or 2 CTAs of 1024 threads with `book` bytes of
+// shared memory) the device can place; 0 if none.
+static int lit_cluster_size(size_t book)
+{
+    cudaFuncSetAttribute(k_lit_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLitSmem);
+    cudaFuncSetAttribute(k_lit_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    for (int cs = 16; cs >= 2; cs /= 2) {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = cs;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(cs);
+        cfg.blockDim = dim3(kLT);
+        cfg.dynamicSmemBytes = book;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, k_lit_cluster, &cfg) == cudaSuccess && n > 0) return cs;
+        cudaGetLastError();
+    }
+    return 0;
+}
+
 int ibip_literal_run(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, int64_t max_steps, int32_t *seq,
                      int32_t *cstep, int32_t *step_r2, int32_t *step_count, int64_t cap, int64_t *h_out)
 {
@@ -293,14 +437,14 @@ int ibip_literal_run(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, 
         if (cudaStreamSynchronize(s) != cudaSuccess) return IBIP_ERR_CUDA;
         B = h[0];
     }
-    const int nw = (B + 63) / 64;
+    const int nw = (B + 31) / 32;
     // one arena: list | bstart | bval | tail | head | cnt | ne | queued | out
     const size_t planes = ((size_t)N + 31) / 32;
     auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
     const size_t o_list = 0, o_bstart = o_list + up((size_t)npore * 4), o_bval = o_bstart + up((size_t)B * 4),
                  o_tail = o_bval + up((size_t)B * 4), o_head = o_tail + up((size_t)B * 4),
                  o_cnt = o_head + up((size_t)B * 4), o_ne = o_cnt + up((size_t)B * 4),
-                 o_q = o_ne + up((size_t)nw * 8), o_out = o_q + up(planes * 4), total = o_out + up(64);
+                 o_q = o_ne + up((size_t)nw * 4), o_out = o_q + up(planes * 4), total = o_out + up(64);
     char *w = (char *)ibip_scratch(ctx, SC_LIT, total);
     if (!w) return IBIP_ERR_OOM;
     Lit a;
@@ -312,7 +456,7 @@ int ibip_literal_run(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, 
     a.bval = (const int32_t *)(w + o_bval);
     a.tail = (int32_t *)(w + o_tail);
     a.head = (int32_t *)(w + o_head);
-    a.ne = (unsigned long long *)(w + o_ne);
+    a.ne = (uint32_t *)(w + o_ne);
     a.queued = (uint32_t *)(w + o_q);
     a.incl = incl;
     a.B = B; a.hasinf = hasinf;
@@ -333,8 +477,24 @@ int ibip_literal_run(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, 
     IBIP_LAUNCH(ctx);
     ibip_prof_end(ctx, IBIP_K_RANK);
     ibip_prof_begin(ctx, IBIP_K_INVADE);
-    const size_t book = (size_t)nw * 8 + (size_t)B * 16;
-    if (book <= kLitSmem) {
+    const size_t book = (size_t)nw * 4 + (size_t)B * 16;
+    const int cs = book <= kLitSmem ? lit_cluster_size(book) : 0;
+    if (cs > 1) {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = cs;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(cs);
+        cfg.blockDim = dim3(kLT);
+        cfg.dynamicSmemBytes = book;
+        cfg.stream = s;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cudaError_t e = cudaLaunchKernelEx(&cfg, k_lit_cluster, a);
+        if (e != cudaSuccess) return ibip_cuda_status(e);
+    } else if (book <= kLitSmem) {
         cudaFuncSetAttribute(k_lit_steps<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLitSmem);
         k_lit_steps<true><<<1, kLT, book, s>>>(a);
     } else {
