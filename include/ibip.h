@@ -137,6 +137,26 @@ IBIP_API int ibip_invade(ibip_ctx *ctx, const uint8_t *image, const int32_t *dt2
                 int inlet, int64_t max_steps, int32_t *seq, int32_t *step_r2,
                 int32_t *step_centre, int64_t capacity_steps, int64_t *h_n_steps);
 
+/* ibip_invade with two extensions of Section 2.1.
+ *   inlet_mask: uint8[N] or NULL.  Nonzero voxels are the inlets ("a Boolean
+ *               image ... with non-zeros indicating the inlet voxels", which
+ *               may lie inside the image, e.g. for evaporation): the pore
+ *               voxels among them are the first candidates.  NULL: the
+ *               `inlet` face, as ibip_invade.
+ *   resume:     0, or 1 to continue an earlier run: seq then holds on entry
+ *               the sequence image an earlier call wrote (steps 1..K0, where
+ *               K0 is its largest value; -1 uninvaded pore; 0 solid) for the
+ *               same image and inlets, and step_r2 / step_centre hold its
+ *               first K0 entries.  The candidates are rebuilt from seq (inlet
+ *               voxels and neighbours of invaded voxels that are still
+ *               uninvaded), steps K0+1, ... are appended, and max_steps counts
+ *               the new steps only.  The result equals one uninterrupted run.
+ *   h_n_steps:  the total K.
+ * Other arguments, statuses and synchronisation as ibip_invade. */
+IBIP_API int ibip_invade_ex(ibip_ctx *ctx, const uint8_t *image, const int32_t *dt2, ibip_dims dims, int inlet,
+                            const uint8_t *inlet_mask, int resume, int64_t max_steps, int32_t *seq,
+                            int32_t *step_r2, int32_t *step_centre, int64_t capacity_steps, int64_t *h_n_steps);
+
 /* The invasion exactly as Section 2.1 prints it (the "paper-literal" rule;
  * ibip_invade uses the frontier rule instead).  The inlets start as every
  * voxel of the `inlet` face.  Step k = 1, 2, ...: the candidates are the

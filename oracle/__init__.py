@@ -52,6 +52,8 @@ def lib():
                 "or_edt_sep": (None, [P, i32, i32, i32, P]),
                 "or_invade_scan": (i64, [P, P, i32, i32, i32, i32, i64, P, P, P, i64, P]),
                 "or_invade_heap": (i64, [P, P, i32, i32, i32, i32, i64, P, P, P, i64, P]),
+                "or_invade_scan_mask": (i64, [P, P, i32, i32, i32, i32, P, i64, P, P, P, i64, P]),
+                "or_invade_heap_mask": (i64, [P, P, i32, i32, i32, i32, P, i64, P, P, P, i64, P]),
                 "or_invade_literal_scan": (i64, [P, P, i32, i32, i32, i32, i64, P, P, P, P, i64, P]),
                 "or_invade_literal_queue": (i64, [P, P, i32, i32, i32, i32, i64, P, P, P, P, i64, P]),
                 "or_trap_bfs": (None, [P, i32, i32, i32, i32, i32, P, P]),
@@ -96,9 +98,11 @@ def edt(image):
     return out
 
 
-def invade(image, dt2, inlet=0, max_steps=None, method="heap", capacity=None):
+def invade(image, dt2, inlet=0, max_steps=None, method="heap", capacity=None, mask=None):
     """Run the invasion (Section 2.1).  Returns (seq, step_r2, step_centre,
-    status).  method: "heap" (priority queue) or "scan" (rescan every step)."""
+    status, K).  method: "heap" (priority queue) or "scan" (rescan every
+    step).  mask: optional uint8 image of inlet voxels (nonzero), replacing
+    the inlet face."""
     a = _img(image)
     d = np.ascontiguousarray(dt2, dtype=np.int32)
     n = a.size
@@ -110,9 +114,12 @@ def invade(image, dt2, inlet=0, max_steps=None, method="heap", capacity=None):
     r2 = np.zeros(max(cap, 1), np.int32)
     cen = np.zeros(max(cap, 1), np.int32)
     st = C.c_int(0)
-    f = lib().or_invade_heap if method == "heap" else lib().or_invade_scan
-    k = f(_p(a), _p(d), *a.shape, int(inlet), int(max_steps), _p(seq), _p(r2), _p(cen), cap,
-          C.addressof(st))
+    m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
+    if m is not None and m.shape != a.shape:
+        raise ValueError("mask shape differs from the image")
+    f = lib().or_invade_heap_mask if method == "heap" else lib().or_invade_scan_mask
+    k = f(_p(a), _p(d), *a.shape, int(inlet), None if m is None else _p(m), int(max_steps), _p(seq), _p(r2),
+          _p(cen), cap, C.addressof(st))
     k = int(k)
     kk = min(k, cap)
     del n

@@ -208,9 +208,18 @@ static int has_invaded_nb(const int32_t *seq, int nx, int ny, int nz, int64_t x,
 /* Invade-scan: every step rescans the whole image for the candidate set,
  * exactly as the definition reads.  O(steps * N).  Returns the number of
  * steps K; *status = OR_STEP_LIMIT if max_steps stopped a non-empty front. */
-int64_t or_invade_scan(const uint8_t *img, const int32_t *dt2, int nx, int ny, int nz, int inlet,
-                       int64_t max_steps, int32_t *seq, int32_t *step_r2, int32_t *step_centre,
-                       int64_t cap, int *status)
+/* inlet voxels: the given mask (nonzero = inlet, Section 2.1: "an empty
+ * Boolean image ... with non-zeros indicating the inlet voxels"), else the
+ * inlet face */
+static int is_inlet(const uint8_t *mask, int64_t v, int64_t x, int64_t y, int64_t z, int nx, int ny, int nz,
+                    int inlet)
+{
+    return mask ? mask[v] != 0 : on_face(x, y, z, nx, ny, nz, inlet);
+}
+
+int64_t or_invade_scan_mask(const uint8_t *img, const int32_t *dt2, int nx, int ny, int nz, int inlet,
+                            const uint8_t *mask, int64_t max_steps, int32_t *seq, int32_t *step_r2,
+                            int32_t *step_centre, int64_t cap, int *status)
 {
     int64_t N = (int64_t)nx * ny * nz, k = 0;
     for (int64_t v = 0; v < N; v++) seq[v] = img[v] ? -1 : 0;
@@ -221,7 +230,7 @@ int64_t or_invade_scan(const uint8_t *img, const int32_t *dt2, int nx, int ny, i
             if (seq[v] != -1) continue;
             int64_t x, y, z;
             coords(v, ny, nz, &x, &y, &z);
-            if (!on_face(x, y, z, nx, ny, nz, inlet) && !has_invaded_nb(seq, nx, ny, nz, x, y, z)) continue;
+            if (!is_inlet(mask, v, x, y, z, nx, ny, nz, inlet) && !has_invaded_nb(seq, nx, ny, nz, x, y, z)) continue;
             if (dt2[v] > bestd) { bestd = dt2[v]; best = v; }
         }
         if (best < 0) break;
@@ -284,9 +293,9 @@ static uint64_t hkey(int32_t d, int64_t idx)
  * candidate; popped entries already invaded are skipped.  Same result as
  * invade-scan, far faster; used on large images and as the timed CPU
  * baseline. */
-int64_t or_invade_heap(const uint8_t *img, const int32_t *dt2, int nx, int ny, int nz, int inlet,
-                       int64_t max_steps, int32_t *seq, int32_t *step_r2, int32_t *step_centre,
-                       int64_t cap, int *status)
+int64_t or_invade_heap_mask(const uint8_t *img, const int32_t *dt2, int nx, int ny, int nz, int inlet,
+                            const uint8_t *mask, int64_t max_steps, int32_t *seq, int32_t *step_r2,
+                            int32_t *step_centre, int64_t cap, int *status)
 {
     int64_t N = (int64_t)nx * ny * nz, k = 0;
     uint8_t *queued = calloc(N ? N : 1, 1);
@@ -296,7 +305,7 @@ int64_t or_invade_heap(const uint8_t *img, const int32_t *dt2, int nx, int ny, i
         seq[v] = img[v] ? -1 : 0;
         int64_t x, y, z;
         coords(v, ny, nz, &x, &y, &z);
-        if (img[v] && on_face(x, y, z, nx, ny, nz, inlet)) {
+        if (img[v] && is_inlet(mask, v, x, y, z, nx, ny, nz, inlet)) {
             queued[v] = 1;
             hpush(&h, hkey(dt2[v], v));
         }
@@ -837,6 +846,21 @@ int64_t or_invade_literal_queue(const uint8_t *img, const int32_t *dt2, int nx, 
     free(queued);
     free(pts);
     return k;
+}
+
+/* the inlet face as the inlets (no mask) */
+int64_t or_invade_scan(const uint8_t *img, const int32_t *dt2, int nx, int ny, int nz, int inlet,
+                       int64_t max_steps, int32_t *seq, int32_t *step_r2, int32_t *step_centre,
+                       int64_t cap, int *status)
+{
+    return or_invade_scan_mask(img, dt2, nx, ny, nz, inlet, NULL, max_steps, seq, step_r2, step_centre, cap, status);
+}
+
+int64_t or_invade_heap(const uint8_t *img, const int32_t *dt2, int nx, int ny, int nz, int inlet,
+                       int64_t max_steps, int32_t *seq, int32_t *step_r2, int32_t *step_centre,
+                       int64_t cap, int *status)
+{
+    return or_invade_heap_mask(img, dt2, nx, ny, nz, inlet, NULL, max_steps, seq, step_r2, step_centre, cap, status);
 }
 
 int or_abi_version(void) { return 1; }

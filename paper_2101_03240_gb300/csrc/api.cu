@@ -9,7 +9,8 @@
 #include "common.cuh"
 
 int ibip_invade_run(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, int64_t max_steps,
-                    int32_t *seq, int32_t *step_r2, int32_t *step_centre, int64_t cap, int64_t *h_out);
+                    int32_t *seq, int32_t *step_r2, int32_t *step_centre, int64_t cap, int64_t *h_out,
+                    const uint8_t *mask = nullptr, int resume = 0);
 int ibip_pc_launch(ibip_ctx *ctx, const int32_t *seq, ibip_dims d, const int32_t *r2, int64_t K, double voxel,
                    double sigma, double cos_theta, float *S, float *Pc, float *sat);
 int ibip_trap_finish(ibip_ctx *ctx, const int32_t *seq, const int32_t *M, ibip_dims d, int rerank, uint8_t *trapped,
@@ -293,6 +294,34 @@ int ibip_invade(ibip_ctx *ctx, const uint8_t *image, const int32_t *dt2, ibip_di
     }
     int64_t out[36] = {0};
     int st = ibip_invade_run(ctx, d, dims, inlet, max_steps, seq, step_r2, step_centre, capacity_steps, out);
+    if (st) return st;
+    memcpy(ctx->inv_stats, out, sizeof(out));
+    *h_n_steps = out[0];
+    if (out[1] != IBIP_OK) return (int)out[1];
+    if (out[0] > capacity_steps) return IBIP_ERR_ARG;
+    return IBIP_OK;
+}
+
+int ibip_invade_ex(ibip_ctx *ctx, const uint8_t *image, const int32_t *dt2, ibip_dims dims, int inlet,
+                   const uint8_t *inlet_mask, int resume, int64_t max_steps, int32_t *seq, int32_t *step_r2,
+                   int32_t *step_centre, int64_t capacity_steps, int64_t *h_n_steps)
+{
+    if (!ctx || !image || !seq || !h_n_steps || !dims_ok(dims) || (!inlet_mask && !face_ok(inlet)) ||
+        max_steps < 0 || capacity_steps < 0 || (capacity_steps > 0 && !step_r2) || (resume != 0 && resume != 1))
+        return IBIP_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    *h_n_steps = 0;
+    const int32_t *d = dt2;
+    if (!d) {
+        int32_t *t = (int32_t *)ibip_scratch(ctx, SC_DT2, (size_t)nvox(dims) * sizeof(int32_t));
+        if (!t) return IBIP_ERR_OOM;
+        int st = ibip_edt_launch(ctx, image, dims, t);
+        if (st) return st;
+        d = t;
+    }
+    int64_t out[36] = {0};
+    int st = ibip_invade_run(ctx, d, dims, inlet_mask ? 0 : inlet, max_steps, seq, step_r2, step_centre,
+                             capacity_steps, out, inlet_mask, resume);
     if (st) return st;
     memcpy(ctx->inv_stats, out, sizeof(out));
     *h_n_steps = out[0];

@@ -175,6 +175,9 @@ struct Inv {
     u64 *fb0, *fb1, *fb2, *fb3;
     int32_t *seq, *step_r2, *step_centre;
     int64_t *out;      // out[0] = steps, out[1] = status, out[2] = iterations
+    const uint8_t *mask;   // inlet voxels (nonzero), or null: the inlet face
+    int resume;            // seq holds an earlier run's steps 1..k0 on entry
+    int64_t k0;            // steps already taken (resume), else 0
 };
 
 __global__ void k_seq_init(const int32_t *__restrict__ dt2, int64_t N, int32_t *seq)
@@ -183,7 +186,9 @@ __global__ void k_seq_init(const int32_t *__restrict__ dt2, int64_t N, int32_t *
         seq[v] = dt2[v] > 0 ? -1 : 0;
 }
 
-// one thread per bit-plane word: avail bits, inlet-face candidates
+// one thread per bit-plane word: avail bits (pore, not yet invaded) and the
+// first candidates: inlet voxels (the mask, else the inlet face) and, when
+// resuming, every uninvaded pore voxel next to an invaded one
 __global__ void k_plane_init(Inv a)
 {
     const int64_t nw = (int64_t)a.nx * a.ny * a.NW;
@@ -197,8 +202,19 @@ __global__ void k_plane_init(Inv a)
             if (z >= a.nz) break;
             int64_t v = row * a.nz + z;
             if (a.dt2[v] <= 0) continue;
+            if (a.resume && a.seq[v] != -1) continue;
             av |= 1u << b;
-            if (d_on_face(x, y, z, a.nx, a.ny, a.nz, a.inlet)) {
+            bool cand = a.mask ? a.mask[v] != 0 : d_on_face(x, y, z, a.nx, a.ny, a.nz, a.inlet);
+            if (!cand && a.resume) {
+                const int nxs[6] = {x - 1, x + 1, x, x, x, x}, nys[6] = {y, y, y - 1, y + 1, y, y},
+                          nzs[6] = {z, z, z, z, z - 1, z + 1};
+                for (int q = 0; q < 6 && !cand; q++) {
+                    if (nxs[q] < 0 || nys[q] < 0 || nzs[q] < 0 || nxs[q] >= a.nx || nys[q] >= a.ny || nzs[q] >= a.nz)
+                        continue;
+                    cand = a.seq[d_lin(nxs[q], nys[q], nzs[q], a.ny, a.nz)] >= 1;
+                }
+            }
+            if (cand) {
                 ad |= 1u << b;
                 int r = a.rank[v];
                 atomicOr(a.fb0 + (r >> 6), 1ull << (r & 63));
@@ -697,7 +713,7 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
     }
     __syncthreads();
 
-    int64_t k = 0, iters = 0;
+    int64_t k = a.k0, iters = 0;
     // diagnostics kept by thread 0: cycles per phase, items, stale summary bits
     long long c_sel = 0, c_shell = 0, c_commit = 0, n_items = 0, n_commit_items = 0, n_stale = 0, n_units = 0;
     long long c_small = 0, n_small = 0, n_tiny = 0, n_tiny_steps = 0, c_tiny = 0;
@@ -1210,14 +1226,16 @@ JobMem carve(char *p, const JobSizes &z)
 // once (the number of distinct dt2 values sizes the counting sort).
 int invade_setup(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, int64_t max_steps, int32_t *seq,
                  int32_t *step_r2, int32_t *step_centre, int64_t cap, int maxd, int npore, int hasinf,
-                 const JobMem &mem, Inv *out_a)
+                 const JobMem &mem, Inv *out_a, const uint8_t *mask = nullptr, int resume = 0, int64_t k0 = 0)
 {
     cudaStream_t s = ctx->stream;
     const int64_t N = nvox(d);
     const int gs = ctx->sm_count * 8;
     int *h = (int *)ctx->h_pinned;
-    k_seq_init<<<gs, 256, 0, s>>>(dt2, N, seq);
-    IBIP_LAUNCH(ctx);
+    if (!resume) {
+        k_seq_init<<<gs, 256, 0, s>>>(dt2, N, seq);
+        IBIP_LAUNCH(ctx);
+    }
     // -- bucket ids by dt2 value
     int32_t *incl = (int32_t *)ibip_scratch(ctx, SC_PRES, ((size_t)maxd + 2) * sizeof(int32_t));
     if (!incl) return IBIP_ERR_OOM;
@@ -1261,8 +1279,11 @@ int invade_setup(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, int6
     a.NL1 = (a.NL0 + 63) / 64;
     a.NL2 = (a.NL1 + 63) / 64;
     a.NL3 = (a.NL2 + 63) / 64;
-    a.max_steps = max_steps;
+    a.max_steps = max_steps > INT64_MAX - k0 ? INT64_MAX : k0 + max_steps;   // a total
     a.cap = cap;
+    a.mask = mask;
+    a.resume = resume;
+    a.k0 = k0;
     a.npore = npore;
     a.rank = mem.rank; a.okey = mem.okey; a.dt2 = dt2;
     a.avail = mem.avail; a.added = mem.added;
@@ -1285,10 +1306,16 @@ size_t invade_dyn_smem(const Inv &a, bool l1smem)
 }  // namespace
 
 int ibip_invade_run(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, int64_t max_steps,
-                    int32_t *seq, int32_t *step_r2, int32_t *step_centre, int64_t cap, int64_t *h_out)
+                    int32_t *seq, int32_t *step_r2, int32_t *step_centre, int64_t cap, int64_t *h_out,
+                    const uint8_t *mask, int resume)
 {
     cudaStream_t s = ctx->stream;
     const int64_t N = nvox(d);
+    int k0 = 0;   // steps of the run being resumed: the largest seq value
+    if (resume) {
+        int st = ibip_max_launch(ctx, seq, N, &k0);
+        if (st) return st;
+    }
     int *stats = (int *)ibip_scratch(ctx, SC_SMALL, kSmallBytes);
     if (!stats) return IBIP_ERR_OOM;
     int *h = (int *)ctx->h_pinned;
@@ -1300,10 +1327,13 @@ int ibip_invade_run(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, i
     if (cudaStreamSynchronize(s) != cudaSuccess) return IBIP_ERR_CUDA;
     const int maxd = h[0], npore = h[1], hasinf = h[2];
     if (npore == 0) {
-        k_seq_init<<<ctx->sm_count * 8, 256, 0, s>>>(dt2, N, seq);
-        IBIP_LAUNCH(ctx);
+        if (!resume) {
+            k_seq_init<<<ctx->sm_count * 8, 256, 0, s>>>(dt2, N, seq);
+            IBIP_LAUNCH(ctx);
+        }
         ibip_prof_end(ctx, IBIP_K_RANK);
         for (int i = 0; i < kNOut; i++) h_out[i] = 0;
+        h_out[0] = k0;
         h_out[1] = IBIP_OK;
         return ibip_cuda_status(cudaStreamSynchronize(s));
     }
@@ -1319,7 +1349,8 @@ int ibip_invade_run(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, i
     if (!mem.rank || !mem.okey || !mem.avail || !mem.added || !mem.fb || !mem.gl || !small) return IBIP_ERR_OOM;
     mem.out = small + 8;
     Inv a;
-    int st = invade_setup(ctx, dt2, d, inlet, max_steps, seq, step_r2, step_centre, cap, maxd, npore, hasinf, mem, &a);
+    int st = invade_setup(ctx, dt2, d, inlet, max_steps, seq, step_r2, step_centre, cap, maxd, npore, hasinf, mem, &a,
+                          mask, resume, k0);
     if (st) return st;
     ibip_prof_end(ctx, IBIP_K_RANK);
     const FastDiv fd_nyz = make_fastdiv((uint32_t)d.ny * (uint32_t)d.nz), fd_nz = make_fastdiv((uint32_t)d.nz);

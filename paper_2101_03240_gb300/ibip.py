@@ -84,6 +84,7 @@ def _lib():
                 "ibip_invade_stats": (C.c_int, [P, C.POINTER(i64), C.c_int]),
                 "ibip_profile_read": (C.c_int, [P, C.c_int, C.POINTER(dbl), C.POINTER(i64)]),
                 "ibip_job_footprint": (i64, [Dims, C.c_int]),
+                "ibip_invade_ex": (C.c_int, [P, P, P, Dims, C.c_int, P, C.c_int, i64, P, P, P, i64, C.POINTER(i64)]),
                 "ibip_equal_saturation": (C.c_int, [P, P, P, Dims, i64, i32, C.POINTER(i64), C.POINTER(i64),
                                                     C.POINTER(i64)]),
                 "ibip_invade_literal": (C.c_int, [P, P, P, Dims, C.c_int, i64, P, P, P, P, i64, C.POINTER(i64)]),
@@ -255,6 +256,40 @@ class Context:
         k = int(K.value)
         kk = min(k, capacity)
         return seq, step_r2[:kk], (step_centre[:kk] if centres else None), k, st
+
+    def invade_ex(self, image, dt2=None, inlet=0, inlet_mask=None, resume_from=None, max_steps=None,
+                  capacity=None):
+        """ibip_invade_ex: `inlet_mask` (uint8 CUDA tensor, nonzero = inlet
+        voxels) replaces the inlet face; `resume_from` = (seq, step_r2,
+        step_centre) of an earlier call continues that run (the tensors are
+        updated in place).  Returns (seq, step_r2, step_centre, K, status)
+        with the step arrays trimmed to K."""
+        _need(image, torch.uint8, "image")
+        if dt2 is not None:
+            _need(dt2, torch.int32, "dt2")
+        if inlet_mask is not None:
+            _need(inlet_mask, torch.uint8, "inlet_mask")
+        dev, N = image.device, image.numel()
+        cap = N if capacity is None else int(capacity)
+        if resume_from is not None:
+            seq, r2p, cp = resume_from
+            r2 = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+            cen = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+            r2[:r2p.numel()] = r2p
+            cen[:cp.numel()] = cp
+        else:
+            seq = torch.empty(image.shape, dtype=torch.int32, device=dev)
+            r2 = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+            cen = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+        k = C.c_int64(0)
+        self._stream()
+        st = _lib().ibip_invade_ex(self._h, _ptr(image), _ptr(dt2), _dims(image.shape), int(inlet), _ptr(inlet_mask),
+                                   1 if resume_from is not None else 0, N if max_steps is None else int(max_steps),
+                                   _ptr(seq), _ptr(r2), _ptr(cen), cap, C.byref(k))
+        if st not in (OK, ERR_STEP_LIMIT):
+            raise IbipError("ibip_invade_ex", st)
+        K = int(k.value)
+        return seq, r2[:min(K, cap)], cen[:min(K, cap)], K, st
 
     def invade_literal(self, image, dt2=None, inlet=0, max_steps=None, capacity=None):
         """The invasion exactly as Section 2.1 prints it (ibip_invade_literal).
