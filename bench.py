@@ -504,6 +504,22 @@ def run_ours(args, rank, world):
     e2e_step = sum(e2e_ms) / len(e2e_ms)
     e2e_step = max_over_ranks(e2e_step, world, dev)
 
+    # ---- trapped wetting phase, invasion vs opening (Figure 9), once, untimed
+    trap_cmp = None
+    if w.outlet is not None:
+        d_ = ctx.edt(img_d)
+        if args.rule == "paper":
+            s_ = ctx.invade_literal(img_d, d_, inlet=w.inlet)[0]
+        else:
+            s_ = ctx.invade(img_d, d_, inlet=w.inlet)[0]
+        lev_, _ = ctx.morph_drainage(img_d, d_, levels, inlet=w.inlet)
+        npore_ = int((img_d > 0).sum().item())
+        t_ibip = int(ctx.trapping(s_, w.outlet)[0].sum().item())
+        t_mio = int(ctx.trapping(lev_, w.outlet)[0].sum().item())
+        trap_cmp = {"trapped_frac_invasion": t_ibip / npore_, "trapped_frac_opening": t_mio / npore_,
+                    "note": "pore voxels trapped (defending phase cut from the outlet) after the invasion and "
+                            "after the opening's last level, the opening's levels read as a sequence"}
+
     if rank != 0:
         return None
 
@@ -562,6 +578,7 @@ def run_ours(args, rank, world):
                              "mean_diff_frac": sum(eq[1]) / len(eq[1]) / npore,
                              "note": "voxels in exactly one of the opening's level set and the invasion's "
                                      "matched-count set, over all pore voxels (Section 3.1.1)"},
+        "trapping_vs_opening": trap_cmp,
         "invasion_steps_per_s": K / (prof["invade"][0] / args.steps * 1e-3) if prof["invade"][1] else None,
         "invasion_us_per_step": us_per_step,
         "e2e": {"value": job_rate(N, world, e2e_step * 1e-3), "unit": "voxels/s",

@@ -195,6 +195,25 @@ IBIP_API int ibip_invade_literal(ibip_ctx *ctx, const uint8_t *image, const int3
 IBIP_API int ibip_trapping(ibip_ctx *ctx, const int32_t *seq, ibip_dims dims, int outlet, int rerank,
                   uint8_t *trapped, int32_t *seq_out);
 
+/* Trapping with re-ranking (Section 2.2.3) that also re-indexes the step
+ * radii, so the re-ranked sequence feeds ibip_pc_curve directly.  Steps
+ * left without any voxel after trapping are dropped and the survivors are
+ * numbered 1, 2, ... in their old order.
+ *   seq, dims, outlet, trapped: as ibip_trapping; seq_out: required.
+ *   step_r2:       int32[n_steps] radii of the original steps.
+ *   step_r2_out:   int32[n_steps] output: radii of the surviving steps.
+ *   h_n_steps_out: host int64 output: number of surviving steps.
+ * Synchronous. */
+IBIP_API int ibip_trapping_ex(ibip_ctx *ctx, const int32_t *seq, ibip_dims dims, int outlet, uint8_t *trapped,
+                              int32_t *seq_out, const int32_t *step_r2, int64_t n_steps, int32_t *step_r2_out,
+                              int64_t *h_n_steps_out);
+
+/* Sphere-size image (Section 2.2.2, Figure 5 right): r2_image[v] =
+ * step_r2[seq[v] - 1] for 1 <= seq[v] <= n_steps (the squared radius of the
+ * sphere that invaded v), 0 on solid, -1 on uninvaded pore.  Asynchronous. */
+IBIP_API int ibip_size_image(ibip_ctx *ctx, const int32_t *seq, ibip_dims dims, const int32_t *step_r2,
+                             int64_t n_steps, int32_t *r2_image);
+
 /* Pressure-based drainage by morphological image opening, MIO (Section 1,
  * Section 2.4.1): for each squared radius T_i (strictly decreasing), keep
  * the pore voxels with dt2 >= T_i (erosion), trim those not 6-connected

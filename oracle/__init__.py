@@ -223,3 +223,26 @@ def equal_saturation(seq, level, n_levels):
         ns.append(n)
         diffs.append(int(np.count_nonzero(in_mio != in_ibip)))
     return np.array(ks, np.int64), np.array(diffs, np.int64), np.array(ns, np.int64)
+
+
+def rerank_radii(seq, step_r2, outlet=1):
+    """Trapping with re-ranking (Section 2.2.3) and the radii of the steps
+    that keep at least one voxel, in their old order.  Returns (trapped,
+    seq_out re-ranked, step_r2 of the surviving steps)."""
+    tr, so = trapping(seq, outlet, rerank=False)
+    kept = np.unique(so[so >= 1])
+    r2 = np.asarray(step_r2)[kept - 1] if kept.size else np.zeros(0, np.int32)
+    tr2, so2 = trapping(seq, outlet, rerank=True)
+    return tr2, so2, np.asarray(r2, np.int32)
+
+
+def size_image(seq, step_r2):
+    """Squared radius of the sphere that invaded each voxel (Section 2.2.2,
+    Figure 5 right): 0 on solid, -1 on uninvaded pore."""
+    s = np.asarray(seq)
+    r2 = np.asarray(step_r2)
+    K = r2.size
+    out = np.where(s == 0, 0, -1).astype(np.int32)
+    inv = (s >= 1) & (s <= K)
+    out[inv] = r2[s[inv] - 1]
+    return out

@@ -14,7 +14,9 @@ int ibip_invade_run(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, i
 int ibip_pc_launch(ibip_ctx *ctx, const int32_t *seq, ibip_dims d, const int32_t *r2, int64_t K, double voxel,
                    double sigma, double cos_theta, float *S, float *Pc, float *sat);
 int ibip_trap_finish(ibip_ctx *ctx, const int32_t *seq, const int32_t *M, ibip_dims d, int rerank, uint8_t *trapped,
-                     int32_t *seq_out);
+                     int32_t *seq_out, const int32_t *r2_in = nullptr, int64_t k_in = 0, int32_t *r2_out = nullptr,
+                     int64_t *h_nout = nullptr);
+int ibip_size_launch(ibip_ctx *ctx, const int32_t *seq, ibip_dims d, const int32_t *r2, int64_t K, int32_t *out);
 int ibip_level_init(ibip_ctx *ctx, const uint8_t *img, ibip_dims d, int32_t *level);
 int ibip_level_counts(ibip_ctx *ctx, const int32_t *level, ibip_dims d, int L, int64_t *h_counts);
 
@@ -368,6 +370,32 @@ int ibip_trapping(ibip_ctx *ctx, const int32_t *seq, ibip_dims dims, int outlet,
     st = ibip_trap_finish(ctx, seq, M, dims, rerank, trapped, seq_out);
     if (st) return st;
     return ibip_cuda_status(cudaStreamSynchronize(ctx->stream));
+}
+
+int ibip_trapping_ex(ibip_ctx *ctx, const int32_t *seq, ibip_dims dims, int outlet, uint8_t *trapped,
+                     int32_t *seq_out, const int32_t *step_r2, int64_t n_steps, int32_t *step_r2_out,
+                     int64_t *h_n_steps_out)
+{
+    if (!ctx || !seq || !trapped || !seq_out || !h_n_steps_out || !dims_ok(dims) || !face_ok(outlet) ||
+        n_steps < 0 || (n_steps > 0 && (!step_r2 || !step_r2_out)))
+        return IBIP_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    int32_t *M = (int32_t *)ibip_scratch(ctx, SC_MM, (size_t)nvox(dims) * sizeof(int32_t));
+    if (!M) return IBIP_ERR_OOM;
+    int st = ibip_maximin_launch(ctx, seq, dims, outlet, M, kMaxRounds);
+    if (st) return st;
+    st = ibip_trap_finish(ctx, seq, M, dims, 1, trapped, seq_out, step_r2, n_steps, step_r2_out, h_n_steps_out);
+    if (st) return st;
+    return ibip_cuda_status(cudaStreamSynchronize(ctx->stream));
+}
+
+int ibip_size_image(ibip_ctx *ctx, const int32_t *seq, ibip_dims dims, const int32_t *step_r2, int64_t n_steps,
+                    int32_t *r2_image)
+{
+    if (!ctx || !seq || !r2_image || !dims_ok(dims) || n_steps < 0 || (n_steps > 0 && !step_r2))
+        return IBIP_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    return ibip_size_launch(ctx, seq, dims, step_r2, n_steps, r2_image);
 }
 
 int ibip_morph_drainage(ibip_ctx *ctx, const uint8_t *image, const int32_t *dt2, ibip_dims dims, int inlet,

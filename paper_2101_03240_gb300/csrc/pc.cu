@@ -148,6 +148,26 @@ __global__ void k_eqsat(const int32_t *__restrict__ seq, const int32_t *__restri
         if (s_h[i]) atomicAdd(dh + i, s_h[i]);
 }
 
+// re-ranked trapping: the radius of every surviving step, in its new order
+// (map = inclusive prefix count of surviving steps)
+__global__ void k_compact_r2(const int32_t *__restrict__ map, int64_t K, const int32_t *__restrict__ r2,
+                             int32_t *r2_out)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x + 1; k <= K; k += (int64_t)gridDim.x * blockDim.x)
+        if (map[k] != map[k - 1]) r2_out[map[k] - 1] = r2[k - 1];
+}
+
+// the size of the sphere that invaded each voxel (Section 2.2.2, Figure 5
+// right), as its squared radius; 0 on solid, -1 on uninvaded pore
+__global__ void k_size_image(const int32_t *__restrict__ seq, int64_t N, const int32_t *__restrict__ r2, int64_t K,
+                             int32_t *out)
+{
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (int64_t)gridDim.x * blockDim.x) {
+        const int s = seq[v];
+        out[v] = s == 0 ? 0 : (s >= 1 && s <= K ? r2[s - 1] : -1);
+    }
+}
+
 }  // namespace
 
 int ibip_pc_launch(ibip_ctx *ctx, const int32_t *seq, ibip_dims d, const int32_t *r2, int64_t K, double voxel,
@@ -181,7 +201,7 @@ int ibip_pc_launch(ibip_ctx *ctx, const int32_t *seq, ibip_dims d, const int32_t
 }
 
 int ibip_trap_finish(ibip_ctx *ctx, const int32_t *seq, const int32_t *M, ibip_dims d, int rerank, uint8_t *trapped,
-                     int32_t *seq_out)
+                     int32_t *seq_out, const int32_t *r2_in, int64_t k_in, int32_t *r2_out, int64_t *h_nout)
 {
     cudaStream_t s = ctx->stream;
     const int64_t N = nvox(d);
@@ -213,7 +233,24 @@ int ibip_trap_finish(ibip_ctx *ctx, const int32_t *seq, const int32_t *M, ibip_d
     if (st) return st;
     k_remap<<<gs, 256, 0, s>>>(seq_out, N, mark);
     IBIP_LAUNCH(ctx);
+    if (r2_in && r2_out) {
+        const int64_t Kc = K < k_in ? K : k_in;
+        k_compact_r2<<<gs, 256, 0, s>>>(mark, Kc, r2_in, r2_out);
+        IBIP_LAUNCH(ctx);
+    }
+    if (h_nout) {
+        cudaMemcpyAsync(h, mark + K, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) return IBIP_ERR_CUDA;
+        *h_nout = h[0];
+    }
     ibip_prof_end(ctx, IBIP_K_TRAP);
+    return ibip_cuda_status(cudaGetLastError());
+}
+
+int ibip_size_launch(ibip_ctx *ctx, const int32_t *seq, ibip_dims d, const int32_t *r2, int64_t K, int32_t *out)
+{
+    k_size_image<<<ctx->sm_count * 8, 256, 0, ctx->stream>>>(seq, nvox(d), r2, K, out);
+    IBIP_LAUNCH(ctx);
     return ibip_cuda_status(cudaGetLastError());
 }
 

@@ -84,6 +84,8 @@ def _lib():
                 "ibip_invade_stats": (C.c_int, [P, C.POINTER(i64), C.c_int]),
                 "ibip_profile_read": (C.c_int, [P, C.c_int, C.POINTER(dbl), C.POINTER(i64)]),
                 "ibip_job_footprint": (i64, [Dims, C.c_int]),
+                "ibip_trapping_ex": (C.c_int, [P, P, Dims, C.c_int, P, P, P, i64, P, C.POINTER(i64)]),
+                "ibip_size_image": (C.c_int, [P, P, Dims, P, i64, P]),
                 "ibip_invade_ex": (C.c_int, [P, P, P, Dims, C.c_int, P, C.c_int, i64, P, P, P, i64, C.POINTER(i64)]),
                 "ibip_equal_saturation": (C.c_int, [P, P, P, Dims, i64, i32, C.POINTER(i64), C.POINTER(i64),
                                                     C.POINTER(i64)]),
@@ -323,6 +325,34 @@ class Context:
         if st != OK:
             raise IbipError("ibip_trapping", st)
         return tr, so
+
+    def trapping_rerank(self, seq, step_r2, outlet=1):
+        """Trapping with re-ranking and the surviving steps' radii
+        (ibip_trapping_ex).  Returns (trapped, seq_out, step_r2_out)."""
+        _need(seq, torch.int32, "seq")
+        K = int(step_r2.numel())
+        tr = torch.empty(seq.shape, dtype=torch.uint8, device=seq.device)
+        so = torch.empty(seq.shape, dtype=torch.int32, device=seq.device)
+        r2o = torch.empty(max(K, 1), dtype=torch.int32, device=seq.device)
+        r2 = step_r2.contiguous()
+        n = C.c_int64(0)
+        self._stream()
+        st = _lib().ibip_trapping_ex(self._h, _ptr(seq), _dims(seq.shape), int(outlet), _ptr(tr), _ptr(so), _ptr(r2),
+                                     K, _ptr(r2o), C.byref(n))
+        if st != OK:
+            raise IbipError("ibip_trapping_ex", st)
+        return tr, so, r2o[:int(n.value)]
+
+    def size_image(self, seq, step_r2):
+        """Squared radius of the sphere that invaded each voxel (ibip_size_image)."""
+        _need(seq, torch.int32, "seq")
+        out = torch.empty(seq.shape, dtype=torch.int32, device=seq.device)
+        r2 = step_r2.contiguous()
+        self._stream()
+        st = _lib().ibip_size_image(self._h, _ptr(seq), _dims(seq.shape), _ptr(r2), int(r2.numel()), _ptr(out))
+        if st != OK:
+            raise IbipError("ibip_size_image", st)
+        return out
 
     def morph_drainage(self, image, dt2, levels, inlet=0):
         _need(image, torch.uint8, "image")
