@@ -80,8 +80,8 @@ IBIP_API int ibip_destroy(ibip_ctx *ctx);
 /* Change the stream later calls queue on (NULL = legacy default stream). */
 IBIP_API int ibip_set_stream(ibip_ctx *ctx, void *cuda_stream);
 
-/* Squared Euclidean distance transform of the pore space (Section 2.1, the
- * "distance transform (dt) of the pore space image", Figure 2b).
+/* Squared Euclidean distance transform of the pore space (Section 2.1,
+ * Figure 2b).
  *   image: uint8[nx*ny*nz], nonzero = pore.
  *   dt2:   int32[nx*ny*nz] output as defined above (exact integers).
  * Asynchronous. */
@@ -138,9 +138,9 @@ IBIP_API int ibip_invade(ibip_ctx *ctx, const uint8_t *image, const int32_t *dt2
                 int32_t *step_centre, int64_t capacity_steps, int64_t *h_n_steps);
 
 /* ibip_invade with two extensions of Section 2.1.
- *   inlet_mask: uint8[N] or NULL.  Nonzero voxels are the inlets ("a Boolean
- *               image ... with non-zeros indicating the inlet voxels", which
- *               may lie inside the image, e.g. for evaporation): the pore
+ *   inlet_mask: uint8[N] or NULL.  Nonzero voxels are the inlets (Section
+ *               2.1 marks inlets with a Boolean image; they may lie inside
+ *               the image, e.g. for evaporation): the pore
  *               voxels among them are the first candidates.  NULL: the
  *               `inlet` face, as ibip_invade.
  *   resume:     0, or 1 to continue an earlier run: seq then holds on entry
@@ -292,7 +292,8 @@ typedef struct {
  * invasions of all images run in one launch, one persistent CTA per image,
  * largest first; results equal the per-image calls bit for bit.
  *   h_jobs: host array of n jobs (1 <= n <= 4096); n_steps and status are
- *           written back.  An image's pore count must stay below 2^25.
+ *           written back.  An image's pore count must stay below 2^25,
+ *           the whole batch's below 2^31.
  * Synchronous.  Returns IBIP_OK when every job succeeded, else the first
  * failing job's status (IBIP_ERR_ARG with n_steps = K when K exceeded
  * capacity_steps). */

@@ -71,9 +71,9 @@ static int64_t ball_halfwidth(int64_t r2)
 }
 
 /* ------------------------------------------------------------------------
- * Distance transform (Section 2.1: "the distance transform (dt) of the pore
- * space image").  dt2 is the squared Euclidean distance from each pore voxel
- * to the nearest solid voxel.
+ * Distance transform of the pore space (Section 2.1, Figure 2b).  dt2 is
+ * the squared Euclidean distance from each pore voxel to the nearest solid
+ * voxel.
  * ---------------------------------------------------------------------- */
 
 /* EDT-brute: the definition written out.  O(N * Nsolid). */
@@ -208,8 +208,8 @@ static int has_invaded_nb(const int32_t *seq, int nx, int ny, int nz, int64_t x,
 /* Invade-scan: every step rescans the whole image for the candidate set,
  * exactly as the definition reads.  O(steps * N).  Returns the number of
  * steps K; *status = OR_STEP_LIMIT if max_steps stopped a non-empty front. */
-/* inlet voxels: the given mask (nonzero = inlet, Section 2.1: "an empty
- * Boolean image ... with non-zeros indicating the inlet voxels"), else the
+/* inlet voxels: the given mask (nonzero = inlet; Section 2.1 marks the
+ * inlets with a Boolean image of the image's shape), else the
  * inlet face */
 static int is_inlet(const uint8_t *mask, int64_t v, int64_t x, int64_t y, int64_t z, int nx, int ny, int nz,
                     int inlet)

@@ -32,6 +32,7 @@ enum ScratchSlot {
     SC_BJOBS,     // batched invasion: job table
     SC_BDT2,      // batched invasion: EDTs of images given without one
     SC_LIT,       // paper-literal invasion: bucket lists, counters, bit-plane
+    SC_BSORT,     // batched invasion: sort job table, presence pool
     SC_NSLOTS
 };
 

@@ -161,6 +161,151 @@ __global__ void k_chunk_scatter(const int32_t *__restrict__ dt2, int64_t N, int 
     }
 }
 
+// ------------------------------------------- rank sort of many images --
+// The same counting sort for every image of a batch at once: per-image
+// arrays live at offsets in pooled buffers, one flat scan serves all images
+// (each subtracts the pool's running total at its own start), and each
+// kernel finds its image from its block index by binary search over the
+// images' first blocks.
+struct SortJob {
+    const int32_t *dt2;
+    int64_t N;
+    int32_t *seq, *rank;
+    int2 *okey;
+    int64_t pres_off;   // first entry of this image's presence segment
+    int maxd, hasinf;
+    int pres_base;      // pool total before the segment (device-written)
+    int B;              // distinct values (device-written, then read back)
+    int S, C, smem;     // chunk length, chunks, counters in shared memory
+    int64_t mat_off;    // first entry of this image's (bucket, chunk) matrix
+    int mat_base;       // pool total before the matrix (device-written)
+    int blk_vox, blk_chunk;   // first block of this image in the voxel / chunk launches
+};
+
+__device__ __forceinline__ int find_job(const SortJob *jobs, int n, int blk, bool chunk)
+{
+    int lo = 0, hi = n;   // largest j whose first block is <= blk
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if ((chunk ? jobs[mid].blk_chunk : jobs[mid].blk_vox) <= blk) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+constexpr int kVoxBlock = 256, kVoxPer = 8;   // voxel launches: 2048 voxels per block
+
+// seq = -1 on pore, 0 on solid; presence of each finite value
+__global__ void k_seq_pres_b(const SortJob *__restrict__ jobs, int n, int32_t *pres)
+{
+    const int j = find_job(jobs, n, blockIdx.x, false);
+    const SortJob &J = jobs[j];
+    const int64_t v0 = (int64_t)(blockIdx.x - J.blk_vox) * kVoxBlock * kVoxPer;
+    for (int q = 0; q < kVoxPer; q++) {
+        const int64_t v = v0 + q * kVoxBlock + threadIdx.x;
+        if (v >= J.N) break;
+        const int d = J.dt2[v];
+        J.seq[v] = d > 0 ? -1 : 0;
+        if (d > 0 && d != IBIP_INF32) pres[J.pres_off + d] = 1;
+    }
+}
+
+// after the flat inclusive scan of the presence pool: each image's base and
+// number of distinct values
+__global__ void k_pres_base_b(SortJob *jobs, int n, const int32_t *__restrict__ incl)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    SortJob &J = jobs[j];
+    const int base = J.pres_off > 0 ? incl[J.pres_off - 1] : 0;
+    J.pres_base = base;
+    J.B = J.hasinf ? 1 : incl[J.pres_off + J.maxd] - base;
+}
+
+__device__ __forceinline__ int bucket_b(const SortJob &J, const int32_t *__restrict__ incl, int d)
+{
+    if (d <= 0) return -1;
+    if (J.hasinf) return 0;
+    return J.B - (__ldg(incl + J.pres_off + d) - J.pres_base);
+}
+
+// k_chunk_hist for every image: one warp per chunk
+__global__ void k_chunk_hist_b(const SortJob *__restrict__ jobs, int n, const int32_t *__restrict__ incl,
+                               int32_t *mat)
+{
+    extern __shared__ int32_t s_cnt[];
+    const int j = find_job(jobs, n, blockIdx.x, true);
+    const SortJob &J = jobs[j];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int c = (blockIdx.x - J.blk_chunk) * (blockDim.x >> 5) + w;
+    if (c >= J.C) return;
+    int32_t *m = mat + J.mat_off;
+    int32_t *cnt = J.smem ? s_cnt + w * J.B : nullptr;
+    for (int b = lane; b < J.B; b += 32) {
+        if (J.smem) cnt[b] = 0; else m[(int64_t)b * J.C + c] = 0;
+    }
+    __syncwarp();
+    const int64_t v0 = (int64_t)c * J.S, v1 = min(J.N, v0 + J.S);
+    for (int64_t v = v0 + lane; v - lane < v1; v += 32) {
+        const int b = v < v1 ? bucket_b(J, incl, J.dt2[v]) : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, b);
+        const int leader = __ffs(peers) - 1;
+        if (lane == leader && b >= 0) {
+            if (J.smem) cnt[b] += __popc(peers);
+            else m[(int64_t)b * J.C + c] += __popc(peers);
+        }
+        __syncwarp();
+    }
+    if (J.smem)
+        for (int b = lane; b < J.B; b += 32) m[(int64_t)b * J.C + c] = cnt[b];
+}
+
+// after the flat exclusive scan of the matrix pool: each image's base
+__global__ void k_mat_base_b(SortJob *jobs, int n, const int32_t *__restrict__ mat)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) jobs[j].mat_base = mat[jobs[j].mat_off];
+}
+
+__global__ void k_chunk_scatter_b(const SortJob *__restrict__ jobs, int n, const int32_t *__restrict__ incl,
+                                  int32_t *mat)
+{
+    extern __shared__ int32_t s_cnt[];
+    const int j = find_job(jobs, n, blockIdx.x, true);
+    const SortJob &J = jobs[j];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int c = (blockIdx.x - J.blk_chunk) * (blockDim.x >> 5) + w;
+    if (c >= J.C) return;
+    int32_t *m = mat + J.mat_off;
+    int32_t *cnt = J.smem ? s_cnt + w * J.B : nullptr;
+    if (J.smem) {
+        for (int b = lane; b < J.B; b += 32) cnt[b] = m[(int64_t)b * J.C + c] - J.mat_base;
+        __syncwarp();
+    }
+    const int64_t v0 = (int64_t)c * J.S, v1 = min(J.N, v0 + J.S);
+    const unsigned lt = (1u << lane) - 1;
+    for (int64_t v = v0 + lane; v - lane < v1; v += 32) {
+        const int d = v < v1 ? J.dt2[v] : 0;
+        const int b = v < v1 ? bucket_b(J, incl, d) : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, b);
+        const int leader = __ffs(peers) - 1;
+        int base = 0;
+        if (lane == leader && b >= 0) base = J.smem ? cnt[b] : m[(int64_t)b * J.C + c] - J.mat_base;
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (b >= 0) {
+            const int r = base + __popc(peers & lt);
+            J.rank[v] = r;
+            J.okey[r] = make_int2((int)v, d);
+        } else if (v < v1) {
+            J.rank[v] = -1;
+        }
+        if (lane == leader && b >= 0) {
+            if (J.smem) cnt[b] = base + __popc(peers);
+            else m[(int64_t)b * J.C + c] = base + __popc(peers) + J.mat_base;
+        }
+        __syncwarp();
+    }
+}
+
 // ------------------------------------------------------- invasion state --
 
 struct Inv {
@@ -189,43 +334,47 @@ __global__ void k_seq_init(const int32_t *__restrict__ dt2, int64_t N, int32_t *
 // one thread per bit-plane word: avail bits (pore, not yet invaded) and the
 // first candidates: inlet voxels (the mask, else the inlet face) and, when
 // resuming, every uninvaded pore voxel next to an invaded one
+__device__ void plane_word(const Inv &a, int64_t w)
+{
+    int64_t row = w / a.NW;
+    int zw = (int)(w - row * a.NW);
+    int x = (int)(row / a.ny), y = (int)(row - (int64_t)x * a.ny);
+    uint32_t av = 0, ad = 0;
+    for (int b = 0; b < 32; b++) {
+        int z = zw * 32 + b;
+        if (z >= a.nz) break;
+        int64_t v = row * a.nz + z;
+        if (a.dt2[v] <= 0) continue;
+        if (a.resume && a.seq[v] != -1) continue;
+        av |= 1u << b;
+        bool cand = a.mask ? a.mask[v] != 0 : d_on_face(x, y, z, a.nx, a.ny, a.nz, a.inlet);
+        if (!cand && a.resume) {
+            const int nxs[6] = {x - 1, x + 1, x, x, x, x}, nys[6] = {y, y, y - 1, y + 1, y, y},
+                      nzs[6] = {z, z, z, z, z - 1, z + 1};
+            for (int q = 0; q < 6 && !cand; q++) {
+                if (nxs[q] < 0 || nys[q] < 0 || nzs[q] < 0 || nxs[q] >= a.nx || nys[q] >= a.ny || nzs[q] >= a.nz)
+                    continue;
+                cand = a.seq[d_lin(nxs[q], nys[q], nzs[q], a.ny, a.nz)] >= 1;
+            }
+        }
+        if (cand) {
+            ad |= 1u << b;
+            int r = a.rank[v];
+            atomicOr(a.fb0 + (r >> 6), 1ull << (r & 63));
+            atomicOr(a.fb1 + (r >> 12), 1ull << ((r >> 6) & 63));
+            atomicOr(a.fb2 + (r >> 18), 1ull << ((r >> 12) & 63));
+            atomicOr(a.fb3 + (r >> 24), 1ull << ((r >> 18) & 63));
+        }
+    }
+    a.avail[w] = av;
+    a.added[w] = ad;
+}
+
 __global__ void k_plane_init(Inv a)
 {
     const int64_t nw = (int64_t)a.nx * a.ny * a.NW;
-    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += (int64_t)gridDim.x * blockDim.x) {
-        int64_t row = w / a.NW;
-        int zw = (int)(w - row * a.NW);
-        int x = (int)(row / a.ny), y = (int)(row - (int64_t)x * a.ny);
-        uint32_t av = 0, ad = 0;
-        for (int b = 0; b < 32; b++) {
-            int z = zw * 32 + b;
-            if (z >= a.nz) break;
-            int64_t v = row * a.nz + z;
-            if (a.dt2[v] <= 0) continue;
-            if (a.resume && a.seq[v] != -1) continue;
-            av |= 1u << b;
-            bool cand = a.mask ? a.mask[v] != 0 : d_on_face(x, y, z, a.nx, a.ny, a.nz, a.inlet);
-            if (!cand && a.resume) {
-                const int nxs[6] = {x - 1, x + 1, x, x, x, x}, nys[6] = {y, y, y - 1, y + 1, y, y},
-                          nzs[6] = {z, z, z, z, z - 1, z + 1};
-                for (int q = 0; q < 6 && !cand; q++) {
-                    if (nxs[q] < 0 || nys[q] < 0 || nzs[q] < 0 || nxs[q] >= a.nx || nys[q] >= a.ny || nzs[q] >= a.nz)
-                        continue;
-                    cand = a.seq[d_lin(nxs[q], nys[q], nzs[q], a.ny, a.nz)] >= 1;
-                }
-            }
-            if (cand) {
-                ad |= 1u << b;
-                int r = a.rank[v];
-                atomicOr(a.fb0 + (r >> 6), 1ull << (r & 63));
-                atomicOr(a.fb1 + (r >> 12), 1ull << ((r >> 6) & 63));
-                atomicOr(a.fb2 + (r >> 18), 1ull << ((r >> 12) & 63));
-                atomicOr(a.fb3 + (r >> 24), 1ull << ((r >> 18) & 63));
-            }
-        }
-        a.avail[w] = av;
-        a.added[w] = ad;
-    }
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += (int64_t)gridDim.x * blockDim.x)
+        plane_word(a, w);
 }
 
 // n / d for 0 <= n < 2^31 and a run-time invariant d >= 1: one multiply-high
@@ -1146,7 +1295,21 @@ struct InvJob {
     Inv a;
     FastDiv fd_nyz, fd_nz;
     int *gC, *gD;
+    int blk_plane;   // first block of this image in the batched plane set-up
 };
+
+// bit-planes and first candidates of every image: one thread per word
+__global__ void k_plane_init_b(const InvJob *__restrict__ jobs, int n)
+{
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (jobs[mid].blk_plane <= (int)blockIdx.x) lo = mid; else hi = mid;
+    }
+    const Inv &a = jobs[lo].a;
+    const int64_t w = (int64_t)(blockIdx.x - jobs[lo].blk_plane) * blockDim.x + threadIdx.x;
+    if (w < (int64_t)a.nx * a.ny * a.NW) plane_word(a, w);
+}
 
 __global__ void __launch_bounds__(kNT, 1) k_invade_batch(const InvJob *__restrict__ jobs)
 {
@@ -1220,6 +1383,33 @@ JobMem carve(char *p, const JobSizes &z)
     return m;
 }
 
+// The invasion kernel's view of one image, its scratch carved as in `mem`.
+Inv make_inv(const int32_t *dt2, ibip_dims d, int inlet, int64_t max_steps, int32_t *seq, int32_t *step_r2,
+             int32_t *step_centre, int64_t cap, int maxd, int npore, const JobMem &mem, const uint8_t *mask,
+             int resume, int64_t k0)
+{
+    Inv a;
+    a.nx = d.nx; a.ny = d.ny; a.nz = d.nz; a.NW = (d.nz + 31) / 32; a.inlet = inlet;
+    a.NL0 = (npore + 63) / 64;
+    a.NL1 = (a.NL0 + 63) / 64;
+    a.NL2 = (a.NL1 + 63) / 64;
+    a.NL3 = (a.NL2 + 63) / 64;
+    a.max_steps = max_steps > INT64_MAX - k0 ? INT64_MAX : k0 + max_steps;   // a total
+    a.cap = cap;
+    a.mask = mask;
+    a.resume = resume;
+    a.k0 = k0;
+    a.npore = npore;
+    a.rank = mem.rank; a.okey = mem.okey; a.dt2 = dt2;
+    a.avail = mem.avail; a.added = mem.added;
+    a.fb0 = mem.fb; a.fb1 = mem.fb + a.NL0; a.fb2 = a.fb1 + a.NL1; a.fb3 = a.fb2 + a.NL2;
+    a.seq = seq; a.step_r2 = step_r2; a.step_centre = step_centre; a.out = mem.out;
+    a.isq_n = std::min(maxd + 1, 16384);
+    return a;
+}
+
+size_t fb_words(const Inv &a) { return (size_t)a.NL0 + a.NL1 + a.NL2 + a.NL3; }
+
 // Rank sort, sequence initialisation and bit-plane / bitmap set-up of one
 // invasion whose pore statistics (largest finite dt2, pore count, whether
 // dt2 is infinite) are known.  Queued on the context stream; synchronises
@@ -1273,25 +1463,8 @@ int invade_setup(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, int6
     else k_chunk_scatter<false><<<nb, wpb * 32, 0, s>>>(dt2, N, (int)S, C, bk, mat, mem.rank, mem.okey);
     IBIP_LAUNCH(ctx);
     // -- bit-planes and the candidate bitmap
-    Inv a;
-    a.nx = d.nx; a.ny = d.ny; a.nz = d.nz; a.NW = (d.nz + 31) / 32; a.inlet = inlet;
-    a.NL0 = (npore + 63) / 64;
-    a.NL1 = (a.NL0 + 63) / 64;
-    a.NL2 = (a.NL1 + 63) / 64;
-    a.NL3 = (a.NL2 + 63) / 64;
-    a.max_steps = max_steps > INT64_MAX - k0 ? INT64_MAX : k0 + max_steps;   // a total
-    a.cap = cap;
-    a.mask = mask;
-    a.resume = resume;
-    a.k0 = k0;
-    a.npore = npore;
-    a.rank = mem.rank; a.okey = mem.okey; a.dt2 = dt2;
-    a.avail = mem.avail; a.added = mem.added;
-    const size_t nfb = (size_t)a.NL0 + a.NL1 + a.NL2 + a.NL3;
-    a.fb0 = mem.fb; a.fb1 = mem.fb + a.NL0; a.fb2 = a.fb1 + a.NL1; a.fb3 = a.fb2 + a.NL2;
-    a.seq = seq; a.step_r2 = step_r2; a.step_centre = step_centre; a.out = mem.out;
-    a.isq_n = std::min(maxd + 1, 16384);
-    cudaMemsetAsync(mem.fb, 0, nfb * sizeof(u64), s);
+    Inv a = make_inv(dt2, d, inlet, max_steps, seq, step_r2, step_centre, cap, maxd, npore, mem, mask, resume, k0);
+    cudaMemsetAsync(mem.fb, 0, fb_words(a) * sizeof(u64), s);
     k_plane_init<<<gs, 256, 0, s>>>(a);
     IBIP_LAUNCH(ctx);
     *out_a = a;
@@ -1414,33 +1587,101 @@ int ibip_invade_batch_run(ibip_ctx *ctx, int n, IbipBatchItem *it)
     }
     char *arena = (char *)ibip_scratch(ctx, SC_BARENA, total + 256);
     if (!arena) return IBIP_ERR_OOM;
-    // per-image set-up, then one launch with the largest images first
     std::vector<InvJob> jobs;
     std::vector<int> idx;
     std::vector<int64_t *> outs(n, nullptr);
     size_t off = 0, dyn = 0;
+    // images with pore: one sort job each; the others only need seq
+    std::vector<SortJob> sj;
+    std::vector<JobMem> mems;
+    int64_t pres_total = 0, pore_total = 0;
+    int blk_vox = 0;
     for (int j = 0; j < n; j++) {
         if (npore[j] == 0) {
             k_seq_init<<<ctx->sm_count * 2, 256, 0, s>>>(it[j].dt2, nvox(it[j].d), it[j].seq);
             IBIP_LAUNCH(ctx);
             continue;
         }
+        pore_total += npore[j];
+        if (pore_total >= (1ll << 31)) return IBIP_ERR_ARG;   // the whole batch's ranks share one int32 scan
         const JobMem mem = carve(arena + off, z[j]);
         off += z[j].total();
-        InvJob J;
-        int st = invade_setup(ctx, it[j].dt2, it[j].d, it[j].inlet, it[j].max_steps, it[j].seq, it[j].step_r2,
-                              it[j].step_centre, it[j].cap, maxd[j], npore[j], hasinf[j], mem, &J.a);
+        SortJob q = {};
+        q.dt2 = it[j].dt2; q.N = nvox(it[j].d); q.seq = it[j].seq; q.rank = mem.rank; q.okey = mem.okey;
+        q.maxd = hasinf[j] ? 0 : maxd[j]; q.hasinf = hasinf[j];
+        q.pres_off = pres_total;
+        pres_total += (int64_t)q.maxd + 1;
+        q.blk_vox = blk_vox;
+        blk_vox += (int)((q.N + kVoxBlock * kVoxPer - 1) / (kVoxBlock * kVoxPer));
+        sj.push_back(q);
+        mems.push_back(mem);
+        idx.push_back(j);
+    }
+    const int m0 = (int)sj.size();
+    if (m0 > 0) {
+        // presence of every value: one scan and one read-back for all images
+        const size_t tab = ((size_t)m0 * sizeof(SortJob) + 255) / 256 * 256;
+        char *sw = (char *)ibip_scratch(ctx, SC_BSORT, tab + (size_t)pres_total * 4);
+        if (!sw) return IBIP_ERR_OOM;
+        SortJob *djobs = (SortJob *)sw;
+        int32_t *pres = (int32_t *)(sw + tab);
+        cudaMemcpyAsync(djobs, sj.data(), (size_t)m0 * sizeof(SortJob), cudaMemcpyHostToDevice, s);
+        cudaMemsetAsync(pres, 0, (size_t)pres_total * 4, s);
+        k_seq_pres_b<<<blk_vox, kVoxBlock, 0, s>>>(djobs, m0, pres);
+        IBIP_LAUNCH(ctx);
+        int st = ibip_scan_incl_i32(ctx, pres, pres, pres_total);
         if (st) return st;
+        k_pres_base_b<<<(m0 + 127) / 128, 128, 0, s>>>(djobs, m0, pres);
+        IBIP_LAUNCH(ctx);
+        cudaMemcpyAsync(sj.data(), djobs, (size_t)m0 * sizeof(SortJob), cudaMemcpyDeviceToHost, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) return IBIP_ERR_CUDA;
+        // chunking of each image's counting sort, as in the one-image set-up
+        const int wpb = 4;
+        int64_t mat_total = 0;
+        int blk_chunk = 0, maxBs = 1;
+        for (auto &q : sj) {
+            int64_t S = kChunk;
+            const int64_t mat_lim = std::max(q.N / 4, (int64_t)1 << 20);
+            while (S < q.N && (q.N + S - 1) / S * (int64_t)q.B > mat_lim) S *= 2;
+            q.S = (int)S;
+            q.C = (int)((q.N + S - 1) / S);
+            q.smem = q.B <= 1024;
+            if (q.smem) maxBs = std::max(maxBs, q.B);
+            q.mat_off = mat_total;
+            mat_total += (int64_t)q.C * q.B;
+            q.blk_chunk = blk_chunk;
+            blk_chunk += (q.C + wpb - 1) / wpb;
+        }
+        if (mat_total >= (1ll << 31)) return IBIP_ERR_ARG;
+        int32_t *mat = (int32_t *)ibip_scratch(ctx, SC_MAT, (size_t)mat_total * sizeof(int32_t));
+        if (!mat) return IBIP_ERR_OOM;
+        cudaMemcpyAsync(djobs, sj.data(), (size_t)m0 * sizeof(SortJob), cudaMemcpyHostToDevice, s);
+        const size_t sm = (size_t)wpb * maxBs * sizeof(int32_t);
+        k_chunk_hist_b<<<blk_chunk, wpb * 32, sm, s>>>(djobs, m0, pres, mat);
+        IBIP_LAUNCH(ctx);
+        st = ibip_scan_excl_i32(ctx, mat, mat, mat_total);
+        if (st) return st;
+        k_mat_base_b<<<(m0 + 127) / 128, 128, 0, s>>>(djobs, m0, mat);
+        IBIP_LAUNCH(ctx);
+        k_chunk_scatter_b<<<blk_chunk, wpb * 32, sm, s>>>(djobs, m0, pres, mat);
+        IBIP_LAUNCH(ctx);
+    }
+    for (int q = 0; q < m0; q++) {
+        const int j = idx[q];
+        const JobMem &mem = mems[q];
+        InvJob J;
+        J.a = make_inv(it[j].dt2, it[j].d, it[j].inlet, it[j].max_steps, it[j].seq, it[j].step_r2, it[j].step_centre,
+                       it[j].cap, maxd[j], npore[j], mem, nullptr, 0, 0);
+        cudaMemsetAsync(mem.fb, 0, fb_words(J.a) * sizeof(u64), s);
         J.fd_nyz = make_fastdiv((uint32_t)it[j].d.ny * (uint32_t)it[j].d.nz);
         J.fd_nz = make_fastdiv((uint32_t)it[j].d.nz);
         J.gC = mem.gl;
         J.gD = mem.gl + npore[j];
+        J.blk_plane = 0;
         dyn = std::max(dyn, invade_dyn_smem(J.a, true));
         outs[j] = mem.out;
         jobs.push_back(J);
-        idx.push_back(j);
     }
-    ibip_prof_end(ctx, IBIP_K_RANK);
     const int m = (int)jobs.size();
     if (m > 0) {
         std::vector<int> order(m);
@@ -1449,10 +1690,19 @@ int ibip_invade_batch_run(ibip_ctx *ctx, int n, IbipBatchItem *it)
             return nvox(it[idx[a]].d) > nvox(it[idx[b]].d);
         });
         std::vector<InvJob> sorted(m);
-        for (int q = 0; q < m; q++) sorted[q] = jobs[order[q]];
+        int blk_plane = 0;
+        for (int q = 0; q < m; q++) {
+            sorted[q] = jobs[order[q]];
+            sorted[q].blk_plane = blk_plane;
+            const Inv &a = sorted[q].a;
+            blk_plane += (int)(((int64_t)a.nx * a.ny * a.NW + 255) / 256);
+        }
         InvJob *djobs = (InvJob *)ibip_scratch(ctx, SC_BJOBS, (size_t)m * sizeof(InvJob));
         if (!djobs) return IBIP_ERR_OOM;
         cudaMemcpyAsync(djobs, sorted.data(), (size_t)m * sizeof(InvJob), cudaMemcpyHostToDevice, s);
+        k_plane_init_b<<<blk_plane, 256, 0, s>>>(djobs, m);
+        IBIP_LAUNCH(ctx);
+        ibip_prof_end(ctx, IBIP_K_RANK);
         ibip_prof_begin(ctx, IBIP_K_INVADE);
         allow_max_dyn_smem((const void *)k_invade_batch);
         k_invade_batch<<<m, kNT, dyn, s>>>(djobs);
@@ -1468,6 +1718,7 @@ int ibip_invade_batch_run(ibip_ctx *ctx, int n, IbipBatchItem *it)
             it[idx[q]].status = (int)ho[2 * q + 1];
         }
     } else {
+        ibip_prof_end(ctx, IBIP_K_RANK);
         cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return ibip_cuda_status(e);
     }
