@@ -392,7 +392,9 @@ IBIP_API int ibip_profile_read(ibip_ctx *ctx, int cls, double *h_ms, int64_t *h_
  * pairwise tests, bookkeeping) and the three phase cycles of single-voxel
  * batches, iterations, steps and cycles of the single-voxel loop, then
  * gather sub-phase cycles for the two loops and the single-voxel loop's
- * phase cycles]; n <= 35 entries. */
+ * phase cycles]; entries 30-32 hold the rounds, tile activations and
+ * relaxation sweeps of the context's last widest-path propagation
+ * (trapping or the opening's trim, one-launch form); n <= 36 entries. */
 IBIP_API int ibip_invade_stats(const ibip_ctx *ctx, int64_t *h_stats, int n);
 
 /* Static text for a status code. */

@@ -91,13 +91,16 @@ struct MMArgs {
     int *list0, *list1;   // work lists of global tile ids, alternating by round
     int *count, *head;    // per-round list sizes and take counters [max_rounds + 2]
     int *mark;            // per tile: last round it was queued for
-    int *status;          // [0] rounds run, [1] 1 if the round cap was hit
+    int *status;          // [0] rounds run, [1] 1 if the round cap was hit, [2] relaxation sweeps
     int max_rounds;
 };
 
 // Claims and relaxes the tiles of round r's list until the list is drained.
-// Tiles that changed queue their neighbours for round r + 1.
-__device__ void mm_round(const MMArgs &a, int r, int32_t (*sM)[TY + 2][TZ + 2], int *s_tile)
+// A tile queues a neighbour for round r + 1 only where one of its face
+// voxels rose in this activation above the neighbour's value across that
+// face (as loaded): M only grows, so no other neighbour can improve.  In
+// round 0 the seeded values count as risen.
+__device__ void mm_round(const MMArgs &a, int r, int32_t (*sM)[TY + 2][TZ + 2], int *s_tile, int *s_wake)
 {
     const int cnt = __ldcg(a.count + r);
     const int *list = (r & 1) ? a.list1 : a.list0;
@@ -136,9 +139,15 @@ __device__ void mm_round(const MMArgs &a, int r, int32_t (*sM)[TY + 2][TZ + 2], 
             const int x = x0 + lx[k], y = y0 + ly[k], z = z0 + lz[k];
             sval[k] = (x < J.nx && y < J.ny && z < J.nz) ? as_val(J.val[d_lin(x, y, z, J.ny, J.nz)]) : 0;
         }
+        if (threadIdx.x < 6) s_wake[threadIdx.x] = 0;
         __syncthreads();
+        int mold[kPer];
+#pragma unroll
+        for (int k = 0; k < kPer; k++) mold[k] = r == 0 ? -1 : sM[lx[k] + 1][ly[k] + 1][lz[k] + 1];
         bool any = false, conv = false;
+        int sweeps = 0;
         for (int it = 0; it < kInner; it++) {
+            sweeps++;
             int ch = 0;
 #pragma unroll
             for (int k = 0; k < kPer; k++) {
@@ -152,29 +161,42 @@ __device__ void mm_round(const MMArgs &a, int r, int32_t (*sM)[TY + 2][TZ + 2], 
             if (!__syncthreads_or(ch)) { conv = true; break; }
             any = true;
         }
-        // the first round's tiles hold the seeds: they always wake their
-        // neighbours (a tile that is only the face layer does not change)
-        if (any || r == 0) {
+        if (threadIdx.x == 0) atomicAdd(a.status + 2, sweeps);
+#pragma unroll
+        for (int k = 0; k < kPer; k++) {
+            if (sval[k] == 0) continue;
+            const int hx = lx[k] + 1, hy = ly[k] + 1, hz = lz[k] + 1;
+            const int mv = sM[hx][hy][hz];
+            if (mv <= mold[k]) continue;   // not risen here
+            if (lx[k] == 0 && mv > sM[0][hy][hz]) s_wake[0] = 1;
+            if (lx[k] == TX - 1 && mv > sM[TX + 1][hy][hz]) s_wake[1] = 1;
+            if (ly[k] == 0 && mv > sM[hx][0][hz]) s_wake[2] = 1;
+            if (ly[k] == TY - 1 && mv > sM[hx][TY + 1][hz]) s_wake[3] = 1;
+            if (lz[k] == 0 && mv > sM[hx][hy][0]) s_wake[4] = 1;
+            if (lz[k] == TZ - 1 && mv > sM[hx][hy][TZ + 1]) s_wake[5] = 1;
+        }
+        __syncthreads();
+        if (any) {
 #pragma unroll
             for (int k = 0; k < kPer; k++) {
                 const int x = x0 + lx[k], y = y0 + ly[k], z = z0 + lz[k];
                 if (x < J.nx && y < J.ny && z < J.nz && sval[k] != 0)
                     J.M[d_lin(x, y, z, J.ny, J.nz)] = sM[lx[k] + 1][ly[k] + 1][lz[k] + 1];
             }
-            if (threadIdx.x == 0) {
-                const int nr = r + 1;
-                int nb[7] = {-1, -1, -1, -1, -1, -1, -1};
-                if (bx > 0) nb[0] = g - J.tz * J.ty;
-                if (bx < J.tx - 1) nb[1] = g + J.tz * J.ty;
-                if (by > 0) nb[2] = g - J.tz;
-                if (by < J.ty - 1) nb[3] = g + J.tz;
-                if (bz > 0) nb[4] = g - 1;
-                if (bz < J.tz - 1) nb[5] = g + 1;
-                if (!conv) nb[6] = g;
-                for (int q = 0; q < 7; q++) {
-                    if (nb[q] < 0) continue;
-                    if (atomicMax(&a.mark[nb[q]], nr) < nr) next[atomicAdd(&a.count[nr], 1)] = nb[q];
-                }
+        }
+        if (threadIdx.x == 0) {
+            const int nr = r + 1;
+            int nb[7] = {-1, -1, -1, -1, -1, -1, -1};
+            if (bx > 0 && s_wake[0]) nb[0] = g - J.tz * J.ty;
+            if (bx < J.tx - 1 && s_wake[1]) nb[1] = g + J.tz * J.ty;
+            if (by > 0 && s_wake[2]) nb[2] = g - J.tz;
+            if (by < J.ty - 1 && s_wake[3]) nb[3] = g + J.tz;
+            if (bz > 0 && s_wake[4]) nb[4] = g - 1;
+            if (bz < J.tz - 1 && s_wake[5]) nb[5] = g + 1;
+            if (!conv) nb[6] = g;
+            for (int q = 0; q < 7; q++) {
+                if (nb[q] < 0) continue;
+                if (atomicMax(&a.mark[nb[q]], nr) < nr) next[atomicAdd(&a.count[nr], 1)] = nb[q];
             }
         }
         __syncthreads();
@@ -186,11 +208,11 @@ __global__ void __launch_bounds__(kThreads) k_mm_persistent(MMArgs a)
 {
     cg::grid_group grid = cg::this_grid();
     __shared__ int32_t sM[TX + 2][TY + 2][TZ + 2];
-    __shared__ int s_tile;
+    __shared__ int s_tile, s_wake[6];
     int r = 0;
     for (;; r++) {
         if (__ldcg(a.count + r) == 0 || r >= a.max_rounds) break;
-        mm_round(a, r, sM, &s_tile);
+        mm_round(a, r, sM, &s_tile, s_wake);
         __threadfence();
         grid.sync();
     }
@@ -205,9 +227,9 @@ __global__ void __launch_bounds__(kThreads) k_mm_persistent(MMArgs a)
 __global__ void __launch_bounds__(kThreads) k_mm_round(MMArgs a, int r)
 {
     __shared__ int32_t sM[TX + 2][TY + 2][TZ + 2];
-    __shared__ int s_tile;
+    __shared__ int s_tile, s_wake[6];
     if (r >= a.max_rounds || __ldcg(a.count + r) == 0) return;
-    mm_round(a, r, sM, &s_tile);
+    mm_round(a, r, sM, &s_tile, s_wake);
 }
 
 }  // namespace
@@ -245,7 +267,7 @@ int ibip_maximin_multi(ibip_ctx *ctx, int n, const IbipMaximinJob *jobs, int max
     ibip_prof_begin(ctx, IBIP_K_MAXIMIN);
     cudaMemcpyAsync(djobs, J.data(), (size_t)n * sizeof(MMJob), cudaMemcpyHostToDevice, s);
     cudaMemsetAsync(a.mark, 0xff, (size_t)nt * sizeof(int), s);   // -1: never queued
-    cudaMemsetAsync(a.count, 0, (2 * ((size_t)rounds + 2) + 4) * sizeof(int), s);
+    cudaMemsetAsync(a.count, 0, (2 * ((size_t)rounds + 2) + 4) * sizeof(int), s);   // counts, heads, status
     for (int j = 0; j < n; j++) {
         k_mm_init<<<ctx->sm_count * 4, 256, 0, s>>>(J[j].val, J[j].nx, J[j].ny, J[j].nz, J[j].face, J[j].M);
         IBIP_LAUNCH(ctx);
@@ -288,11 +310,26 @@ int ibip_maximin_multi(ibip_ctx *ctx, int n, const IbipMaximinJob *jobs, int max
     cudaError_t e = cudaLaunchCooperativeKernel((void *)k_mm_persistent, grid, kThreads, args, 0, s);
     IBIP_LAUNCH(ctx);
     if (e != cudaSuccess) return ibip_cuda_status(e);
-    cudaMemcpyAsync(h, a.status, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(h, a.status, 3 * sizeof(int), cudaMemcpyDeviceToHost, s);
     e = cudaStreamSynchronize(s);
     ibip_prof_end(ctx, IBIP_K_MAXIMIN);
     if (e != cudaSuccess) return ibip_cuda_status(e);
-    return h[1] ? IBIP_ERR_NOT_CONVERGED : IBIP_OK;
+    // diagnostics of the last propagation: rounds, tile activations, sweeps
+    {
+        const int nr = h[0] < rounds ? h[0] : rounds, conv_flag = h[1], sweeps = h[2];
+        int *hc = (int *)ctx->h_pinned;
+        int64_t act = 0;
+        for (int r0 = 0; r0 < nr; r0 += 8192) {
+            const int c = nr - r0 < 8192 ? nr - r0 : 8192;
+            cudaMemcpyAsync(hc, a.count + r0, (size_t)c * sizeof(int), cudaMemcpyDeviceToHost, s);
+            if (cudaStreamSynchronize(s) != cudaSuccess) return IBIP_ERR_CUDA;
+            for (int q = 0; q < c; q++) act += hc[q];
+        }
+        ctx->inv_stats[30] = nr;
+        ctx->inv_stats[31] = act;
+        ctx->inv_stats[32] = sweeps;
+        return conv_flag ? IBIP_ERR_NOT_CONVERGED : IBIP_OK;
+    }
 }
 
 int ibip_maximin_launch(ibip_ctx *ctx, const int32_t *val, ibip_dims d, int face, int32_t *M, int max_rounds)

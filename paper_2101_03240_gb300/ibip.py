@@ -212,7 +212,10 @@ class Context:
         a = (C.c_int64 * 36)()
         _lib().ibip_invade_stats(self._h, a, 36)
         keys = ["steps", "status", "iterations", "cycles_select", "cycles_bound", "cycles_commit", "items",
-                "items_committed", "stale_bits", "rows_committed", "cycles_small_batches", "small_batches", "sel_gather", "sel_items", "sel_pairs", "sel_tail", "small_select", "small_bound", "small_commit", "tiny_iterations", "tiny_steps", "cycles_tiny", "s3_cont", "s3_prefix", "g_scan", "g_extract", "g_items", "t_walk", "t_words", "t_scan", "t_extract", "t_items", "tiny_gather", "tiny_bound", "tiny_commit"]
+                "items_committed", "stale_bits", "rows_committed", "cycles_small_batches", "small_batches",
+                "sel_gather", "sel_items", "sel_pairs", "sel_tail", "small_select", "small_bound", "small_commit",
+                "tiny_iterations", "tiny_steps", "cycles_tiny", "s3_cont", "s3_prefix", "g_scan", "g_extract",
+                "g_items", "t_walk", "t_words", "t_scan", "mm_rounds", "mm_activations", "mm_sweeps"]
         return dict(zip(keys, [int(x) for x in a]))
 
     def synchronize(self):
