@@ -122,23 +122,36 @@ __device__ void mm_round(const MMArgs &a, int r, int32_t (*sM)[TY + 2][TZ + 2], 
         const int t = g - J.tile0;
         const int bz = t % J.tz, by = (t / J.tz) % J.ty, bx = t / (J.tz * J.ty);
         const int x0 = bx * TX, y0 = by * TY, z0 = bz * TZ;
-        // tile + one-voxel halo of the field
-        for (int i = threadIdx.x; i < (TX + 2) * (TY + 2) * (TZ + 2); i += kThreads) {
-            const int hz = i % (TZ + 2), hy = (i / (TZ + 2)) % (TY + 2), hx = i / ((TZ + 2) * (TY + 2));
-            const int x = x0 + hx - 1, y = y0 + hy - 1, z = z0 + hz - 1;
-            int m = -1;
-            if (x >= 0 && y >= 0 && z >= 0 && x < J.nx && y < J.ny && z < J.nz)
-                m = __ldcg(J.M + d_lin(x, y, z, J.ny, J.nz));
-            sM[hx][hy][hz] = m;
-        }
+        // the tile's values and the field on the tile plus a one-voxel halo:
+        // every load is issued before the first store to shared memory
         int sval[kPer], lx[kPer], ly[kPer], lz[kPer];
 #pragma unroll
         for (int k = 0; k < kPer; k++) {
             const int i = threadIdx.x + k * kThreads;
             lz[k] = i % TZ; ly[k] = (i / TZ) % TY; lx[k] = i / (TZ * TY);
             const int x = x0 + lx[k], y = y0 + ly[k], z = z0 + lz[k];
-            sval[k] = (x < J.nx && y < J.ny && z < J.nz) ? as_val(J.val[d_lin(x, y, z, J.ny, J.nz)]) : 0;
+            sval[k] = (x < J.nx && y < J.ny && z < J.nz) ? J.val[d_lin(x, y, z, J.ny, J.nz)] : 0;
         }
+        constexpr int kHalo = (TX + 2) * (TY + 2) * (TZ + 2);
+        constexpr int kHaloPer = (kHalo + kThreads - 1) / kThreads;
+        int hv[kHaloPer];
+#pragma unroll
+        for (int u = 0; u < kHaloPer; u++) {
+            const int i = threadIdx.x + u * kThreads;
+            const int hz = i % (TZ + 2), hy = (i / (TZ + 2)) % (TY + 2), hx = i / ((TZ + 2) * (TY + 2));
+            const int x = x0 + hx - 1, y = y0 + hy - 1, z = z0 + hz - 1;
+            hv[u] = -1;
+            if (i < kHalo && x >= 0 && y >= 0 && z >= 0 && x < J.nx && y < J.ny && z < J.nz)
+                hv[u] = __ldcg(J.M + d_lin(x, y, z, J.ny, J.nz));
+        }
+        int32_t *sflat = &sM[0][0][0];
+#pragma unroll
+        for (int u = 0; u < kHaloPer; u++) {
+            const int i = threadIdx.x + u * kThreads;
+            if (i < kHalo) sflat[i] = hv[u];
+        }
+#pragma unroll
+        for (int k = 0; k < kPer; k++) sval[k] = as_val(sval[k]);
         if (threadIdx.x < 6) s_wake[threadIdx.x] = 0;
         __syncthreads();
         int mold[kPer];
@@ -184,20 +197,19 @@ __device__ void mm_round(const MMArgs &a, int r, int32_t (*sM)[TY + 2][TZ + 2], 
                     J.M[d_lin(x, y, z, J.ny, J.nz)] = sM[lx[k] + 1][ly[k] + 1][lz[k] + 1];
             }
         }
-        if (threadIdx.x == 0) {
-            const int nr = r + 1;
-            int nb[7] = {-1, -1, -1, -1, -1, -1, -1};
-            if (bx > 0 && s_wake[0]) nb[0] = g - J.tz * J.ty;
-            if (bx < J.tx - 1 && s_wake[1]) nb[1] = g + J.tz * J.ty;
-            if (by > 0 && s_wake[2]) nb[2] = g - J.tz;
-            if (by < J.ty - 1 && s_wake[3]) nb[3] = g + J.tz;
-            if (bz > 0 && s_wake[4]) nb[4] = g - 1;
-            if (bz < J.tz - 1 && s_wake[5]) nb[5] = g + 1;
-            if (!conv) nb[6] = g;
-            for (int q = 0; q < 7; q++) {
-                if (nb[q] < 0) continue;
-                if (atomicMax(&a.mark[nb[q]], nr) < nr) next[atomicAdd(&a.count[nr], 1)] = nb[q];
+        if (threadIdx.x < 7) {   // one lane per neighbour (6) and the tile itself: the atomics overlap
+            const int q = threadIdx.x, nr = r + 1;
+            int nb = -1;
+            switch (q) {
+            case 0: if (bx > 0 && s_wake[0]) nb = g - J.tz * J.ty; break;
+            case 1: if (bx < J.tx - 1 && s_wake[1]) nb = g + J.tz * J.ty; break;
+            case 2: if (by > 0 && s_wake[2]) nb = g - J.tz; break;
+            case 3: if (by < J.ty - 1 && s_wake[3]) nb = g + J.tz; break;
+            case 4: if (bz > 0 && s_wake[4]) nb = g - 1; break;
+            case 5: if (bz < J.tz - 1 && s_wake[5]) nb = g + 1; break;
+            default: if (!conv) nb = g; break;
             }
+            if (nb >= 0 && atomicMax(&a.mark[nb], nr) < nr) next[atomicAdd(&a.count[nr], 1)] = nb;
         }
         __syncthreads();
     }
