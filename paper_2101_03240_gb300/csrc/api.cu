@@ -457,17 +457,21 @@ int ibip_invade_batched(ibip_ctx *ctx, int32_t n, ibip_job *jobs)
     int32_t *pool = need_dt2 ? (int32_t *)ibip_scratch(ctx, SC_BDT2, (size_t)need_dt2 * sizeof(int32_t)) : nullptr;
     if (need_dt2 && !pool) return IBIP_ERR_OOM;
     std::vector<IbipBatchItem> it(n);
+    std::vector<const uint8_t *> ims(n);
+    std::vector<ibip_dims> dms(n);
+    std::vector<int32_t *> dts(n);
     int64_t off = 0;
     for (int j = 0; j < n; j++) {
         ibip_job &J = jobs[j];
         int32_t *d = J.dt2;
         if (!d) { d = pool + off; off += (nvox(J.dims) + 63) & ~(int64_t)63; }
-        int st = ibip_edt_launch(ctx, J.image, J.dims, d);
-        if (st) return st;
+        ims[j] = J.image; dms[j] = J.dims; dts[j] = d;
         it[j] = IbipBatchItem{d, J.dims, J.inlet, nvox(J.dims), J.seq, J.step_r2, J.step_centre,
                               J.capacity_steps, 0, 0};
     }
-    int st = ibip_invade_batch_run(ctx, n, it.data());
+    int st = ibip_edt_batch_launch(ctx, n, ims.data(), dms.data(), dts.data());
+    if (st) return st;
+    st = ibip_invade_batch_run(ctx, n, it.data());
     if (st) return st;
     int first_bad = IBIP_OK;
     // trapping: one widest-path propagation over every image that asks for it
@@ -492,23 +496,28 @@ int ibip_invade_batched(ibip_ctx *ctx, int32_t n, ibip_job *jobs)
         int64_t o = 0;
         for (auto &m : mj) { m.M = M + o; o += (nvox(m.d) + 63) & ~(int64_t)63; }
         st = ibip_maximin_multi(ctx, (int)mj.size(), mj.data(), kMaxRounds);
-        for (size_t q = 0; q < mj.size(); q++) {
-            ibip_job &J = jobs[mj_of[q]];
-            int sq = st ? st : ibip_trap_finish(ctx, J.seq, mj[q].M, J.dims, 0, J.trapped, J.seq_out);
-            if (sq) { J.status = sq; if (first_bad == IBIP_OK) first_bad = sq; }
+        if (st) {
+            for (size_t q = 0; q < mj.size(); q++) {
+                jobs[mj_of[q]].status = st;
+                if (first_bad == IBIP_OK) first_bad = st;
+            }
         }
     }
+    // trapped masks and curves of every image: one launch per stage
+    std::vector<IbipCurveItem> ci;
+    std::vector<const int32_t *> Mof(n, nullptr);
+    for (size_t q = 0; q < mj.size(); q++) Mof[mj_of[q]] = mj[q].M;
+    const double pi = 3.14159265358979323846;
     for (int j = 0; j < n; j++) {
         ibip_job &J = jobs[j];
         if (J.status != IBIP_OK) continue;
-        const int32_t *curve_seq = (J.trapped && J.seq_out) ? J.seq_out : J.seq;
-        if (J.sat_per_step) {
-            const double pi = 3.14159265358979323846;
-            st = ibip_pc_launch(ctx, curve_seq, J.dims, J.step_r2, J.n_steps, J.voxel_m, J.sigma,
-                                cos(J.theta_deg * pi / 180.0), J.sat_per_step, J.pc_per_step, nullptr);
-            if (st) { J.status = st; if (first_bad == IBIP_OK) first_bad = st; }
-        }
+        const int32_t *M = J.trapped ? Mof[j] : nullptr;
+        if (!M && !J.sat_per_step) continue;
+        ci.push_back(IbipCurveItem{J.seq, M, J.trapped, J.seq_out, J.step_r2, J.sat_per_step, J.pc_per_step, J.dims,
+                                   J.n_steps, J.voxel_m, J.sigma, cos(J.theta_deg * pi / 180.0)});
     }
+    st = ibip_curve_batch_launch(ctx, (int)ci.size(), ci.data());
+    if (st) return st;
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return ibip_cuda_status(e);
     return first_bad;

@@ -96,6 +96,9 @@ static inline int64_t nvox(ibip_dims d) { return (int64_t)d.nx * d.ny * d.nz; }
 // ---- internal launchers (one file each) ---------------------------------
 // EDT: feature = (image == 0).  Output dt2.
 int ibip_edt_launch(ibip_ctx *ctx, const uint8_t *image, ibip_dims d, int32_t *dt2);
+// The same for n images, one launch per pass (batched call).
+int ibip_edt_batch_launch(ibip_ctx *ctx, int n, const uint8_t *const *images, const ibip_dims *dims,
+                          int32_t *const *dt2);
 // MIO helper: for feature = (W >= T), marks level[v] = lvl where level[v] == -1
 // and the squared distance to the feature set is < T.
 int ibip_dilate_level_launch(ibip_ctx *ctx, const int32_t *W, int32_t T, int32_t lvl, ibip_dims d,
@@ -127,6 +130,19 @@ int ibip_literal_run(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, 
 // Equal-saturation comparison of a sequence image with opening levels.
 int ibip_eqsat_launch(ibip_ctx *ctx, const int32_t *seq, const int32_t *level, ibip_dims d, int64_t K, int L,
                       int64_t *h_steps, int64_t *h_diff, int64_t *h_count);
+// Trapped mask and saturation / Pc curve of many images in one launch per
+// stage (batched call): M null = no trapping, S null = no curve.
+struct IbipCurveItem {
+    const int32_t *seq, *M;
+    uint8_t *trapped;
+    int32_t *seq_out;
+    const int32_t *r2;
+    float *S, *Pc;
+    ibip_dims d;
+    int64_t K;
+    double voxel, sigma, cos_theta;
+};
+int ibip_curve_batch_launch(ibip_ctx *ctx, int n, const IbipCurveItem *items);
 // Scans.
 int ibip_scan_excl_i32(ibip_ctx *ctx, const int32_t *in, int32_t *out, int64_t n);
 int ibip_scan_incl_i32(ibip_ctx *ctx, const int32_t *in, int32_t *out, int64_t n);

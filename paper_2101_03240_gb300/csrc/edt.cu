@@ -13,6 +13,9 @@
 // evaluate each output by a search that widens from j = i outwards and stops
 // once (i-j)^2 alone reaches the best value (or the optional cap): exact,
 // integer-only, and proportional to the distance itself.
+#include <algorithm>
+#include <vector>
+
 #include "common.cuh"
 
 namespace {
@@ -109,12 +112,12 @@ __global__ void k_first_level(const int32_t *__restrict__ W, int64_t N, const in
 // then right to left for the nearest on the right (min-scan), writing the
 // distances as packed 16-byte stores.
 template <class Feat>
-__global__ void __launch_bounds__(kZWarps * 32) k_edt_z(Feat feat, int nrows, int nz, int cap,
-                                                        uint16_t *__restrict__ d1)
+__device__ __forceinline__ void edt_z_block(const Feat &feat, int blk, int nrows, int nz, int cap,
+                                            uint16_t *__restrict__ d1)
 {
     extern __shared__ unsigned char s_zraw[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t row = (int64_t)blockIdx.x * kZWarps + w;
+    const int64_t row = (int64_t)blk * kZWarps + w;
     if (row >= nrows) return;   // whole warps only; no block barrier follows
     const int ntile = (nz + 511) >> 9;
     uint16_t *s_m = (uint16_t *)s_zraw + (size_t)w * ntile * 32;
@@ -177,6 +180,13 @@ __global__ void __launch_bounds__(kZWarps * 32) k_edt_z(Feat feat, int nrows, in
     }
 }
 
+template <class Feat>
+__global__ void __launch_bounds__(kZWarps * 32) k_edt_z(Feat feat, int nrows, int nz, int cap,
+                                                        uint16_t *__restrict__ d1)
+{
+    edt_z_block(feat, blockIdx.x, nrows, nz, cap, d1);
+}
+
 size_t edt_z_smem(int nz) { return (size_t)kZWarps * ((nz + 511) >> 9) * 32 * 6; }
 
 // Sentinel of the partial sums: larger than any squared distance of an image
@@ -232,30 +242,42 @@ __device__ __forceinline__ int line_min_smem(const int32_t *col, int i, int n, i
 // pass y: strip = (x, all y, 32 z).  blockIdx.x = z strip, blockIdx.y = x.
 // Output: partial sums < cap2, kNone elsewhere.  The staged column holds
 // the squared pass-z distances.
+// the staged body of pass y for z strip `strip` of plane x
+__device__ __forceinline__ void edt_y_block_smem(const uint16_t *__restrict__ d1, int ny, int nz, int cap2,
+                                                 int32_t *__restrict__ g2, int strip, int x)
+{
+    extern __shared__ int32_t s_col[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int z = strip * kStripW + lane;
+    const bool ok = z < nz;
+    const int64_t b = (int64_t)x * ny * nz + z;
+    const int lim = min(cap2, kNone);
+#pragma unroll 8
+    for (int y = w; y < ny; y += kStripWarps) {
+        const int v = ok ? __ldg(d1 + b + (int64_t)y * nz) : 0xffff;
+        s_col[y * kStripW + lane] = v == 0xffff ? kNone : v * v;
+    }
+    __syncthreads();
+    if (!ok) return;
+    for (int y = w; y < ny; y += kStripWarps) {
+        const int v = line_min_smem(s_col + lane, y, ny, lim);
+        g2[b + (int64_t)y * nz] = v >= lim ? kNone : v;
+    }
+}
+
 template <bool SMEM>
 __global__ void __launch_bounds__(kStripWarps * 32) k_edt_y(const uint16_t *__restrict__ d1, int ny,
                                                             int nz, int cap2, int32_t *__restrict__ g2)
 {
-    extern __shared__ int32_t s_col[];
+    if (SMEM) {
+        edt_y_block_smem(d1, ny, nz, cap2, g2, blockIdx.x, blockIdx.y);
+        return;
+    }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int x = blockIdx.y, z = blockIdx.x * kStripW + lane;
     const bool ok = z < nz;
     const int64_t b = (int64_t)x * ny * nz + z;
     const int lim = min(cap2, kNone);
-    if (SMEM) {
-#pragma unroll 8
-        for (int y = w; y < ny; y += kStripWarps) {
-            const int v = ok ? __ldg(d1 + b + (int64_t)y * nz) : 0xffff;
-            s_col[y * kStripW + lane] = v == 0xffff ? kNone : v * v;
-        }
-        __syncthreads();
-        if (!ok) return;
-        for (int y = w; y < ny; y += kStripWarps) {
-            const int v = line_min_smem(s_col + lane, y, ny, lim);
-            g2[b + (int64_t)y * nz] = v >= lim ? kNone : v;
-        }
-        return;
-    }
     if (!ok) return;
     auto g = [&](int j) -> int {
         const int v = __ldg(d1 + b + (int64_t)j * nz);
@@ -283,28 +305,42 @@ struct EpiLevel {
 
 // pass x: strip = (y, all x, 32 z).  blockIdx.x = z strip, blockIdx.y = y.
 // Final values >= cap2 (or no feature at all) are reported as IBIP_INF32.
+// the staged body of pass x for z strip `strip` of row y
+template <class Epi>
+__device__ __forceinline__ void edt_x_block_smem(const int32_t *__restrict__ g2, int nx, int ny, int nz, int cap2,
+                                                 const Epi &epi, int strip, int y)
+{
+    extern __shared__ int32_t s_colx[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int z = strip * kStripW + lane;
+    const bool ok = z < nz;
+    const int64_t st = (int64_t)ny * nz;
+    const int64_t b = (int64_t)y * nz + z;
+    const int lim = min(cap2, kNone);
+#pragma unroll 8
+    for (int x = w; x < nx; x += kStripWarps) s_colx[x * kStripW + lane] = ok ? __ldg(g2 + b + x * st) : kNone;
+    __syncthreads();
+    if (!ok) return;
+    for (int x = w; x < nx; x += kStripWarps) {
+        const int v = line_min_smem(s_colx + lane, x, nx, lim);
+        epi(b + x * st, v >= lim ? IBIP_INF32 : v);
+    }
+}
+
 template <bool SMEM, class Epi>
 __global__ void __launch_bounds__(kStripWarps * 32) k_edt_x(const int32_t *__restrict__ g2, int nx,
                                                             int ny, int nz, int cap2, Epi epi)
 {
-    extern __shared__ int32_t s_colx[];
+    if (SMEM) {
+        edt_x_block_smem(g2, nx, ny, nz, cap2, epi, blockIdx.x, blockIdx.y);
+        return;
+    }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int y = blockIdx.y, z = blockIdx.x * kStripW + lane;
     const bool ok = z < nz;
     const int64_t st = (int64_t)ny * nz;
     const int64_t b = (int64_t)y * nz + z;
     const int lim = min(cap2, kNone);
-    if (SMEM) {
-#pragma unroll 8
-        for (int x = w; x < nx; x += kStripWarps) s_colx[x * kStripW + lane] = ok ? __ldg(g2 + b + x * st) : kNone;
-        __syncthreads();
-        if (!ok) return;
-        for (int x = w; x < nx; x += kStripWarps) {
-            const int v = line_min_smem(s_colx + lane, x, nx, lim);
-            epi(b + x * st, v >= lim ? IBIP_INF32 : v);
-        }
-        return;
-    }
     if (!ok) return;
     auto g = [&](int j) -> int { return __ldg(g2 + b + j * st); };
     for (int x = w; x < nx; x += kStripWarps) {
@@ -347,6 +383,48 @@ int edt_passes(ibip_ctx *ctx, Feat feat, ibip_dims d, int cap, int cap2, Epi epi
     IBIP_LAUNCH(ctx);
     ibip_prof_end(ctx, cls);
     return ibip_cuda_status(cudaGetLastError());
+}
+
+// ---- the three passes for many images, one launch per pass: each block
+// finds its image by binary search over the images' first blocks
+struct EdtJob {
+    const uint8_t *img;
+    int32_t *dt2;
+    uint16_t *d1;
+    int32_t *g2;
+    int nx, ny, nz;
+    int blk_z, blk_y, blk_x;
+};
+
+__device__ __forceinline__ int find_ejob(const EdtJob *jobs, int n, int blk, int pass)
+{
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        const int f = pass == 0 ? jobs[mid].blk_z : pass == 1 ? jobs[mid].blk_y : jobs[mid].blk_x;
+        if (f <= blk) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kZWarps * 32) k_edt_z_b(const EdtJob *__restrict__ jobs, int n)
+{
+    const EdtJob &J = jobs[find_ejob(jobs, n, blockIdx.x, 0)];
+    edt_z_block(FeatSolid{J.img}, blockIdx.x - J.blk_z, J.nx * J.ny, J.nz, 0xfffe, J.d1);
+}
+
+__global__ void __launch_bounds__(kStripWarps * 32) k_edt_y_b(const EdtJob *__restrict__ jobs, int n)
+{
+    const EdtJob &J = jobs[find_ejob(jobs, n, blockIdx.x, 1)];
+    const int lb = blockIdx.x - J.blk_y, ns = (J.nz + kStripW - 1) / kStripW;
+    edt_y_block_smem(J.d1, J.ny, J.nz, IBIP_INF32, J.g2, lb % ns, lb / ns);
+}
+
+__global__ void __launch_bounds__(kStripWarps * 32) k_edt_x_b(const EdtJob *__restrict__ jobs, int n)
+{
+    const EdtJob &J = jobs[find_ejob(jobs, n, blockIdx.x, 2)];
+    const int lb = blockIdx.x - J.blk_x, ns = (J.nz + kStripW - 1) / kStripW;
+    edt_x_block_smem(J.g2, J.nx, J.ny, J.nz, IBIP_INF32, EpiStore{J.dt2}, lb % ns, lb / ns);
 }
 
 }  // namespace
@@ -450,5 +528,61 @@ extern "C" int ibip_edt_noalloc(const uint8_t *image, ibip_dims d, int32_t *dt2,
     } else {
         k_edt_x<false, EpiStore><<<gx, kStripWarps * 32, 0, s>>>(g2, d.nx, d.ny, d.nz, IBIP_INF32, EpiStore{dt2});
     }
+    return ibip_cuda_status(cudaGetLastError());
+}
+
+int ibip_edt_batch_launch(ibip_ctx *ctx, int n, const uint8_t *const *images, const ibip_dims *dims,
+                          int32_t *const *dt2)
+{
+    cudaStream_t s = ctx->stream;
+    if (n <= 0) return IBIP_OK;
+    std::vector<EdtJob> jobs(n);
+    int64_t vox = 0;
+    size_t smz = 0, smy = 0, smx = 0;
+    int bz = 0, by = 0, bx = 0;
+    for (int j = 0; j < n; j++) {
+        const ibip_dims d = dims[j];
+        EdtJob &J = jobs[j];
+        J.img = images[j]; J.dt2 = dt2[j];
+        J.nx = d.nx; J.ny = d.ny; J.nz = d.nz;
+        const int ns = (d.nz + kStripW - 1) / kStripW;
+        J.blk_z = bz; bz += (d.nx * d.ny + kZWarps - 1) / kZWarps;
+        J.blk_y = by; by += ns * d.nx;
+        J.blk_x = bx; bx += ns * d.ny;
+        smz = std::max(smz, edt_z_smem(d.nz));
+        smy = std::max(smy, (size_t)d.ny * kStripW * sizeof(int32_t));
+        smx = std::max(smx, (size_t)d.nx * kStripW * sizeof(int32_t));
+        vox += (nvox(d) + 63) & ~(int64_t)63;
+    }
+    if (smy > kSmemBudget || smx > kSmemBudget) {
+        // a column too long to stage: one image at a time
+        for (int j = 0; j < n; j++) {
+            const int st = ibip_edt_launch(ctx, images[j], dims[j], dt2[j]);
+            if (st) return st;
+        }
+        return IBIP_OK;
+    }
+    uint16_t *d1 = (uint16_t *)ibip_scratch(ctx, SC_D1, (size_t)vox * sizeof(uint16_t));
+    int32_t *g2 = (int32_t *)ibip_scratch(ctx, SC_G2, (size_t)vox * sizeof(int32_t));
+    const size_t tab = (size_t)n * sizeof(EdtJob);
+    EdtJob *dj = (EdtJob *)ibip_scratch(ctx, SC_BJOBS, tab);
+    if (!d1 || !g2 || !dj) return IBIP_ERR_OOM;
+    int64_t off = 0;
+    for (int j = 0; j < n; j++) {
+        jobs[j].d1 = d1 + off;
+        jobs[j].g2 = g2 + off;
+        off += (nvox(dims[j]) + 63) & ~(int64_t)63;
+    }
+    ibip_prof_begin(ctx, IBIP_K_EDT);
+    cudaMemcpyAsync(dj, jobs.data(), tab, cudaMemcpyHostToDevice, s);
+    cudaFuncSetAttribute(k_edt_y_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget);
+    cudaFuncSetAttribute(k_edt_x_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget);
+    k_edt_z_b<<<bz, kZWarps * 32, smz, s>>>(dj, n);
+    IBIP_LAUNCH(ctx);
+    k_edt_y_b<<<by, kStripWarps * 32, smy, s>>>(dj, n);
+    IBIP_LAUNCH(ctx);
+    k_edt_x_b<<<bx, kStripWarps * 32, smx, s>>>(dj, n);
+    IBIP_LAUNCH(ctx);
+    ibip_prof_end(ctx, IBIP_K_EDT);
     return ibip_cuda_status(cudaGetLastError());
 }

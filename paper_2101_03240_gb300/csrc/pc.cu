@@ -2,6 +2,8 @@
 // 2.2.2; Washburn relation as written in Section 2.4.1), plus the helpers
 // trapping and opening need: thresholding against seq, re-ranking and
 // level counts.
+#include <vector>
+
 #include "common.cuh"
 
 namespace {
@@ -168,6 +170,85 @@ __global__ void k_size_image(const int32_t *__restrict__ seq, int64_t N, const i
     }
 }
 
+// ---- the same for every image of a batch: one launch per stage, each
+// block finding its image by binary search over the images' first blocks
+struct CurveJob {
+    const int32_t *seq;     // invasion sequence
+    const int32_t *M;       // widest-path field from the outlet, or null: no trapping
+    uint8_t *trapped;
+    int32_t *seq_out;       // or null
+    const int32_t *cseq;    // the sequence the curve counts (seq_out after trapping, else seq)
+    const int32_t *r2;
+    float *S, *Pc;          // null: no curve
+    int64_t N, K, cnt_off;  // voxels, steps, first entry of the pooled per-step counts [K + 2]
+    double voxel, num;      // voxel size and -2 sigma cos(theta)
+    int blk_vox, blk_k;     // first block in the voxel and step launches
+};
+
+constexpr int kCvBlock = 256, kCvPer = 8;
+
+__device__ __forceinline__ int find_cjob(const CurveJob *jobs, int n, int blk, bool steps)
+{
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if ((steps ? jobs[mid].blk_k : jobs[mid].blk_vox) <= blk) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_trap_cmp_b(const CurveJob *__restrict__ jobs, int n)
+{
+    const CurveJob &J = jobs[find_cjob(jobs, n, blockIdx.x, false)];
+    if (!J.M) return;
+    const int64_t v0 = (int64_t)(blockIdx.x - J.blk_vox) * kCvBlock * kCvPer;
+    for (int q = 0; q < kCvPer; q++) {
+        const int64_t v = v0 + q * kCvBlock + threadIdx.x;
+        if (v >= J.N) break;
+        const int sq = J.seq[v];
+        const bool t = sq >= 1 && J.M[v] < sq;
+        J.trapped[v] = t;
+        if (J.seq_out) J.seq_out[v] = t ? -1 : sq;
+    }
+}
+
+// per-step counts (warp-aggregated; a block holds one image) and pore counts
+__global__ void k_hist_seq_b(const CurveJob *__restrict__ jobs, int n, int32_t *cnt, int *npore)
+{
+    const int j = find_cjob(jobs, n, blockIdx.x, false);
+    const CurveJob &J = jobs[j];
+    if (!J.S) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t v0 = (int64_t)(blockIdx.x - J.blk_vox) * kCvBlock * kCvPer;
+    int np = 0;
+    for (int q = 0; q < kCvPer; q++) {
+        const int64_t v = v0 + q * kCvBlock + threadIdx.x;
+        const int sq = v < J.N ? J.cseq[v] : 0;
+        np += sq != 0;
+        const int key = (sq >= 1 && sq <= J.K) ? sq : 0;
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        if (key && lane == __ffs(peers) - 1) atomicAdd(cnt + J.cnt_off + key, __popc(peers));
+    }
+    for (int o = 16; o; o >>= 1) np += __shfl_xor_sync(0xffffffffu, np, o);
+    if (lane == 0 && np) atomicAdd(npore + j, np);
+}
+
+// after the flat inclusive scan of the counts: S and Pc of every step (the
+// formulas of k_pc; an image's counts are relative to its segment's start)
+__global__ void k_pc_b(const CurveJob *__restrict__ jobs, int n, const int32_t *__restrict__ cum,
+                       const int *__restrict__ npore)
+{
+    const int j = find_cjob(jobs, n, blockIdx.x, true);
+    const CurveJob &J = jobs[j];
+    if (!J.S) return;
+    const int64_t k = (int64_t)(blockIdx.x - J.blk_k) * blockDim.x + threadIdx.x;
+    if (k >= J.K) return;
+    const double np = (double)npore[j];
+    const int32_t base = cum[J.cnt_off];   // the segment's count of step 0 is zero
+    J.S[k] = (float)((double)(cum[J.cnt_off + k + 1] - base) / np);
+    J.Pc[k] = (float)(J.num / (sqrt((double)J.r2[k]) * J.voxel));
+}
+
 }  // namespace
 
 int ibip_pc_launch(ibip_ctx *ctx, const int32_t *seq, ibip_dims d, const int32_t *r2, int64_t K, double voxel,
@@ -332,4 +413,66 @@ int ibip_eqsat_launch(ibip_ctx *ctx, const int32_t *seq, const int32_t *level, i
         h_diff[i] = run;
     }
     return IBIP_OK;
+}
+
+int ibip_curve_batch_launch(ibip_ctx *ctx, int n, const IbipCurveItem *items)
+{
+    cudaStream_t s = ctx->stream;
+    if (n <= 0) return IBIP_OK;
+    std::vector<CurveJob> jobs;
+    std::vector<int> which;
+    int64_t cnt_total = 0;
+    int blk_vox = 0, blk_k = 0;
+    bool any_trap = false, any_curve = false;
+    for (int i = 0; i < n; i++) {
+        const IbipCurveItem &it = items[i];
+        if (!it.M && !it.S) continue;
+        CurveJob J = {};
+        J.seq = it.seq; J.M = it.M; J.trapped = it.trapped; J.seq_out = it.seq_out;
+        J.cseq = (it.M && it.seq_out) ? it.seq_out : it.seq;
+        J.r2 = it.r2; J.S = it.S; J.Pc = it.Pc;
+        J.N = nvox(it.d); J.K = it.S ? it.K : 0;
+        J.cnt_off = cnt_total;
+        if (it.S) cnt_total += J.K + 2;
+        J.voxel = it.voxel; J.num = -2.0 * it.sigma * it.cos_theta;
+        J.blk_vox = blk_vox;
+        blk_vox += (int)((J.N + kCvBlock * kCvPer - 1) / (kCvBlock * kCvPer));
+        J.blk_k = blk_k;
+        blk_k += (int)((J.K + 255) / 256);
+        any_trap |= it.M != nullptr;
+        any_curve |= it.S != nullptr;
+        jobs.push_back(J);
+        which.push_back(i);
+    }
+    const int m = (int)jobs.size();
+    if (m == 0) return IBIP_OK;
+    if (cnt_total >= (1ll << 31)) return IBIP_ERR_ARG;
+    const size_t tab = ((size_t)m * sizeof(CurveJob) + 255) / 256 * 256;
+    const size_t npb = ((size_t)m * sizeof(int) + 255) / 256 * 256;
+    char *w = (char *)ibip_scratch(ctx, SC_HIST, tab + npb + (size_t)(cnt_total + 1) * sizeof(int32_t));
+    if (!w) return IBIP_ERR_OOM;
+    CurveJob *dj = (CurveJob *)w;
+    int *np = (int *)(w + tab);
+    int32_t *cnt = (int32_t *)(w + tab + npb);
+    cudaMemcpyAsync(dj, jobs.data(), (size_t)m * sizeof(CurveJob), cudaMemcpyHostToDevice, s);
+    if (any_trap) {
+        ibip_prof_begin(ctx, IBIP_K_TRAP);
+        k_trap_cmp_b<<<blk_vox, kCvBlock, 0, s>>>(dj, m);
+        IBIP_LAUNCH(ctx);
+        ibip_prof_end(ctx, IBIP_K_TRAP);
+    }
+    if (any_curve) {
+        ibip_prof_begin(ctx, IBIP_K_PC);
+        cudaMemsetAsync(w + tab, 0, npb + (size_t)(cnt_total + 1) * sizeof(int32_t), s);
+        k_hist_seq_b<<<blk_vox, kCvBlock, 0, s>>>(dj, m, cnt, np);
+        IBIP_LAUNCH(ctx);
+        int st = ibip_scan_incl_i32(ctx, cnt, cnt, cnt_total);
+        if (st) return st;
+        if (blk_k > 0) {
+            k_pc_b<<<blk_k, 256, 0, s>>>(dj, m, cnt, np);
+            IBIP_LAUNCH(ctx);
+        }
+        ibip_prof_end(ctx, IBIP_K_PC);
+    }
+    return ibip_cuda_status(cudaGetLastError());
 }
