@@ -379,18 +379,56 @@ class Context:
         n = len(images)
         inl = inlets if isinstance(inlets, (list, tuple)) else [inlets] * n
         outl = outlets if isinstance(outlets, (list, tuple)) else [outlets] * n
+        for im in images:
+            _need(im, torch.uint8, "image")
+        dev = images[0].device
+        sizes = [im.numel() for im in images]
+        offs, tot = [], 0
+        for N in sizes:
+            offs.append(tot)
+            tot += max(N, 1)
+        # one buffer per output kind, every image a slice of it
+        pool = {"seq": torch.empty(tot, dtype=torch.int32, device=dev),
+                "step_r2": torch.empty(tot, dtype=torch.int32, device=dev),
+                "step_centre": torch.empty(tot, dtype=torch.int32, device=dev)}
+        if trapping:
+            pool["trapped"] = torch.empty(tot, dtype=torch.uint8, device=dev)
+            pool["seq_out"] = torch.empty(tot, dtype=torch.int32, device=dev)
+        if curve:
+            pool["S"] = torch.empty(tot, dtype=torch.float32, device=dev)
+            pool["Pc"] = torch.empty(tot, dtype=torch.float32, device=dev)
+        base = {k: (v.data_ptr(), v.element_size()) for k, v in pool.items()}
         arr = (Job * n)()
-        res = []
+        vm, sg, th = float(voxel_m), float(sigma), float(theta_deg)
         for j, im in enumerate(images):
-            res.append(_fill_job(arr[j], im, int(inl[j]), int(outl[j]), trapping, curve, voxel_m, sigma, theta_deg))
+            J, o = arr[j], offs[j]
+            J.image = im.data_ptr()
+            J.dims = _dims(im.shape)
+            J.inlet, J.outlet = int(inl[j]), int(outl[j]) if trapping else -1
+            J.dt2 = None
+            J.seq = base["seq"][0] + 4 * o
+            J.step_r2 = base["step_r2"][0] + 4 * o
+            J.step_centre = base["step_centre"][0] + 4 * o
+            J.capacity_steps = sizes[j]
+            J.trapped = base["trapped"][0] + o if trapping else None
+            J.seq_out = base["seq_out"][0] + 4 * o if trapping else None
+            J.sat_per_step = base["S"][0] + 4 * o if curve else None
+            J.pc_per_step = base["Pc"][0] + 4 * o if curve else None
+            J.voxel_m, J.sigma, J.theta_deg = vm, sg, th
         self._stream()
         st = _lib().ibip_invade_batched(self._h, n, arr)
         if check and st != OK:
             raise IbipError("ibip_invade_batched", st)
-        for j, r in enumerate(res):
-            K = int(arr[j].n_steps)
-            r["K"], r["status"] = K, int(arr[j].status)
-            _trim(r, K)
+        res = []
+        for j, im in enumerate(images):
+            o, N, K = offs[j], sizes[j], int(arr[j].n_steps)
+            r = {"K": K, "status": int(arr[j].status)}
+            for key, v in pool.items():
+                if key in ("seq", "trapped", "seq_out"):
+                    r[key] = v[o:o + N].view(im.shape)
+                else:
+                    r[key] = v[o:o + min(K, N)]
+            res.append(r)
         return res
 
     def equal_saturation(self, seq, level, n_steps, n_levels):
