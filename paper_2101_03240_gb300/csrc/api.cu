@@ -171,6 +171,70 @@ int ibip_run_job(ibip_ctx *ctx, ibip_job &J)
     return ibip_cuda_status(cudaStreamSynchronize(ctx->stream));
 }
 
+// Post-processing of a batched call (trapping, curves) for a group of its
+// images, after their invasions are done.
+struct BatchPost {
+    ibip_ctx *ctx;
+    ibip_job *jobs;
+    IbipBatchItem *it;
+    int32_t *M;
+    std::vector<int64_t> M_off;
+    std::vector<char> early;
+    int early_err = IBIP_OK;
+};
+
+int batch_post_group(BatchPost &P, const std::vector<int> &group, bool shared_device)
+{
+    ibip_ctx *ctx = P.ctx;
+    std::vector<IbipMaximinJob> mj;
+    std::vector<int> mj_of;
+    for (int j : group) {
+        ibip_job &J = P.jobs[j];
+        J.n_steps = P.it[j].n_steps;
+        J.status = P.it[j].status;
+        if (J.status == IBIP_OK && J.n_steps > J.capacity_steps) J.status = IBIP_ERR_ARG;
+        if (J.status != IBIP_OK || !J.trapped) continue;
+        mj.push_back(IbipMaximinJob{J.seq, J.dims, J.outlet, P.M + P.M_off[j]});
+        mj_of.push_back(j);
+    }
+    const int keep_nc = ctx->no_coop;
+    ctx->no_coop = shared_device ? 1 : keep_nc;   // beside a running kernel: no cooperative grid
+    int st = mj.empty() ? IBIP_OK : ibip_maximin_multi(ctx, (int)mj.size(), mj.data(), kMaxRounds);
+    ctx->no_coop = keep_nc;
+    if (st) {
+        if (st != IBIP_ERR_NOT_CONVERGED) return st;
+        for (int j : mj_of) P.jobs[j].status = st;
+    }
+    std::vector<IbipCurveItem> ci;
+    const double pi = 3.14159265358979323846;
+    std::vector<const int32_t *> Mof(P.M_off.size(), nullptr);
+    for (size_t q = 0; q < mj.size(); q++) Mof[mj_of[q]] = mj[q].M;
+    for (int j : group) {
+        ibip_job &J = P.jobs[j];
+        if (J.status != IBIP_OK) continue;
+        const int32_t *M = J.trapped ? Mof[j] : nullptr;
+        if (!M && !J.sat_per_step) continue;
+        ci.push_back(IbipCurveItem{J.seq, M, J.trapped, J.seq_out, J.step_r2, J.sat_per_step, J.pc_per_step, J.dims,
+                                   J.n_steps, J.voxel_m, J.sigma, cos(J.theta_deg * pi / 180.0)});
+    }
+    return ibip_curve_batch_launch(ctx, (int)ci.size(), ci.data());
+}
+
+// the images done while the largest invasions still run: on the second stream
+int batch_early(void *user, int n_done, const int *done)
+{
+    BatchPost &P = *(BatchPost *)user;
+    ibip_ctx *ctx = P.ctx;
+    std::vector<int> group(done, done + n_done);
+    for (int j : group) P.early[j] = 1;
+    cudaStream_t keep = ctx->stream;
+    ctx->stream = ctx->stream2;
+    const int st = batch_post_group(P, group, true);
+    ctx->stream = keep;
+    P.early_err = st;
+    return st;
+}
+
 extern "C" {
 
 int ibip_create(ibip_ctx **out, int device, void *cuda_stream)
@@ -194,6 +258,14 @@ int ibip_create(ibip_ctx **out, int device, void *cuda_stream)
         delete c;
         return IBIP_ERR_CUDA;
     }
+    if (cudaHostAlloc(&c->h_done, (size_t)kMaxBatch * sizeof(IbipBatchDone), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer(&c->d_done, c->h_done, 0) != cudaSuccess) {
+        cudaGetLastError();
+        if (c->h_done) cudaFreeHost(c->h_done);
+        cudaFreeHost(c->h_pinned);
+        delete c;
+        return IBIP_ERR_CUDA;
+    }
     *out = c;
     return IBIP_OK;
 }
@@ -206,6 +278,11 @@ int ibip_destroy(ibip_ctx *ctx)
     delete (ProfLog *)ctx->prof;
     for (int i = 0; i < SC_NSLOTS; i++)
         if (ctx->slot[i] && !ctx->arena) cudaFree(ctx->slot[i]);
+    if (ctx->stream2) {
+        cudaStreamSynchronize(ctx->stream2);
+        cudaStreamDestroy(ctx->stream2);
+    }
+    if (ctx->h_done) cudaFreeHost(ctx->h_done);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
     delete ctx;
     return IBIP_OK;
@@ -471,56 +548,52 @@ int ibip_invade_batched(ibip_ctx *ctx, int32_t n, ibip_job *jobs)
     }
     int st = ibip_edt_batch_launch(ctx, n, ims.data(), dms.data(), dts.data());
     if (st) return st;
-    st = ibip_invade_batch_run(ctx, n, it.data());
-    if (st) return st;
-    int first_bad = IBIP_OK;
-    // trapping: one widest-path propagation over every image that asks for it
-    std::vector<IbipMaximinJob> mj;
-    std::vector<int> mj_of;
-    int64_t mm_total = 0;
+    // Trapping and curves run in two groups: the images whose invasion is
+    // done while the last few still run (on a second stream, overlapping
+    // them), then the rest.  All scratch they use is sized first, so nothing
+    // is reallocated while kernels run.
+    if (!ctx->stream2 && cudaStreamCreateWithFlags(&ctx->stream2, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->stream2 = nullptr;
+        return IBIP_ERR_CUDA;
+    }
+    BatchPost P;
+    P.ctx = ctx;
+    P.jobs = jobs;
+    P.it = it.data();
+    P.M_off.assign(n, -1);
+    P.early.assign(n, 0);
+    int64_t mm_total = 0, nt_total = 0, cnt_total = 0;
     for (int j = 0; j < n; j++) {
-        ibip_job &J = jobs[j];
-        J.n_steps = it[j].n_steps;
-        J.status = it[j].status;
-        if (J.status == IBIP_OK && J.n_steps > J.capacity_steps) J.status = IBIP_ERR_ARG;
-        if (J.status != IBIP_OK) { if (first_bad == IBIP_OK) first_bad = J.status; continue; }
+        const ibip_job &J = jobs[j];
         if (J.trapped) {
-            mj.push_back(IbipMaximinJob{J.seq, J.dims, J.outlet, nullptr});
-            mj_of.push_back(j);
+            P.M_off[j] = mm_total;
             mm_total += (nvox(J.dims) + 63) & ~(int64_t)63;
+            nt_total += (int64_t)((J.dims.nx + 3) / 4) * ((J.dims.ny + 7) / 8) * ((J.dims.nz + 31) / 32);
         }
+        if (J.sat_per_step) cnt_total += nvox(J.dims) + 2;
     }
-    if (!mj.empty()) {
-        int32_t *M = (int32_t *)ibip_scratch(ctx, SC_MM, (size_t)mm_total * sizeof(int32_t));
-        if (!M) return IBIP_ERR_OOM;
-        int64_t o = 0;
-        for (auto &m : mj) { m.M = M + o; o += (nvox(m.d) + 63) & ~(int64_t)63; }
-        st = ibip_maximin_multi(ctx, (int)mj.size(), mj.data(), kMaxRounds);
-        if (st) {
-            for (size_t q = 0; q < mj.size(); q++) {
-                jobs[mj_of[q]].status = st;
-                if (first_bad == IBIP_OK) first_bad = st;
-            }
-        }
-    }
-    // trapped masks and curves of every image: one launch per stage
-    std::vector<IbipCurveItem> ci;
-    std::vector<const int32_t *> Mof(n, nullptr);
-    for (size_t q = 0; q < mj.size(); q++) Mof[mj_of[q]] = mj[q].M;
-    const double pi = 3.14159265358979323846;
-    for (int j = 0; j < n; j++) {
-        ibip_job &J = jobs[j];
-        if (J.status != IBIP_OK) continue;
-        const int32_t *M = J.trapped ? Mof[j] : nullptr;
-        if (!M && !J.sat_per_step) continue;
-        ci.push_back(IbipCurveItem{J.seq, M, J.trapped, J.seq_out, J.step_r2, J.sat_per_step, J.pc_per_step, J.dims,
-                                   J.n_steps, J.voxel_m, J.sigma, cos(J.theta_deg * pi / 180.0)});
-    }
-    st = ibip_curve_batch_launch(ctx, (int)ci.size(), ci.data());
+    P.M = mm_total ? (int32_t *)ibip_scratch(ctx, SC_MM, (size_t)mm_total * sizeof(int32_t)) : nullptr;
+    const size_t tile_bytes = ((size_t)n * 64 + 255) / 256 * 256 + ((size_t)3 * nt_total + 2 * ((1 << 16) + 2) + 4) * 4;
+    if ((mm_total && !P.M) || (nt_total && !ibip_scratch(ctx, SC_TILE, tile_bytes)) ||
+        !ibip_scratch(ctx, SC_HIST, ibip_curve_batch_bytes(n, cnt_total)) ||
+        !ibip_scratch(ctx, SC_SCAN, ibip_scan_scratch_bytes(cnt_total + 1)) || !ibip_scratch(ctx, SC_SMALL, kSmallBytes))
+        return IBIP_ERR_OOM;
+    st = ibip_invade_batch_run(ctx, n, it.data(), batch_early, &P);
+    cudaError_t e2 = cudaStreamSynchronize(ctx->stream2);
+    if (st && st != P.early_err) return st;
+    if (e2 != cudaSuccess) return ibip_cuda_status(e2);
+    std::vector<int> rest;
+    for (int j = 0; j < n; j++)
+        if (!P.early[j]) rest.push_back(j);
+    st = batch_post_group(P, rest, false);
     if (st) return st;
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return ibip_cuda_status(e);
-    return first_bad;
+    if (P.early_err) return P.early_err;
+    for (int j = 0; j < n; j++)
+        if (jobs[j].status != IBIP_OK) return jobs[j].status;
+    return IBIP_OK;
 }
 
 int ibip_equal_saturation(ibip_ctx *ctx, const int32_t *seq, const int32_t *level, ibip_dims dims,

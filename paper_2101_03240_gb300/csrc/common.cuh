@@ -52,7 +52,22 @@ struct ibip_ctx {
     size_t arena_size, arena_used;
     // Kernels share the device with other streams: no cooperative launches.
     int no_coop;
+    // Batched invasion: a second stream for post-processing images whose
+    // invasion is done while others still run, and host-mapped completion
+    // records written by the invasion CTAs.
+    cudaStream_t stream2;
+    void *h_done, *d_done;
 };
+
+// Completion record of one image of a batched invasion (host-mapped).
+struct IbipBatchDone {
+    int64_t steps;
+    int32_t status;
+    int32_t done;
+};
+// Called once, on the host, when all but a few images of a batched invasion
+// are done (their n_steps and status are filled in); the others still run.
+typedef int (*IbipBatchEarly)(void *user, int n_done, const int *done_items);
 
 // Profiling: CUDA-event pairs around each kernel class, on the context's
 // stream, only while ibip_profile_enable(ctx, 1) is in effect.
@@ -80,7 +95,10 @@ struct IbipBatchItem {
     int status;        // out
 };
 constexpr int kMaxBatch = 4096;   // two int64 per image fit the pinned readback buffer
-int ibip_invade_batch_run(ibip_ctx *ctx, int n, IbipBatchItem *items);
+int ibip_invade_batch_run(ibip_ctx *ctx, int n, IbipBatchItem *items, IbipBatchEarly early = nullptr,
+                          void *user = nullptr);
+// Scratch bytes the scans take for n entries.
+size_t ibip_scan_scratch_bytes(int64_t n);
 
 // Argument checks of one ibip_job, and the whole one-image path for it
 // (EDT, invasion, trapping and curve as requested), synchronous on the
@@ -143,6 +161,8 @@ struct IbipCurveItem {
     double voxel, sigma, cos_theta;
 };
 int ibip_curve_batch_launch(ibip_ctx *ctx, int n, const IbipCurveItem *items);
+// Scratch bytes of that launch for n items with cnt_total pooled counts (sum of K + 2).
+size_t ibip_curve_batch_bytes(int n, int64_t cnt_total);
 // Scans.
 int ibip_scan_excl_i32(ibip_ctx *ctx, const int32_t *in, int32_t *out, int64_t n);
 int ibip_scan_incl_i32(ibip_ctx *ctx, const int32_t *in, int32_t *out, int64_t n);

@@ -28,6 +28,8 @@
 //    committed ball covering it), covered candidates leave the bitmap, and
 //    new candidates (outside every committed ball) enter it.
 #include <algorithm>
+#include <atomic>
+#include <thread>
 #include <vector>
 #include <climits>
 
@@ -1296,6 +1298,7 @@ struct InvJob {
     FastDiv fd_nyz, fd_nz;
     int *gC, *gD;
     int blk_plane;   // first block of this image in the batched plane set-up
+    int flag;        // this image's completion record
 };
 
 // bit-planes and first candidates of every image: one thread per word
@@ -1311,10 +1314,22 @@ __global__ void k_plane_init_b(const InvJob *__restrict__ jobs, int n)
     if (w < (int64_t)a.nx * a.ny * a.NW) plane_word(a, w);
 }
 
-__global__ void __launch_bounds__(kNT, 1) k_invade_batch(const InvJob *__restrict__ jobs)
+// rec (host-mapped, when given): image i's steps and status, then its done
+// flag, once its results are visible to later kernels on the device.
+__global__ void __launch_bounds__(kNT, 1) k_invade_batch(const InvJob *__restrict__ jobs, IbipBatchDone *rec)
 {
     const InvJob j = jobs[blockIdx.x];
     invade_body<true>(j.a, j.fd_nyz, j.fd_nz, j.gC, j.gD);
+    if (!rec) return;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile IbipBatchDone *r = rec + j.flag;
+        r->steps = j.a.out[0];
+        r->status = (int32_t)j.a.out[1];
+        __threadfence_system();
+        r->done = 1;
+    }
 }
 
 }  // namespace
@@ -1556,7 +1571,7 @@ int ibip_stats_launch(ibip_ctx *ctx, const int32_t *dt2, int64_t N, int *stats)
 
 // ------------------------------------------------------------- batched --
 
-int ibip_invade_batch_run(ibip_ctx *ctx, int n, IbipBatchItem *it)
+int ibip_invade_batch_run(ibip_ctx *ctx, int n, IbipBatchItem *it, IbipBatchEarly early, void *user)
 {
     cudaStream_t s = ctx->stream;
     if (n <= 0) return IBIP_OK;
@@ -1693,6 +1708,7 @@ int ibip_invade_batch_run(ibip_ctx *ctx, int n, IbipBatchItem *it)
         int blk_plane = 0;
         for (int q = 0; q < m; q++) {
             sorted[q] = jobs[order[q]];
+            sorted[q].flag = order[q];
             sorted[q].blk_plane = blk_plane;
             const Inv &a = sorted[q].a;
             blk_plane += (int)(((int64_t)a.nx * a.ny * a.NW + 255) / 256);
@@ -1705,9 +1721,47 @@ int ibip_invade_batch_run(ibip_ctx *ctx, int n, IbipBatchItem *it)
         ibip_prof_end(ctx, IBIP_K_RANK);
         ibip_prof_begin(ctx, IBIP_K_INVADE);
         allow_max_dyn_smem((const void *)k_invade_batch);
-        k_invade_batch<<<m, kNT, dyn, s>>>(djobs);
+        volatile IbipBatchDone *hd = early ? (volatile IbipBatchDone *)ctx->h_done : nullptr;
+        if (hd)
+            for (int q = 0; q < m; q++) hd[q].done = 0;
+        k_invade_batch<<<m, kNT, dyn, s>>>(djobs, hd ? (IbipBatchDone *)ctx->d_done : nullptr);
         IBIP_LAUNCH(ctx);
         ibip_prof_end(ctx, IBIP_K_INVADE);
+        if (hd) {
+            // records arrive as CTAs finish; once all but kTail images are
+            // done, `early` post-processes those while the rest still run
+            constexpr int kTail = 8;
+            std::vector<char> seen(m, 0);
+            std::vector<int> done;
+            int nseen = 0, first_err = IBIP_OK;
+            bool fired = false;
+            for (;;) {
+                const bool ended = cudaStreamQuery(s) != cudaErrorNotReady;
+                for (int q = 0; q < m; q++) {
+                    if (seen[q] || !hd[q].done) continue;
+                    std::atomic_thread_fence(std::memory_order_acquire);   // the record, then its flag
+                    seen[q] = 1;
+                    nseen++;
+                    it[idx[q]].n_steps = hd[q].steps;
+                    it[idx[q]].status = hd[q].status;
+                    done.push_back(idx[q]);
+                }
+                if (!fired && nseen > 0 && m - nseen <= kTail && nseen < m) {
+                    fired = true;
+                    const int st = early(user, (int)done.size(), done.data());
+                    if (st) first_err = st;
+                }
+                if (nseen == m) break;
+                if (ended) {   // the kernel ended without every record: a device error
+                    cudaGetLastError();
+                    return IBIP_ERR_CUDA;
+                }
+                std::this_thread::yield();
+            }
+            cudaError_t e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) return ibip_cuda_status(e);
+            return first_err;
+        }
         // steps and status of every job
         int64_t *ho = (int64_t *)ctx->h_pinned;
         for (int q = 0; q < m; q++) cudaMemcpyAsync(ho + 2 * q, outs[idx[q]], 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s);

@@ -449,7 +449,7 @@ int ibip_curve_batch_launch(ibip_ctx *ctx, int n, const IbipCurveItem *items)
     if (cnt_total >= (1ll << 31)) return IBIP_ERR_ARG;
     const size_t tab = ((size_t)m * sizeof(CurveJob) + 255) / 256 * 256;
     const size_t npb = ((size_t)m * sizeof(int) + 255) / 256 * 256;
-    char *w = (char *)ibip_scratch(ctx, SC_HIST, tab + npb + (size_t)(cnt_total + 1) * sizeof(int32_t));
+    char *w = (char *)ibip_scratch(ctx, SC_HIST, ibip_curve_batch_bytes(m, cnt_total));
     if (!w) return IBIP_ERR_OOM;
     CurveJob *dj = (CurveJob *)w;
     int *np = (int *)(w + tab);
@@ -475,4 +475,10 @@ int ibip_curve_batch_launch(ibip_ctx *ctx, int n, const IbipCurveItem *items)
         ibip_prof_end(ctx, IBIP_K_PC);
     }
     return ibip_cuda_status(cudaGetLastError());
+}
+
+size_t ibip_curve_batch_bytes(int n, int64_t cnt_total)
+{
+    return ((size_t)n * sizeof(CurveJob) + 255) / 256 * 256 + ((size_t)n * sizeof(int) + 255) / 256 * 256 +
+           (size_t)(cnt_total + 1) * sizeof(int32_t);
 }

@@ -85,12 +85,18 @@ int scan_rec(ibip_ctx *ctx, const int32_t *in, int32_t *out, int64_t n, int incl
     return IBIP_OK;
 }
 
-int scan_impl(ibip_ctx *ctx, const int32_t *in, int32_t *out, int64_t n, int incl)
+size_t scan_words(int64_t n)
 {
-    if (n <= 0) return IBIP_OK;
     size_t need = 16;
     for (int64_t m = (n + kPerBlock - 1) / kPerBlock; m > 1; m = (m + kPerBlock - 1) / kPerBlock)
         need += (size_t)m * 2;
+    return need;
+}
+
+int scan_impl(ibip_ctx *ctx, const int32_t *in, int32_t *out, int64_t n, int incl)
+{
+    if (n <= 0) return IBIP_OK;
+    const size_t need = scan_words(n);
     int32_t *work = (int32_t *)ibip_scratch(ctx, SC_SCAN, need * sizeof(int32_t));
     if (!work) return IBIP_ERR_OOM;
     int st = scan_rec(ctx, in, out, n, incl, work);
@@ -98,6 +104,8 @@ int scan_impl(ibip_ctx *ctx, const int32_t *in, int32_t *out, int64_t n, int inc
 }
 
 }  // namespace
+
+size_t ibip_scan_scratch_bytes(int64_t n) { return scan_words(n) * sizeof(int32_t); }
 
 int ibip_scan_excl_i32(ibip_ctx *ctx, const int32_t *in, int32_t *out, int64_t n)
 {
