@@ -247,18 +247,28 @@ __device__ __forceinline__ void edt_y_block_smem(const uint16_t *__restrict__ d1
                                                  int32_t *__restrict__ g2, int strip, int x)
 {
     extern __shared__ int32_t s_col[];
+    __shared__ int s_any[kStripW];   // per z lane: the column holds a feature
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int z = strip * kStripW + lane;
     const bool ok = z < nz;
     const int64_t b = (int64_t)x * ny * nz + z;
     const int lim = min(cap2, kNone);
+    if (threadIdx.x < kStripW) s_any[threadIdx.x] = 0;
+    __syncthreads();
+    bool any = false;
 #pragma unroll 8
     for (int y = w; y < ny; y += kStripWarps) {
         const int v = ok ? __ldg(d1 + b + (int64_t)y * nz) : 0xffff;
+        any |= v != 0xffff;
         s_col[y * kStripW + lane] = v == 0xffff ? kNone : v * v;
     }
+    if (any) s_any[lane] = 1;
     __syncthreads();
     if (!ok) return;
+    if (!s_any[lane]) {   // no feature in the column: nothing within reach
+        for (int y = w; y < ny; y += kStripWarps) g2[b + (int64_t)y * nz] = kNone;
+        return;
+    }
     for (int y = w; y < ny; y += kStripWarps) {
         const int v = line_min_smem(s_col + lane, y, ny, lim);
         g2[b + (int64_t)y * nz] = v >= lim ? kNone : v;
@@ -289,17 +299,22 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_edt_y(const uint16_t *__re
     }
 }
 
+// Epilogues of pass x: need(v) says whether voxel v's value is wanted at all
+// (the search is skipped otherwise), operator() takes it.
 struct EpiStore {
     int32_t *out;
+    __device__ bool need(int64_t) const { return true; }
     __device__ void operator()(int64_t v, int val) const { out[v] = val; }
 };
-// MIO: voxels within the dilation that have no level yet get `lvl`.
+// MIO: voxels within the dilation that have no level yet get `lvl`; voxels
+// with a level (solid, or an earlier level) keep it and need no search.
 struct EpiLevel {
     int32_t *level;
     int32_t T, lvl;
+    __device__ bool need(int64_t v) const { return level[v] == -1; }
     __device__ void operator()(int64_t v, int val) const
     {
-        if (val < T && level[v] == -1) level[v] = lvl;
+        if (val < T) level[v] = lvl;
     }
 };
 
@@ -311,17 +326,32 @@ __device__ __forceinline__ void edt_x_block_smem(const int32_t *__restrict__ g2,
                                                  const Epi &epi, int strip, int y)
 {
     extern __shared__ int32_t s_colx[];
+    __shared__ int s_anyx[kStripW];   // per z lane: the column holds a finite partial sum
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int z = strip * kStripW + lane;
     const bool ok = z < nz;
     const int64_t st = (int64_t)ny * nz;
     const int64_t b = (int64_t)y * nz + z;
     const int lim = min(cap2, kNone);
+    if (threadIdx.x < kStripW) s_anyx[threadIdx.x] = 0;
+    __syncthreads();
+    bool any = false;
 #pragma unroll 8
-    for (int x = w; x < nx; x += kStripWarps) s_colx[x * kStripW + lane] = ok ? __ldg(g2 + b + x * st) : kNone;
+    for (int x = w; x < nx; x += kStripWarps) {
+        const int v = ok ? __ldg(g2 + b + x * st) : kNone;
+        any |= v != kNone;
+        s_colx[x * kStripW + lane] = v;
+    }
+    if (any) s_anyx[lane] = 1;
     __syncthreads();
     if (!ok) return;
+    const bool none = !s_anyx[lane];   // nothing within reach: every value is IBIP_INF32
     for (int x = w; x < nx; x += kStripWarps) {
+        if (none) {
+            if (epi.need(b + x * st)) epi(b + x * st, IBIP_INF32);
+            continue;
+        }
+        if (!epi.need(b + x * st)) continue;
         const int v = line_min_smem(s_colx + lane, x, nx, lim);
         epi(b + x * st, v >= lim ? IBIP_INF32 : v);
     }
@@ -344,6 +374,7 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_edt_x(const int32_t *__res
     if (!ok) return;
     auto g = [&](int j) -> int { return __ldg(g2 + b + j * st); };
     for (int x = w; x < nx; x += kStripWarps) {
+        if (!epi.need(b + x * st)) continue;
         const int v = line_min(g, x, nx, lim);
         epi(b + x * st, v >= lim ? IBIP_INF32 : v);
     }
