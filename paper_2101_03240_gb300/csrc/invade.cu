@@ -163,6 +163,15 @@ __global__ void k_chunk_scatter(const int32_t *__restrict__ dt2, int64_t N, int 
     }
 }
 
+// out slot holding the rank of the first voxel with the smallest value (the
+// single-voxel regime's dt2 = 1 bucket): every larger value ranks before it
+constexpr int kFirst1Slot = 35;
+
+__global__ void k_last_bucket_rank(const int32_t *pos, int base, int64_t *out)
+{
+    if (threadIdx.x == 0) *out = (int64_t)(*pos - base);
+}
+
 // ------------------------------------------- rank sort of many images --
 // The same counting sort for every image of a batch at once: per-image
 // arrays live at offsets in pooled buffers, one flat scan serves all images
@@ -182,6 +191,7 @@ struct SortJob {
     int64_t mat_off;    // first entry of this image's (bucket, chunk) matrix
     int mat_base;       // pool total before the matrix (device-written)
     int blk_vox, blk_chunk;   // first block of this image in the voxel / chunk launches
+    int64_t *out;             // the invasion's output slots (the last bucket's first rank goes there)
 };
 
 __device__ __forceinline__ int find_job(const SortJob *jobs, int n, int blk, bool chunk)
@@ -265,7 +275,10 @@ __global__ void k_chunk_hist_b(const SortJob *__restrict__ jobs, int n, const in
 __global__ void k_mat_base_b(SortJob *jobs, int n, const int32_t *__restrict__ mat)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < n) jobs[j].mat_base = mat[jobs[j].mat_off];
+    if (j >= n) return;
+    SortJob &J = jobs[j];
+    J.mat_base = mat[J.mat_off];
+    J.out[kFirst1Slot] = (int64_t)(mat[J.mat_off + (int64_t)(J.B - 1) * J.C] - J.mat_base);
 }
 
 __global__ void k_chunk_scatter_b(const SortJob *__restrict__ jobs, int n, const int32_t *__restrict__ incl,
@@ -431,6 +444,9 @@ struct Batch {
     int nA, nC, nD;    // work-list fill counts (shell candidates, removals, additions)
     int ovf;           // the shell-candidate list overflowed this iteration
     int64_t kk;        // step count handed back by the single-voxel loop
+    // single-voxel loop: candidates queued by the last commit, the rank up
+    // to which the batch holds every candidate, and the next batch's source
+    int nN, novf, tmerge, Rk, nT, minN;
 };
 
 // bits [a, b] (inclusive, within word w of a row) as a mask
@@ -765,14 +781,88 @@ __device__ __forceinline__ void bar_sync_64() { asm volatile("bar.sync 1, 64;" :
 // to know what it will queue.  Runs on warps 0-1 (64 threads, named barrier
 // 1) until the best candidate is no longer single-voxel, the front is empty
 // or the step limit is reached.
+constexpr int kNewCap = 6 * kM;   // candidates one single-voxel batch can queue
+constexpr int kMinMerge = 16;     // smaller merged batches are refilled from the bitmap
+
 template <bool L1SMEM>
 __device__ void tiny_loop(const Inv &a, Batch &B, u64 *s1, u64 *s2, u64 *s3, const int tid, int64_t &k,
                           const FastDiv &fd_nyz, const FastDiv &fd_nz, long long &n_stale, long long &n_it,
-                          long long &n_steps)
+                          long long &n_steps, long long &c_tg, long long &c_tb, long long &c_tc, int *sNr,
+                          int *sNv, int *tR, int *tI)
 {
     const int lane = tid & 31;
+    const int first1 = (int)a.out[kFirst1Slot];   // ranks below it hold dt2 > 1
+    if (tid == 0) { B.tmerge = 0; B.nN = 0; B.novf = 0; }
+    bar_sync_64();
     for (;;) {
-        if (tid < 32) {
+        const long long ta = clock64();
+        // Next batch.  A committed single-voxel ball stamps only its own
+        // centre, so the frontier changed only by the committed items and
+        // the candidates that commit queued (ranks known): every candidate
+        // ranked at or below Rk is an uncommitted item or such a new one.
+        // Their sorted merge is an exact prefix of the frontier; it is used
+        // when it is large enough, else the batch is gathered afresh.
+        bool gather = !B.tmerge;
+        if (!gather) {
+            const int m0 = B.m, J0 = B.J, Rk = B.Rk, nN = B.nN;
+            if (tid == 0) { B.nT = m0 - J0; B.minN = INT_MAX; }
+            bar_sync_64();
+            for (int e = tid; e < nN; e += 64) {
+                const int r = sNr[e];
+                if (r <= Rk) { atomicAdd(&B.nT, 1); atomicMin(&B.minN, r); }
+            }
+            bar_sync_64();
+            const int T = B.nT;
+            if (B.minN < first1) {   // a larger ball was exposed: back to the main loop
+                if (tid == 0) B.stop = 0;
+                break;
+            }
+            if (T >= kMinMerge) {
+                // position of each element = ranks below it among both sets
+                for (int e = tid; e < (m0 - J0) + nN; e += 64) {
+                    int key, v;
+                    if (e < m0 - J0) { key = B.rank[J0 + e]; v = B.idx[J0 + e]; }
+                    else {
+                        key = sNr[e - (m0 - J0)]; v = sNv[e - (m0 - J0)];
+                        if (key > Rk) continue;
+                    }
+                    int lo = J0, hi = m0;   // remaining items ranked below key
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if (B.rank[mid] < key) lo = mid + 1; else hi = mid;
+                    }
+                    int pos = lo - J0;
+                    for (int f = 0; f < nN; f++) {
+                        const int r = sNr[f];
+                        pos += (r <= Rk && r < key);
+                    }
+                    if (pos < kM) { tR[pos] = key; tI[pos] = v; }
+                }
+                bar_sync_64();
+                const int m = min(T, kM);
+                if (tid < m) {
+                    const uint32_t v = (uint32_t)tI[tid];
+                    const uint32_t x = fdiv(v, fd_nyz), rem = v - x * (uint32_t)a.ny * (uint32_t)a.nz;
+                    const uint32_t y = fdiv(rem, fd_nz);
+                    B.rank[tid] = tR[tid];
+                    B.idx[tid] = (int)v;
+                    B.r2[tid] = 1;
+                    B.x[tid] = (int)x; B.y[tid] = (int)y; B.z[tid] = (int)(rem - y * (uint32_t)a.nz);
+                }
+                if (tid == 0) {
+                    if (T > kM) B.Rk = tR[kM - 1];   // the truncated tail is still in the bitmap
+                    int stop = 0, mcap = m;
+                    const int64_t remain = a.max_steps - k;
+                    if (remain < (int64_t)m) mcap = (int)max(remain, (int64_t)0);
+                    if (mcap == 0) stop = 2;
+                    if (k > a.npore) stop = 3;
+                    B.tstop = stop; B.m = m; B.mcap = mcap; B.J = mcap;
+                }
+            } else {
+                gather = true;
+            }
+        }
+        if (gather && tid < 32) {
             const int m = gather_items<L1SMEM, false>(a, B, s1, s2, s3, lane, kM, fd_nyz, fd_nz, n_stale);
             if (lane == 0) {
                 int stop = 0, mcap = m;
@@ -785,9 +875,13 @@ __device__ void tiny_loop(const Inv &a, Batch &B, u64 *s1, u64 *s2, u64 *s3, con
                 }
                 if (k > a.npore) stop = 3;
                 B.tstop = stop; B.m = m; B.mcap = mcap; B.J = mcap;
+                B.Rk = m > 0 ? B.rank[m - 1] : INT_MAX;
             }
         }
+        if (tid == 0) { B.nN = 0; B.novf = 0; }
         bar_sync_64();
+        const long long tb = clock64();
+        if (tid == 0) c_tg += tb - ta;
         const int st = B.tstop;
         if (st) {
             if (st != 4 && tid == 0) B.stop = st;
@@ -809,6 +903,8 @@ __device__ void tiny_loop(const Inv &a, Batch &B, u64 *s1, u64 *s2, u64 *s3, con
             if (cand) atomicMin(&B.J, max(j + 1, lower_rank(B, m, best)));
         }
         bar_sync_64();
+        const long long tc = clock64();
+        if (tid == 0) c_tb += tc - tb;
         const int J = B.J;
         if (j < J) {
             const int x = B.x[j], y = B.y[j], z = B.z[j];
@@ -827,10 +923,18 @@ __device__ void tiny_loop(const Inv &a, Batch &B, u64 *s1, u64 *s2, u64 *s3, con
                 const int rq = rr[q];
                 atomicOr(a.fb0 + (rq >> 6), 1ull << (rq & 63));
                 flag_rank(s1, s2, s3, &B.cur1, rq);
+                const int slot = atomicAdd(&B.nN, 1);
+                if (slot < kNewCap) { sNr[slot] = rq; sNv[slot] = nb.v[q]; }
+                else B.novf = 1;
             }
         }
         k += J;
         if (tid == 0) { n_it++; n_steps += J; }
+        bar_sync_64();
+        if (tid == 0) {
+            B.tmerge = !B.novf;
+            c_tc += clock64() - tc;
+        }
         bar_sync_64();
     }
 }
@@ -846,6 +950,7 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
     __shared__ int sLAr[kList];
     __shared__ int sLC[kList];
     __shared__ int sLD[kList];
+    __shared__ int sNr[kNewCap], sNv[kNewCap], tR[kM], tI[kM];
     u64 *s1 = L1SMEM ? s_fb : a.fb1;
     u64 *s2 = s_fb + (L1SMEM ? a.NL1 : 0);
     u64 *s3 = s2 + a.NL2;
@@ -869,6 +974,8 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
     long long c_sel = 0, c_shell = 0, c_commit = 0, n_items = 0, n_commit_items = 0, n_stale = 0, n_units = 0;
     long long c_small = 0, n_small = 0, n_tiny = 0, n_tiny_steps = 0, c_tiny = 0;
     long long c_sub[6] = {0, 0, 0, 0, 0, 0};   // select sub-phases (all batches)
+    // bound stages 1-2, commit stage 1 and the rest, the single-voxel loop's phases
+    long long c_b1 = 0, c_b2 = 0, c_m1 = 0, c_m2 = 0, c_tg = 0, c_tb = 0, c_tc = 0;
     long long c_small_ph[3] = {0, 0, 0};       // select / bound / commit cycles of small batches
     for (;;) {
         long long t0 = clock64();
@@ -894,7 +1001,7 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
         if (B.stop) break;
         if (B.r2[0] == 1) {
             long long tt = clock64();
-            if (tid < 64) tiny_loop<L1SMEM>(a, B, s1, s2, s3, tid, k, fd_nyz, fd_nz, n_stale, n_tiny, n_tiny_steps);
+            if (tid < 64) tiny_loop<L1SMEM>(a, B, s1, s2, s3, tid, k, fd_nyz, fd_nz, n_stale, n_tiny, n_tiny_steps, c_tg, c_tb, c_tc, sNr, sNv, tR, tI);
             if (tid == 0) B.kk = k;
             __syncthreads();
             k = B.kk;
@@ -1082,6 +1189,7 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
                 return true;
             });
             __syncthreads();
+            if (tid == 0) c_b1 += clock64() - t1;
             const int n = min(B.nA, kList);
             for (int e = tid; e < n; e += kNT) {
                 const int i = sLAi[e];
@@ -1094,6 +1202,7 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
         __syncthreads();
         long long t2 = clock64();
         c_shell += t2 - t1;
+        long long tm1 = t2;
 
         // --------------------------------------------------------- commit
         // Stage 1, per row of each committed ball: stamp the voxels this ball
@@ -1156,6 +1265,8 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
             }
         }
         __syncthreads();
+        tm1 = clock64();
+        if (tid == 0) c_m1 += tm1 - t2;
         if (!B.ovf) {
             // Stage 2 from the candidate list of the bound pass (complete for
             // every committed item, ranks already loaded): a listed voxel
@@ -1254,6 +1365,7 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
         __syncthreads();
         long long t3 = clock64();
         c_commit += t3 - t2;
+        c_m2 += t3 - tm1;
         if (small) {
             c_small += t3 - t0;
             n_small++;
@@ -1279,6 +1391,13 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
         for (int q = 0; q < 3; q++) a.out[16 + q] = c_small_ph[q];
         a.out[22] = c_sub[4];
         a.out[23] = c_sub[5];
+        a.out[24] = c_b1;
+        a.out[25] = c_shell - c_b1;
+        a.out[26] = c_m1;
+        a.out[27] = c_m2;
+        a.out[28] = c_tg;
+        a.out[29] = c_tb;
+        a.out[33] = c_tc;
         a.out[19] = n_tiny;
         a.out[20] = n_tiny_steps;
         a.out[21] = c_tiny;
@@ -1474,6 +1593,10 @@ int invade_setup(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, int6
     IBIP_LAUNCH(ctx);
     int st = ibip_scan_excl_i32(ctx, mat, mat, (int64_t)C * B);
     if (st) return st;
+    // rank of the first voxel of the last bucket (the smallest value), read
+    // before the scatter advances the counters
+    k_last_bucket_rank<<<1, 32, 0, s>>>(mat + (int64_t)(B - 1) * C, 0, mem.out + kFirst1Slot);
+    IBIP_LAUNCH(ctx);
     if (smem) k_chunk_scatter<true><<<nb, wpb * 32, sm, s>>>(dt2, N, (int)S, C, bk, mat, mem.rank, mem.okey);
     else k_chunk_scatter<false><<<nb, wpb * 32, 0, s>>>(dt2, N, (int)S, C, bk, mat, mem.rank, mem.okey);
     IBIP_LAUNCH(ctx);
@@ -1623,6 +1746,7 @@ int ibip_invade_batch_run(ibip_ctx *ctx, int n, IbipBatchItem *it, IbipBatchEarl
         off += z[j].total();
         SortJob q = {};
         q.dt2 = it[j].dt2; q.N = nvox(it[j].d); q.seq = it[j].seq; q.rank = mem.rank; q.okey = mem.okey;
+        q.out = mem.out;
         q.maxd = hasinf[j] ? 0 : maxd[j]; q.hasinf = hasinf[j];
         q.pres_off = pres_total;
         pres_total += (int64_t)q.maxd + 1;
