@@ -412,6 +412,53 @@ def run_serve(args, rank, world):
 
 # --------------------------------------------------------------- ours ----
 
+R2_CLASSES = [("r=1", 1, 1), ("1<r<=2", 2, 4), ("2<r<=4", 5, 16), ("4<r<=8", 17, 64), ("r>8", 65, 1 << 62)]
+
+
+def step_time_stats(rec, r2, K, span_cycles, span_ns):
+    """Device time per invasion step, p50/p99 per radius class.  `rec` holds
+    one row per batch (first step, steps, SM cycles, loop); each step of a
+    batch is charged the batch's cycles over its steps, and cycles become
+    microseconds by the kernel's own cycles-per-nanosecond ratio."""
+    import numpy as np
+    rec = np.asarray(rec, dtype=np.int64).reshape(-1, 4)
+    first, n, cyc = rec[:, 0], rec[:, 1], rec[:, 2]
+    if len(rec) == 0 or int(n.sum()) != K or first[0] != 0 or np.any(first[1:] != np.cumsum(n)[:-1]):
+        return None   # batches must tile steps 0..K-1 in order
+    mhz = span_cycles / max(span_ns, 1) * 1e3
+    us = np.repeat(cyc / np.maximum(n, 1) / mhz, n)
+    r2 = np.asarray(r2[:K], dtype=np.int64)
+
+    def pct(x):
+        return {"steps": int(len(x)), "p50_us": float(np.percentile(x, 50)), "p99_us": float(np.percentile(x, 99)),
+                "mean_us": float(x.mean())} if len(x) else {"steps": 0}
+
+    classes = {name: pct(us[(r2 >= lo) & (r2 <= hi)]) for name, lo, hi in R2_CLASSES}
+    busy = cyc.sum() / mhz
+    return {"sm_mhz_in_kernel": mhz, "batches": int(len(rec)),
+            "batches_single_voxel_loop": int((rec[:, 3] == 1).sum()),
+            "batch_us": {"p50": float(np.percentile(cyc / mhz, 50)), "p99": float(np.percentile(cyc / mhz, 99))},
+            "all": pct(us), "by_radius": classes,
+            "traced_fraction_of_kernel": float(busy / (span_ns * 1e-3)) if span_ns else None,
+            "note": "amortised: a batch's device time over the steps it committed, from one untimed "
+                    "traced invasion (ibip_invade_trace)"}
+
+
+def invasion_step_times(ctx, img_d, w):
+    import torch
+    d = ctx.edt(img_d)
+    npore = int((img_d > 0).sum().item())
+    buf = torch.zeros((npore + 1, 4), dtype=torch.int32, device=img_d.device)
+    ctx.invade_trace(buf)
+    try:
+        _, r2, _, K, _ = ctx.invade(img_d, d, inlet=w.inlet)
+    finally:
+        ctx.invade_trace(None)
+    s = ctx.invade_stats()
+    nrec = min(s["trace_batches"], buf.shape[0])
+    return step_time_stats(buf[:nrec].cpu().numpy(), r2.cpu().numpy(), K, s["span_cycles"], s["span_ns"])
+
+
 def run_ours(args, rank, world):
     import numpy as np
     import torch
@@ -520,6 +567,9 @@ def run_ours(args, rank, world):
                     "note": "pore voxels trapped (defending phase cut from the outlet) after the invasion and "
                             "after the opening's last level, the opening's levels read as a sequence"}
 
+    # ---- time per invasion step by radius class, once, untimed
+    step_times = invasion_step_times(ctx, img_d, w) if args.rule == "frontier" else None
+
     if rank != 0:
         return None
 
@@ -581,6 +631,7 @@ def run_ours(args, rank, world):
         "trapping_vs_opening": trap_cmp,
         "invasion_steps_per_s": K / (prof["invade"][0] / args.steps * 1e-3) if prof["invade"][1] else None,
         "invasion_us_per_step": us_per_step,
+        "invasion_step_times": step_times,
         "e2e": {"value": job_rate(N, world, e2e_step * 1e-3), "unit": "voxels/s",
                 "h2d_bytes_per_step": int(img_h.nbytes),
                 "d2h_bytes_per_step": int(out_seq.numel() * 4 + K * 4)},

@@ -383,19 +383,43 @@ IBIP_API int ibip_profile_enable(ibip_ctx *ctx, int on);
  * (*h_spans) since profiling was enabled. */
 IBIP_API int ibip_profile_read(ibip_ctx *ctx, int cls, double *h_ms, int64_t *h_spans);
 
-/* Counters of the context's last ibip_invade call, for tracing: writes up
- * to n of [steps, status, iterations, cycles selecting, cycles in the
- * candidate-bound pass, cycles committing (SM clock, thread 0), batch items
- * taken, batch items committed, stale summary bits cleared, ball rows
- * committed, cycles in batches of single-voxel balls, number of such
- * batches, then select sub-phase cycles (gather, item data,
- * pairwise tests, bookkeeping) and the three phase cycles of single-voxel
- * batches, iterations, steps and cycles of the single-voxel loop, then
- * gather sub-phase cycles for the two loops and the single-voxel loop's
- * phase cycles]; entries 30-32 hold the rounds, tile activations and
- * relaxation sweeps of the context's last widest-path propagation
- * (trapping or the opening's trim, one-launch form); n <= 36 entries. */
+/* Counters of the context's last ibip_invade / ibip_invade_ex call, for
+ * tracing (cycles are SM clock cycles counted by thread 0 of the invasion
+ * CTA).  Writes up to n (at most 48) of:
+ *   0 steps, 1 status, 2 iterations of the main loop,
+ *   3-5 cycles selecting, bounding (candidate shell) and committing,
+ *   6 batch items taken, 7 batch items committed, 8 stale summary bits
+ *   cleared, 9 ball rows committed,
+ *   10-11 cycles and count of main-loop batches of single-voxel balls,
+ *   12-15 select sub-phase cycles (gather, item data, pairwise tests,
+ *   bookkeeping), 16-18 select / bound / commit cycles of those batches,
+ *   19-21 iterations, steps and cycles of the single-voxel loop,
+ *   22-23 bookkeeping sub-phases (containment rounds, row prefix),
+ *   24-25 bound stages 1 (shell listing) and 2 (rank lookups),
+ *   26-27 commit stage 1 (stamping) and the rest (queueing),
+ *   28-29 and 33 the single-voxel loop's gather, bound and commit cycles,
+ *   30-32 rounds, tile activations and relaxation sweeps of the context's
+ *   last widest-path propagation (trapping or the opening's trim,
+ *   one-launch form),
+ *   34 unused, 35 rank of the first voxel with the smallest dt2,
+ *   36 batches seen by the trace (ibip_invade_trace; counted beyond its
+ *   capacity), 37 the kernel's span in SM cycles, 38 the same span in
+ *   nanoseconds of the global timer (their ratio is the SM clock),
+ *   39-41 shell rows, listed shell candidates and removed candidates,
+ *   summed over the main loop's batches. */
 IBIP_API int ibip_invade_stats(const ibip_ctx *ctx, int64_t *h_stats, int n);
+
+/* Per-batch timing trace of later ibip_invade / ibip_invade_ex calls on
+ * this context (diagnostics; the paper has no counterpart: it measures the
+ * per-step cost of the sequential invasion of Section 2.1 on this design).
+ * d_trace: device array of capacity_records records of four int32 each,
+ * 16-byte aligned, owned by the caller and kept alive while tracing is on:
+ * {first step of the batch (0-based), steps it committed, SM cycles from
+ * its selection to the end of its commit, loop (0 main, 1 single-voxel)}.
+ * Records past the capacity are counted (stats entry 36), not written.
+ * d_trace == null turns tracing off.  Returns IBIP_ERR_ARG for a negative
+ * capacity or a misaligned array.  Batched calls are never traced. */
+IBIP_API int ibip_invade_trace(ibip_ctx *ctx, int32_t *d_trace, int64_t capacity_records);
 
 /* Static text for a status code. */
 IBIP_API const char *ibip_status_string(int status);

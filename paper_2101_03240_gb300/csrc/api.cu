@@ -146,7 +146,7 @@ int ibip_run_job(ibip_ctx *ctx, ibip_job &J)
     if (!d) return IBIP_ERR_OOM;
     int st = ibip_edt_launch(ctx, J.image, J.dims, d);
     if (st) return st;
-    int64_t out[36] = {0};
+    int64_t out[kInvStats] = {0};
     st = ibip_invade_run(ctx, d, J.dims, J.inlet, nvox(J.dims), J.seq, J.step_r2, J.step_centre, J.capacity_steps,
                          out);
     if (st) return st;
@@ -307,7 +307,15 @@ int64_t ibip_launch_count(const ibip_ctx *ctx) { return ctx ? ctx->launches : -1
 int ibip_invade_stats(const ibip_ctx *ctx, int64_t *h_stats, int n)
 {
     if (!ctx || !h_stats || n < 0) return IBIP_ERR_ARG;
-    for (int i = 0; i < n && i < 36; i++) h_stats[i] = ctx->inv_stats[i];
+    for (int i = 0; i < n && i < kInvStats; i++) h_stats[i] = ctx->inv_stats[i];
+    return IBIP_OK;
+}
+
+int ibip_invade_trace(ibip_ctx *ctx, int32_t *d_trace, int64_t capacity_records)
+{
+    if (!ctx || (d_trace && (capacity_records < 0 || ((uintptr_t)d_trace & 15)))) return IBIP_ERR_ARG;
+    ctx->trace = d_trace;
+    ctx->trace_cap = d_trace ? capacity_records : 0;
     return IBIP_OK;
 }
 
@@ -371,7 +379,7 @@ int ibip_invade(ibip_ctx *ctx, const uint8_t *image, const int32_t *dt2, ibip_di
         if (st) return st;
         d = t;
     }
-    int64_t out[36] = {0};
+    int64_t out[kInvStats] = {0};
     int st = ibip_invade_run(ctx, d, dims, inlet, max_steps, seq, step_r2, step_centre, capacity_steps, out);
     if (st) return st;
     memcpy(ctx->inv_stats, out, sizeof(out));
@@ -398,7 +406,7 @@ int ibip_invade_ex(ibip_ctx *ctx, const uint8_t *image, const int32_t *dt2, ibip
         if (st) return st;
         d = t;
     }
-    int64_t out[36] = {0};
+    int64_t out[kInvStats] = {0};
     int st = ibip_invade_run(ctx, d, dims, inlet_mask ? 0 : inlet, max_steps, seq, step_r2, step_centre,
                              capacity_steps, out, inlet_mask, resume);
     if (st) return st;

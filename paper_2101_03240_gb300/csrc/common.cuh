@@ -36,6 +36,9 @@ enum ScratchSlot {
     SC_NSLOTS
 };
 
+// int64 counters an invasion reports (ibip_invade_stats)
+constexpr int kInvStats = 48;
+
 struct ibip_ctx {
     int device;
     cudaStream_t stream;
@@ -45,7 +48,11 @@ struct ibip_ctx {
     size_t slot_bytes[SC_NSLOTS];
     void *h_pinned;   // small pinned host buffer for scalar readback
     void *prof;       // event log when profiling is on (api.cu), else null
-    int64_t inv_stats[36];   // counters of the last ibip_invade (ibip_invade_stats)
+    int64_t inv_stats[kInvStats];   // counters of the last ibip_invade (ibip_invade_stats)
+    // Per-batch timing records of later single-image invasions (device
+    // array of int4, capacity in records), or null.
+    void *trace;
+    int64_t trace_cap;
     // Arena mode (server slots): scratch is carved from [arena, arena +
     // arena_size) and never freed; a request that does not fit fails.
     char *arena;

@@ -41,7 +41,7 @@ constexpr int kM = 64;           // batch size (items per iteration)
 constexpr int kNT = 384;         // threads of the persistent CTA
 constexpr int kChunk = 4096;     // voxels per rank-sort chunk (minimum)
 constexpr int kSmemL1Max = 12288;
-constexpr int kNOut = 36;          // int64 outputs of the invasion kernel
+constexpr int kNOut = kInvStats;   // int64 outputs of the invasion kernel
 static_assert(64 + kNOut * sizeof(long long) <= kSmallBytes, "output slot too small");
 
 typedef unsigned long long u64;
@@ -338,6 +338,8 @@ struct Inv {
     const uint8_t *mask;   // inlet voxels (nonzero), or null: the inlet face
     int resume;            // seq holds an earlier run's steps 1..k0 on entry
     int64_t k0;            // steps already taken (resume), else 0
+    int4 *trace;           // per-batch records {first step, steps, SM cycles, loop}, or null
+    int64_t trace_cap;     // records that fit in trace
 };
 
 __global__ void k_seq_init(const int32_t *__restrict__ dt2, int64_t N, int32_t *seq)
@@ -764,15 +766,39 @@ __device__ int gather_items(const Inv &a, Batch &B, u64 *s1, u64 *s2, u64 *s3, i
 
 // Flag rank r in the three summary levels (32-bit halves of the 64-bit
 // words; bit index r >> 6 in level 1, r >> 12 in level 2, r >> 18 in level 3).
+// While a commit runs the summaries only gain bits (the gather clears stale
+// ones in its own phase) and the cursor only falls, so each is read first
+// and written only when it changes: most additions touch no shared atomic.
 __device__ __forceinline__ void flag_rank(u64 *s1, u64 *s2, u64 *s3, int *cur1, int r)
 {
-    atomicMin(cur1, r >> 12);
-    atomicOr((uint32_t *)s1 + (r >> 11), 1u << ((r >> 6) & 31));
-    atomicOr((uint32_t *)s2 + (r >> 17), 1u << ((r >> 12) & 31));
-    atomicOr((uint32_t *)s3 + (r >> 23), 1u << ((r >> 18) & 31));
+    uint32_t *p1 = (uint32_t *)s1 + (r >> 11), *p2 = (uint32_t *)s2 + (r >> 17), *p3 = (uint32_t *)s3 + (r >> 23);
+    const uint32_t b1 = 1u << ((r >> 6) & 31), b2 = 1u << ((r >> 12) & 31), b3 = 1u << ((r >> 18) & 31);
+    const int c = *(volatile int *)cur1;
+    const uint32_t w1 = *(volatile uint32_t *)p1, w2 = *(volatile uint32_t *)p2, w3 = *(volatile uint32_t *)p3;
+    if ((r >> 12) < c) atomicMin(cur1, r >> 12);
+    if (!(w1 & b1)) atomicOr(p1, b1);
+    if (!(w2 & b2)) atomicOr(p2, b2);
+    if (!(w3 & b3)) atomicOr(p3, b3);
 }
 
 __device__ __forceinline__ void bar_sync_64() { asm volatile("bar.sync 1, 64;" ::: "memory"); }
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// One timing record per batch (thread 0): first step (0-based), steps
+// committed, SM cycles from batch selection to the end of its commit, and
+// the loop that ran it (0 main, 1 single-voxel).  Counted past the capacity.
+__device__ __forceinline__ void trace_batch(const Inv &a, long long &ntr, int64_t k, int n, long long cyc, int loop)
+{
+    if (!a.trace) return;
+    if (ntr < a.trace_cap) a.trace[ntr] = make_int4((int)k, n, (int)min(cyc, (long long)INT_MAX), loop);
+    ntr++;
+}
 
 // Single-voxel regime.  Once the best candidate has dt2 == 1 every candidate
 // does, each ball is its own centre, and those centres are queued already:
@@ -788,7 +814,7 @@ template <bool L1SMEM>
 __device__ void tiny_loop(const Inv &a, Batch &B, u64 *s1, u64 *s2, u64 *s3, const int tid, int64_t &k,
                           const FastDiv &fd_nyz, const FastDiv &fd_nz, long long &n_stale, long long &n_it,
                           long long &n_steps, long long &c_tg, long long &c_tb, long long &c_tc, int *sNr,
-                          int *sNv, int *tR, int *tI)
+                          int *sNv, int *tR, int *tI, long long &ntr)
 {
     const int lane = tid & 31;
     const int first1 = (int)a.out[kFirst1Slot];   // ranks below it hold dt2 > 1
@@ -807,10 +833,14 @@ __device__ void tiny_loop(const Inv &a, Batch &B, u64 *s1, u64 *s2, u64 *s3, con
             const int m0 = B.m, J0 = B.J, Rk = B.Rk, nN = B.nN;
             if (tid == 0) { B.nT = m0 - J0; B.minN = INT_MAX; }
             bar_sync_64();
+            int cnt = 0, mn = INT_MAX;
             for (int e = tid; e < nN; e += 64) {
                 const int r = sNr[e];
-                if (r <= Rk) { atomicAdd(&B.nT, 1); atomicMin(&B.minN, r); }
+                if (r <= Rk) { cnt++; mn = min(mn, r); }
             }
+            cnt = __reduce_add_sync(0xffffffffu, cnt);
+            mn = __reduce_min_sync(0xffffffffu, mn);
+            if (lane == 0) { atomicAdd(&B.nT, cnt); atomicMin(&B.minN, mn); }
             bar_sync_64();
             const int T = B.nT;
             if (B.minN < first1) {   // a larger ball was exposed: back to the main loop
@@ -891,6 +921,7 @@ __device__ void tiny_loop(const Inv &a, Batch &B, u64 *s1, u64 *s2, u64 *s3, con
         Nb6 nb;
         unsigned cand = 0;
         int rr[6];
+        int jl = INT_MAX;
         if (j < mcap) {
             nb6(a, B.x[j], B.y[j], B.z[j], B.idx[j], nb);
             cand = nb6_candidates(a, nb);
@@ -900,8 +931,10 @@ __device__ void tiny_loop(const Inv &a, Batch &B, u64 *s1, u64 *s2, u64 *s3, con
                 rr[q] = ((cand >> q) & 1) ? __ldg(a.rank + nb.v[q]) : INT_MAX;
                 best = min(best, rr[q]);
             }
-            if (cand) atomicMin(&B.J, max(j + 1, lower_rank(B, m, best)));
+            if (cand) jl = max(j + 1, lower_rank(B, m, best));
         }
+        jl = __reduce_min_sync(0xffffffffu, jl);
+        if (lane == 0 && jl < INT_MAX) atomicMin(&B.J, jl);
         bar_sync_64();
         const long long tc = clock64();
         if (tid == 0) c_tb += tc - tb;
@@ -916,16 +949,26 @@ __device__ void tiny_loop(const Inv &a, Batch &B, u64 *s1, u64 *s2, u64 *s3, con
                 a.step_r2[k + j] = 1;
                 if (a.step_centre) a.step_centre[k + j] = B.idx[j];
             }
+            uint32_t got[6];
 #pragma unroll
-            for (int q = 0; q < 6; q++) {
-                if (!((cand >> q) & 1)) continue;
-                if (atomicOr(a.added + nb.word[q], nb.bit[q]) & nb.bit[q]) continue;
-                const int rq = rr[q];
-                atomicOr(a.fb0 + (rq >> 6), 1ull << (rq & 63));
-                flag_rank(s1, s2, s3, &B.cur1, rq);
-                const int slot = atomicAdd(&B.nN, 1);
-                if (slot < kNewCap) { sNr[slot] = rq; sNv[slot] = nb.v[q]; }
-                else B.novf = 1;
+            for (int q = 0; q < 6; q++)
+                got[q] = ((cand >> q) & 1) ? atomicOr(a.added + nb.word[q], nb.bit[q]) : nb.bit[q];
+            unsigned fr = 0;
+#pragma unroll
+            for (int q = 0; q < 6; q++)
+                if (!(got[q] & nb.bit[q])) fr |= 1u << q;
+            if (fr) {
+                int slot = atomicAdd(&B.nN, __popc(fr));
+#pragma unroll
+                for (int q = 0; q < 6; q++) {
+                    if (!((fr >> q) & 1)) continue;
+                    const int rq = rr[q];
+                    atomicOr(a.fb0 + (rq >> 6), 1ull << (rq & 63));
+                    flag_rank(s1, s2, s3, &B.cur1, rq);
+                    if (slot < kNewCap) { sNr[slot] = rq; sNv[slot] = nb.v[q]; }
+                    else B.novf = 1;
+                    slot++;
+                }
             }
         }
         k += J;
@@ -933,7 +976,9 @@ __device__ void tiny_loop(const Inv &a, Batch &B, u64 *s1, u64 *s2, u64 *s3, con
         bar_sync_64();
         if (tid == 0) {
             B.tmerge = !B.novf;
-            c_tc += clock64() - tc;
+            const long long te = clock64();
+            c_tc += te - tc;
+            trace_batch(a, ntr, k - J, J, te - ta, 1);
         }
         bar_sync_64();
     }
@@ -969,6 +1014,10 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
     }
     __syncthreads();
 
+    const long long span_c0 = clock64();
+    const unsigned long long span_t0 = global_ns();
+    long long ntr = 0;   // timing records (thread 0)
+    long long n_shell_units = 0, n_listed = 0, n_removed = 0;   // work of the main loop's batches
     int64_t k = a.k0, iters = 0;
     // diagnostics kept by thread 0: cycles per phase, items, stale summary bits
     long long c_sel = 0, c_shell = 0, c_commit = 0, n_items = 0, n_commit_items = 0, n_stale = 0, n_units = 0;
@@ -1001,7 +1050,7 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
         if (B.stop) break;
         if (B.r2[0] == 1) {
             long long tt = clock64();
-            if (tid < 64) tiny_loop<L1SMEM>(a, B, s1, s2, s3, tid, k, fd_nyz, fd_nz, n_stale, n_tiny, n_tiny_steps, c_tg, c_tb, c_tc, sNr, sNv, tR, tI);
+            if (tid < 64) tiny_loop<L1SMEM>(a, B, s1, s2, s3, tid, k, fd_nyz, fd_nz, n_stale, n_tiny, n_tiny_steps, c_tg, c_tb, c_tc, sNr, sNv, tR, tI, ntr);
             if (tid == 0) B.kk = k;
             __syncthreads();
             k = B.kk;
@@ -1153,9 +1202,10 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
                     // single-voxel ball: its shell is its six neighbours
                     Nb6 nb;
                     nb6(a, B.x[i], B.y[i], B.z[i], B.idx[i], nb);
-                    for (unsigned c = nb6_candidates(a, nb); c; c &= c - 1) {
+                    unsigned c = nb6_candidates(a, nb);
+                    if (!c) return true;
+                    for (int slot = atomicAdd(&B.nA, __popc(c)); c; c &= c - 1, slot++) {
                         const int q = __ffs(c) - 1;
-                        const int slot = atomicAdd(&B.nA, 1);
                         if (slot < kList) {
                             sLA[slot] = nb.v[q];
                             sLAi[slot] = (unsigned char)i;
@@ -1173,9 +1223,9 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
                 for (int w = za >> 5; w <= (zb >> 5); w++) {
                     uint32_t cand = ldcg32(a.avail + row * a.NW + w) & ~ldcg32(a.added + row * a.NW + w) &
                                     span_mask(w, za, zb) & ~span_mask(w, ra, rbz);
-                    for (; cand; cand &= cand - 1) {
+                    if (!cand) continue;
+                    for (int slot = atomicAdd(&B.nA, __popc(cand)); cand; cand &= cand - 1, slot++) {
                         const int z = w * 32 + __ffs(cand) - 1;
-                        const int slot = atomicAdd(&B.nA, 1);
                         if (slot < kList) {
                             sLA[slot] = (int)(row * a.nz + z);
                             sLAi[slot] = (unsigned char)i;
@@ -1190,14 +1240,28 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
             });
             __syncthreads();
             if (tid == 0) c_b1 += clock64() - t1;
+            // entries of items at or past J are never committed; the ranks
+            // of up to four entries per thread are loaded together, and each
+            // warp lowers J once
             const int n = min(B.nA, kList);
-            for (int e = tid; e < n; e += kNT) {
-                const int i = sLAi[e];
-                if (i >= *(volatile int *)&B.J) continue;   // never committed
-                const int ru = __ldg(a.rank + sLA[e]);
-                sLAr[e] = ru;
-                if (i + 1 < *(volatile int *)&B.J) atomicMin(&B.J, max(i + 1, lower_rank(B, m, ru)));
+            int jl = *(volatile int *)&B.J;
+            for (int e0 = tid; e0 < n; e0 += 4 * kNT) {
+                int ru[4], it[4];
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const int e = e0 + q * kNT;
+                    it[q] = e < n ? sLAi[e] : kM;
+                    ru[q] = it[q] < jl ? __ldg(a.rank + sLA[e]) : 0;
+                }
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    if (it[q] >= jl) continue;
+                    sLAr[e0 + q * kNT] = ru[q];
+                    if (it[q] + 1 < jl) jl = min(jl, max(it[q] + 1, lower_rank(B, m, ru[q])));
+                }
             }
+            jl = __reduce_min_sync(0xffffffffu, jl);
+            if (lane == 0) atomicMin(&B.J, jl);
         }
         __syncthreads();
         long long t2 = clock64();
@@ -1242,14 +1306,16 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
                         if (ball_run(B, i2, x, y, l2, h2)) own &= ~span_mask(w, l2, h2);
                     }
                     if (!own) continue;
-                    uint32_t newly = ldcg32(a.avail + rb + w) & own;
+                    // `added` does not change during this stage: load it with `avail`
+                    const uint32_t av = ldcg32(a.avail + rb + w), ad = ldcg32(a.added + rb + w);
+                    const uint32_t newly = av & own;
                     if (!newly) continue;
                     atomicAnd(a.avail + rb + w, ~newly);
-                    uint32_t gone = newly & ldcg32(a.added + rb + w);
+                    uint32_t gone = newly & ad;
                     for (uint32_t n2 = newly; n2; n2 &= n2 - 1) a.seq[vb + w * 32 + __ffs(n2) - 1] = label;
-                    for (; gone; gone &= gone - 1) {
-                        int v = (int)(vb + w * 32 + __ffs(gone) - 1);
-                        int slot = atomicAdd(&B.nC, 1);
+                    if (!gone) continue;
+                    for (int slot = atomicAdd(&B.nC, __popc(gone)); gone; gone &= gone - 1, slot++) {
+                        const int v = (int)(vb + w * 32 + __ffs(gone) - 1);
                         if (slot < kList) sLC[slot] = v; else gC[slot - kList] = v;
                     }
                 }
@@ -1272,24 +1338,47 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
             // every committed item, ranks already loaded): a listed voxel
             // that is still uninvaded after the stamping lies outside every
             // committed ball; queue it once.  Apply the removals too.
-            const int n = min(B.nA, kList), nC = B.nC;
-            for (int e = tid; e < n + nC; e += kNT) {
-                if (e < n) {
-                    if (sLAi[e] >= J) continue;
-                    const uint32_t v = (uint32_t)sLA[e];
-                    const uint32_t row = fdiv(v, fd_nz), z = v - row * (uint32_t)a.nz;
-                    const int64_t w = (int64_t)row * a.NW + (z >> 5);
-                    const uint32_t bit = 1u << (z & 31);
-                    if (!(ldcg32(a.avail + w) & bit)) continue;
-                    if (atomicOr(a.added + w, bit) & bit) continue;
-                    const int r = sLAr[e];
+            // Four entries per thread at a time, so that their loads and
+            // returning atomics overlap.  Removed and added voxels differ
+            // (one is stamped, the other not), so the order does not matter.
+            const int n = min(B.nA, kList), tot = n + B.nC;
+            for (int e0 = tid; e0 < tot; e0 += 4 * kNT) {
+                int64_t wd[4];
+                uint32_t bt[4], got[4];
+                int rr[4];
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const int e = e0 + q * kNT;
+                    wd[q] = -1; bt[q] = 0; got[q] = 0; rr[q] = -1;
+                    if (e < n) {
+                        if (sLAi[e] < J) {
+                            const uint32_t v = (uint32_t)sLA[e];
+                            const uint32_t row = fdiv(v, fd_nz), z = v - row * (uint32_t)a.nz;
+                            wd[q] = (int64_t)row * a.NW + (z >> 5);
+                            bt[q] = 1u << (z & 31);
+                            rr[q] = sLAr[e];
+                            got[q] = ldcg32(a.avail + wd[q]);
+                        }
+                    } else if (e < tot) {
+                        const int f = e - n;
+                        rr[q] = __ldg(a.rank + (f < kList ? sLC[f] : gC[f - kList]));
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    if (wd[q] >= 0) {
+                        // still uninvaded after the stamping: queue it once
+                        got[q] = (got[q] & bt[q]) && !(atomicOr(a.added + wd[q], bt[q]) & bt[q]);
+                    } else if (rr[q] >= 0) {
+                        atomicAnd(a.fb0 + (rr[q] >> 6), ~(1ull << (rr[q] & 63)));
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    if (wd[q] < 0 || !got[q]) continue;
+                    const int r = rr[q];
                     atomicOr(a.fb0 + (r >> 6), 1ull << (r & 63));
                     flag_rank(s1, s2, s3, &B.cur1, r);
-                } else {
-                    const int f = e - n;
-                    const int v = f < kList ? sLC[f] : gC[f - kList];
-                    const int r = __ldg(a.rank + v);
-                    atomicAnd(a.fb0 + (r >> 6), ~(1ull << (r & 63)));
                 }
             }
         } else {
@@ -1355,17 +1444,22 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
             }
         }
         }
-        k += __popcll(B.keep & jmask);
+        const int nk = __popcll(B.keep & jmask);
+        k += nk;
         iters++;
         n_items += m;
         n_commit_items += J;
         n_units += B.upre[J];
+        n_shell_units += B.dpre[mcap];
+        n_listed += B.nA;
+        n_removed += B.nC;
         if (tid == 0) B.mtarget = min(kM, max(16, 2 * J + 8));
         const bool small = B.upre[J] == __popcll(B.keep & jmask) && B.r2[0] == 1;
         __syncthreads();
         long long t3 = clock64();
         c_commit += t3 - t2;
         c_m2 += t3 - tm1;
+        if (tid == 0) trace_batch(a, ntr, k - nk, nk, t3 - t0, 0);
         if (small) {
             c_small += t3 - t0;
             n_small++;
@@ -1398,6 +1492,12 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
         a.out[28] = c_tg;
         a.out[29] = c_tb;
         a.out[33] = c_tc;
+        a.out[36] = ntr;
+        a.out[39] = n_shell_units;
+        a.out[40] = n_listed;
+        a.out[41] = n_removed;
+        a.out[37] = clock64() - span_c0;
+        a.out[38] = (int64_t)(global_ns() - span_t0);
         a.out[19] = n_tiny;
         a.out[20] = n_tiny_steps;
         a.out[21] = c_tiny;
@@ -1539,6 +1639,8 @@ Inv make_inv(const int32_t *dt2, ibip_dims d, int inlet, int64_t max_steps, int3
     a.fb0 = mem.fb; a.fb1 = mem.fb + a.NL0; a.fb2 = a.fb1 + a.NL1; a.fb3 = a.fb2 + a.NL2;
     a.seq = seq; a.step_r2 = step_r2; a.step_centre = step_centre; a.out = mem.out;
     a.isq_n = std::min(maxd + 1, 16384);
+    a.trace = nullptr;
+    a.trace_cap = 0;
     return a;
 }
 
@@ -1663,6 +1765,8 @@ int ibip_invade_run(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, i
     int st = invade_setup(ctx, dt2, d, inlet, max_steps, seq, step_r2, step_centre, cap, maxd, npore, hasinf, mem, &a,
                           mask, resume, k0);
     if (st) return st;
+    a.trace = (int4 *)ctx->trace;
+    a.trace_cap = ctx->trace ? ctx->trace_cap : 0;
     ibip_prof_end(ctx, IBIP_K_RANK);
     const FastDiv fd_nyz = make_fastdiv((uint32_t)d.ny * (uint32_t)d.nz), fd_nz = make_fastdiv((uint32_t)d.nz);
     const bool l1smem = a.NL1 <= kSmemL1Max;

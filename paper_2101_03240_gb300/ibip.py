@@ -82,6 +82,7 @@ def _lib():
                 "ibip_profile_enable": (C.c_int, [P, C.c_int]),
                 "ibip_invade_batched": (C.c_int, [P, i32, P]),
                 "ibip_invade_stats": (C.c_int, [P, C.POINTER(i64), C.c_int]),
+                "ibip_invade_trace": (C.c_int, [P, P, i64]),
                 "ibip_profile_read": (C.c_int, [P, C.c_int, C.POINTER(dbl), C.POINTER(i64)]),
                 "ibip_job_footprint": (i64, [Dims, C.c_int]),
                 "ibip_trapping_ex": (C.c_int, [P, P, Dims, C.c_int, P, P, P, i64, P, C.POINTER(i64)]),
@@ -209,14 +210,30 @@ class Context:
 
     def invade_stats(self) -> dict:
         """Counters of the last invade call (see ibip_invade_stats)."""
-        a = (C.c_int64 * 36)()
-        _lib().ibip_invade_stats(self._h, a, 36)
+        a = (C.c_int64 * 48)()
+        _lib().ibip_invade_stats(self._h, a, 48)
         keys = ["steps", "status", "iterations", "cycles_select", "cycles_bound", "cycles_commit", "items",
                 "items_committed", "stale_bits", "rows_committed", "cycles_small_batches", "small_batches",
                 "sel_gather", "sel_items", "sel_pairs", "sel_tail", "small_select", "small_bound", "small_commit",
-                "tiny_iterations", "tiny_steps", "cycles_tiny", "s3_cont", "s3_prefix", "g_scan", "g_extract",
-                "g_items", "t_walk", "t_words", "t_scan", "mm_rounds", "mm_activations", "mm_sweeps"]
+                "tiny_iterations", "tiny_steps", "cycles_tiny", "s3_cont", "s3_prefix", "bound_list",
+                "bound_ranks", "commit_stamp", "commit_queue", "tiny_gather", "tiny_bound", "mm_rounds",
+                "mm_activations", "mm_sweeps", "tiny_commit", "unused", "first_unit_rank", "trace_batches",
+                "span_cycles", "span_ns", "shell_units", "shell_listed", "removed"]
         return dict(zip(keys, [int(x) for x in a]))
+
+    def invade_trace(self, buf):
+        """Record one timing row per batch of later invade calls into `buf`
+        (CUDA int32 tensor of shape (n, 4): first step, steps, SM cycles,
+        loop), or stop recording (None).  See ibip_invade_trace."""
+        if buf is None:
+            st = _lib().ibip_invade_trace(self._h, None, 0)
+        else:
+            assert buf.is_cuda and buf.dtype == torch.int32 and buf.dim() == 2 and buf.shape[1] == 4
+            assert buf.is_contiguous()
+            st = _lib().ibip_invade_trace(self._h, _ptr(buf), buf.shape[0])
+        if st != OK:
+            raise IbipError("ibip_invade_trace", st)
+        self._trace = buf
 
     def synchronize(self):
         st = _lib().ibip_synchronize(self._h)
