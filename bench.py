@@ -421,7 +421,8 @@ def step_time_stats(rec, r2, K, span_cycles, span_ns):
     batch is charged the batch's cycles over its steps, and cycles become
     microseconds by the kernel's own cycles-per-nanosecond ratio."""
     import numpy as np
-    rec = np.asarray(rec, dtype=np.int64).reshape(-1, 4)
+    rec = np.asarray(rec, dtype=np.int64)
+    rec = rec.reshape(len(rec), -1)[:, :4] if len(rec) else rec.reshape(0, 4)
     first, n, cyc = rec[:, 0], rec[:, 1], rec[:, 2]
     if len(rec) == 0 or int(n.sum()) != K or first[0] != 0 or np.any(first[1:] != np.cumsum(n)[:-1]):
         return None   # batches must tile steps 0..K-1 in order
@@ -448,7 +449,7 @@ def invasion_step_times(ctx, img_d, w):
     import torch
     d = ctx.edt(img_d)
     npore = int((img_d > 0).sum().item())
-    buf = torch.zeros((npore + 1, 4), dtype=torch.int32, device=img_d.device)
+    buf = torch.zeros((npore + 1, 8), dtype=torch.int32, device=img_d.device)
     ctx.invade_trace(buf)
     try:
         _, r2, _, K, _ = ctx.invade(img_d, d, inlet=w.inlet)

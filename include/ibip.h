@@ -385,7 +385,10 @@ IBIP_API int ibip_profile_read(ibip_ctx *ctx, int cls, double *h_ms, int64_t *h_
 
 /* Counters of the context's last ibip_invade / ibip_invade_ex call, for
  * tracing (cycles are SM clock cycles counted by thread 0 of the invasion
- * CTA).  Writes up to n (at most 48) of:
+ * CTA).  The cycle entries are measured only by calls made while a trace is
+ * set (ibip_invade_trace), which run a separate, timed build of the loop;
+ * otherwise they read 0 (the clock reads would cost the loop about a tenth
+ * of its time).  Writes up to n (at most 48) of:
  *   0 steps, 1 status, 2 iterations of the main loop,
  *   3-5 cycles selecting, bounding (candidate shell) and committing,
  *   6 batch items taken, 7 batch items committed, 8 stale summary bits
@@ -412,10 +415,12 @@ IBIP_API int ibip_invade_stats(const ibip_ctx *ctx, int64_t *h_stats, int n);
 /* Per-batch timing trace of later ibip_invade / ibip_invade_ex calls on
  * this context (diagnostics; the paper has no counterpart: it measures the
  * per-step cost of the sequential invasion of Section 2.1 on this design).
- * d_trace: device array of capacity_records records of four int32 each,
+ * d_trace: device array of capacity_records records of eight int32 each,
  * 16-byte aligned, owned by the caller and kept alive while tracing is on:
  * {first step of the batch (0-based), steps it committed, SM cycles from
- * its selection to the end of its commit, loop (0 main, 1 single-voxel)}.
+ * its selection to the end of its commit, loop (0 main, 1 single-voxel),
+ * items taken, ball rows stamped (steps in the single-voxel loop), shell
+ * rows scanned, shell candidates listed (both 0 in the single-voxel loop)}.
  * Records past the capacity are counted (stats entry 36), not written.
  * d_trace == null turns tracing off.  Returns IBIP_ERR_ARG for a negative
  * capacity or a misaligned array.  Batched calls are never traced. */

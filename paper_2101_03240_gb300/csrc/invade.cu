@@ -338,7 +338,7 @@ struct Inv {
     const uint8_t *mask;   // inlet voxels (nonzero), or null: the inlet face
     int resume;            // seq holds an earlier run's steps 1..k0 on entry
     int64_t k0;            // steps already taken (resume), else 0
-    int4 *trace;           // per-batch records {first step, steps, SM cycles, loop}, or null
+    int4 *trace;           // per-batch records (two int4 each, see trace_batch), or null
     int64_t trace_cap;     // records that fit in trace
 };
 
@@ -628,7 +628,7 @@ __device__ __forceinline__ unsigned nb6_candidates(const Inv &a, const Nb6 &n)
 // leading set bits, each lane extracting up to two of them.
 template <bool L1SMEM>
 __device__ int gather_top(const Inv &a, u64 *s1, u64 *s2, u64 *s3, int *cur1, int lane, int mt, int *rank_out,
-                          long long &n_stale)
+                          long long *n_stale)
 {
     for (;;) {
         // first two non-empty level-1 words: scan 32 words from the cursor
@@ -687,7 +687,7 @@ __device__ int gather_top(const Inv &a, u64 *s1, u64 *s2, u64 *s3, int *cur1, in
             atomicAnd(p, ~(1u << (c0 & 31)));
         }
         const unsigned stale = __ballot_sync(0xffffffffu, st);
-        if (lane == 0) n_stale += __popc(stale);
+        if (lane == 0 && stale) *n_stale += __popc(stale);
         const int cnt = __popcll(w0);
         int inc = cnt;
 #pragma unroll
@@ -728,7 +728,7 @@ __device__ int gather_top(const Inv &a, u64 *s1, u64 *s2, u64 *s3, int *cur1, in
 // clamped bounding square and row count (in upre[j + 1]).  Returns m.
 template <bool L1SMEM, bool FULL>
 __device__ int gather_items(const Inv &a, Batch &B, u64 *s1, u64 *s2, u64 *s3, int lane, int mt,
-                            const FastDiv &fd_nyz, const FastDiv &fd_nz, long long &n_stale)
+                            const FastDiv &fd_nyz, const FastDiv &fd_nz, long long *n_stale)
 {
     const int m = gather_top<L1SMEM>(a, s1, s2, s3, &B.cur1, lane, mt, B.rank, n_stale);
     const uint32_t nyz = (uint32_t)a.ny * (uint32_t)a.nz;
@@ -783,6 +783,15 @@ __device__ __forceinline__ void flag_rank(u64 *s1, u64 *s2, u64 *s3, int *cur1, 
 
 __device__ __forceinline__ void bar_sync_64() { asm volatile("bar.sync 1, 64;" ::: "memory"); }
 
+// SM clock for the phase timers: read only in the profiling kernel (the
+// reads are scheduling barriers that cost the loop about a tenth of its time)
+template <bool P>
+__device__ __forceinline__ long long tclk()
+{
+    if constexpr (P) return clock64();
+    else return 0;
+}
+
 __device__ __forceinline__ unsigned long long global_ns()
 {
     unsigned long long t;
@@ -790,13 +799,29 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
+// Diagnostic counters of the invasion, kept by thread 0 in shared memory
+// (slot = index in the kernel's output, see ibip_invade_stats).
+enum Diag {
+    D_ITERS = 2, D_SEL = 3, D_BOUND = 4, D_COMMIT = 5, D_ITEMS = 6, D_COMMITTED = 7, D_STALE = 8, D_ROWS = 9,
+    D_SMALL_CYC = 10, D_SMALL_N = 11, D_GATHER = 12, D_PAIRS = 14, D_TAIL = 15, D_SMALL_SEL = 16,
+    D_SMALL_BOUND = 17, D_SMALL_COMMIT = 18, D_TINY_IT = 19, D_TINY_STEPS = 20, D_TINY_CYC = 21, D_S3_CONT = 22,
+    D_S3_PREFIX = 23, D_B1 = 24, D_B2 = 25, D_M1 = 26, D_M2 = 27, D_TG = 28, D_TB = 29, D_TC = 33, D_TRACE = 36,
+    D_SPAN_CYC = 37, D_SPAN_NS = 38, D_SHELL_UNITS = 39, D_LISTED = 40, D_REMOVED = 41
+};
+
 // One timing record per batch (thread 0): first step (0-based), steps
-// committed, SM cycles from batch selection to the end of its commit, and
-// the loop that ran it (0 main, 1 single-voxel).  Counted past the capacity.
-__device__ __forceinline__ void trace_batch(const Inv &a, long long &ntr, int64_t k, int n, long long cyc, int loop)
+// committed, SM cycles from batch selection to the end of its commit, the
+// loop that ran it (0 main, 1 single-voxel), then items taken, ball rows
+// stamped, shell rows scanned and shell candidates listed (the last two 0
+// in the single-voxel loop).  Counted past the capacity.
+__device__ __forceinline__ void trace_batch(const Inv &a, long long &ntr, int64_t k, int n, long long cyc, int loop,
+                                            int items, int rows, int shell, int listed)
 {
     if (!a.trace) return;
-    if (ntr < a.trace_cap) a.trace[ntr] = make_int4((int)k, n, (int)min(cyc, (long long)INT_MAX), loop);
+    if (ntr < a.trace_cap) {
+        a.trace[2 * ntr] = make_int4((int)k, n, (int)min(cyc, (long long)INT_MAX), loop);
+        a.trace[2 * ntr + 1] = make_int4(items, rows, shell, listed);
+    }
     ntr++;
 }
 
@@ -810,18 +835,17 @@ __device__ __forceinline__ void trace_batch(const Inv &a, long long &ntr, int64_
 constexpr int kNewCap = 6 * kM;   // candidates one single-voxel batch can queue
 constexpr int kMinMerge = 16;     // smaller merged batches are refilled from the bitmap
 
-template <bool L1SMEM>
+template <bool L1SMEM, bool PROF>
 __device__ void tiny_loop(const Inv &a, Batch &B, u64 *s1, u64 *s2, u64 *s3, const int tid, int64_t &k,
-                          const FastDiv &fd_nyz, const FastDiv &fd_nz, long long &n_stale, long long &n_it,
-                          long long &n_steps, long long &c_tg, long long &c_tb, long long &c_tc, int *sNr,
-                          int *sNv, int *tR, int *tI, long long &ntr)
+                          const FastDiv &fd_nyz, const FastDiv &fd_nz, long long *sD, int *sNr, int *sNv, int *tR,
+                          int *tI)
 {
     const int lane = tid & 31;
     const int first1 = (int)a.out[kFirst1Slot];   // ranks below it hold dt2 > 1
     if (tid == 0) { B.tmerge = 0; B.nN = 0; B.novf = 0; }
     bar_sync_64();
     for (;;) {
-        const long long ta = clock64();
+        const long long ta = tclk<PROF>();
         // Next batch.  A committed single-voxel ball stamps only its own
         // centre, so the frontier changed only by the committed items and
         // the candidates that commit queued (ranks known): every candidate
@@ -893,7 +917,7 @@ __device__ void tiny_loop(const Inv &a, Batch &B, u64 *s1, u64 *s2, u64 *s3, con
             }
         }
         if (gather && tid < 32) {
-            const int m = gather_items<L1SMEM, false>(a, B, s1, s2, s3, lane, kM, fd_nyz, fd_nz, n_stale);
+            const int m = gather_items<L1SMEM, false>(a, B, s1, s2, s3, lane, kM, fd_nyz, fd_nz, sD + D_STALE);
             if (lane == 0) {
                 int stop = 0, mcap = m;
                 const int64_t remain = a.max_steps - k;
@@ -910,8 +934,8 @@ __device__ void tiny_loop(const Inv &a, Batch &B, u64 *s1, u64 *s2, u64 *s3, con
         }
         if (tid == 0) { B.nN = 0; B.novf = 0; }
         bar_sync_64();
-        const long long tb = clock64();
-        if (tid == 0) c_tg += tb - ta;
+        const long long tb = tclk<PROF>();
+        if (PROF && tid == 0) sD[D_TG] += tb - ta;
         const int st = B.tstop;
         if (st) {
             if (st != 4 && tid == 0) B.stop = st;
@@ -936,8 +960,8 @@ __device__ void tiny_loop(const Inv &a, Batch &B, u64 *s1, u64 *s2, u64 *s3, con
         jl = __reduce_min_sync(0xffffffffu, jl);
         if (lane == 0 && jl < INT_MAX) atomicMin(&B.J, jl);
         bar_sync_64();
-        const long long tc = clock64();
-        if (tid == 0) c_tb += tc - tb;
+        const long long tc = tclk<PROF>();
+        if (PROF && tid == 0) sD[D_TB] += tc - tb;
         const int J = B.J;
         if (j < J) {
             const int x = B.x[j], y = B.y[j], z = B.z[j];
@@ -972,19 +996,21 @@ __device__ void tiny_loop(const Inv &a, Batch &B, u64 *s1, u64 *s2, u64 *s3, con
             }
         }
         k += J;
-        if (tid == 0) { n_it++; n_steps += J; }
+        if (tid == 0) { sD[D_TINY_IT]++; sD[D_TINY_STEPS] += J; }
         bar_sync_64();
         if (tid == 0) {
             B.tmerge = !B.novf;
-            const long long te = clock64();
-            c_tc += te - tc;
-            trace_batch(a, ntr, k - J, J, te - ta, 1);
+            if (PROF) {
+                const long long te = tclk<PROF>();
+                sD[D_TC] += te - tc;
+                trace_batch(a, sD[D_TRACE], k - J, J, te - ta, 1, m, J, 0, 0);
+            }
         }
         bar_sync_64();
     }
 }
 
-template <bool L1SMEM>
+template <bool L1SMEM, bool PROF>
 __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz, const FastDiv &fd_nz, int *gC,
                                             int *gD)
 {
@@ -1016,18 +1042,13 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
 
     const long long span_c0 = clock64();
     const unsigned long long span_t0 = global_ns();
-    long long ntr = 0;   // timing records (thread 0)
-    long long n_shell_units = 0, n_listed = 0, n_removed = 0;   // work of the main loop's batches
-    int64_t k = a.k0, iters = 0;
-    // diagnostics kept by thread 0: cycles per phase, items, stale summary bits
-    long long c_sel = 0, c_shell = 0, c_commit = 0, n_items = 0, n_commit_items = 0, n_stale = 0, n_units = 0;
-    long long c_small = 0, n_small = 0, n_tiny = 0, n_tiny_steps = 0, c_tiny = 0;
-    long long c_sub[6] = {0, 0, 0, 0, 0, 0};   // select sub-phases (all batches)
-    // bound stages 1-2, commit stage 1 and the rest, the single-voxel loop's phases
-    long long c_b1 = 0, c_b2 = 0, c_m1 = 0, c_m2 = 0, c_tg = 0, c_tb = 0, c_tc = 0;
-    long long c_small_ph[3] = {0, 0, 0};       // select / bound / commit cycles of small batches
+    int64_t k = a.k0;
+    // diagnostics (thread 0): cycles per phase, items, stale summary bits, ...
+    __shared__ long long sD[kNOut];
+    if (tid == 0)
+        for (int q = 0; q < kNOut; q++) sD[q] = 0;
     for (;;) {
-        long long t0 = clock64();
+        long long t0 = tclk<PROF>();
         // ------------------------------------------------------ select batch
         // The best candidates are the first set bits of the rank bitmap.  Lane
         // 0 walks the summary levels to the first flagged level-1 word; the
@@ -1036,25 +1057,25 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
         // ones, and takes the leading set bits as the batch.
         // S1 (warp 0): the batch items and their data.
         if (tid < 32) {
-            const int m = gather_items<L1SMEM, true>(a, B, s1, s2, s3, lane, B.mtarget, fd_nyz, fd_nz, n_stale);
+            const int m = gather_items<L1SMEM, true>(a, B, s1, s2, s3, lane, B.mtarget, fd_nyz, fd_nz, sD + D_STALE);
             const bool bg0 = lane < m && B.r2[lane] > 1, bg1 = lane + 32 < m && B.r2[lane + 32] > 1;
             const u64 big = (u64)__ballot_sync(0xffffffffu, bg0) | ((u64)__ballot_sync(0xffffffffu, bg1) << 32);
             if (lane == 0) {
                 B.m = m;
                 B.big = big;
                 B.stop = m == 0 ? 1 : 0;
-                c_sub[0] += clock64() - t0;
+                if (PROF) sD[D_GATHER] += tclk<PROF>() - t0;
             }
         }
         __syncthreads();
         if (B.stop) break;
         if (B.r2[0] == 1) {
-            long long tt = clock64();
-            if (tid < 64) tiny_loop<L1SMEM>(a, B, s1, s2, s3, tid, k, fd_nyz, fd_nz, n_stale, n_tiny, n_tiny_steps, c_tg, c_tb, c_tc, sNr, sNv, tR, tI, ntr);
+            long long tt = tclk<PROF>();
+            if (tid < 64) tiny_loop<L1SMEM, PROF>(a, B, s1, s2, s3, tid, k, fd_nyz, fd_nz, sD, sNr, sNv, tR, tI);
             if (tid == 0) B.kk = k;
             __syncthreads();
             k = B.kk;
-            if (tid == 0) c_tiny += clock64() - tt;
+            if (PROF && tid == 0) sD[D_TINY_CYC] += tclk<PROF>() - tt;
             if (B.stop) break;
             continue;
         }
@@ -1063,7 +1084,7 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
         // single-voxel balls never meet).  cont: j lies in the ball of an
         // earlier b; ovl: the ball boxes of j and b, grown by one voxel, meet.
         {
-            const long long tb = clock64();
+            const long long tb = tclk<PROF>();
             const int m = B.m;
             const u64 big = B.big;
             const int npair = __popcll(big) * m;
@@ -1081,12 +1102,12 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
                 }
             }
             __syncthreads();
-            if (tid == 0) c_sub[2] += clock64() - tb;
+            if (PROF && tid == 0) sD[D_PAIRS] += tclk<PROF>() - tb;
         }
         // S3 (warp 0): skip covered items, apply the step limit and the row
         // budget, number the steps, prefix-sum the row units.
         if (tid < 32) {
-            const long long tc = clock64();
+            const long long tc = tclk<PROF>();
             const int m = B.m;
             u64 cont[2];
 #pragma unroll
@@ -1114,8 +1135,8 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
                 decided |= (u64)__ballot_sync(0xffffffffu, rd[0]) | ((u64)__ballot_sync(0xffffffffu, rd[1]) << 32);
                 keep |= (u64)__ballot_sync(0xffffffffu, kp[0]) | ((u64)__ballot_sync(0xffffffffu, kp[1]) << 32);
             }
-            const long long tc2 = clock64();
-            if (tid == 0) c_sub[4] += tc2 - tc;
+            const long long tc2 = tclk<PROF>();
+            if (PROF && tid == 0) sD[D_S3_CONT] += tc2 - tc;
             // step limit: items past the (max_steps - k)-th kept one are dropped
             int mcap = m;
             int64_t remain = a.max_steps - k;
@@ -1148,7 +1169,7 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
                 cut = ((ob0 >> l) & 1) ? 2 * l : 2 * l + 1;
             }
             mcap = min(mcap, cut);
-            if (tid == 0) c_sub[5] += clock64() - tc2;
+            if (PROF && tid == 0) sD[D_S3_PREFIX] += tclk<PROF>() - tc2;
             // prefix through item mcap - 1, carried by every later item
             const bool odd = (mcap - 1) & 1;
             int last = __shfl_sync(0xffffffffu, odd ? inc : ex + r0, max(mcap - 1, 0) >> 1);
@@ -1174,12 +1195,12 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
                 B.keep = keep;
                 B.stop = mcap == 0 ? 2 : 0;
                 B.nA = 0; B.nC = 0; B.nD = 0; B.ovf = 0;
-                c_sub[3] += clock64() - tc;
+                if (PROF) sD[D_TAIL] += tclk<PROF>() - tc;
             }
         }
         __syncthreads();
-        long long t1 = clock64();
-        c_sel += t1 - t0;
+        long long t1 = tclk<PROF>();
+        if (PROF && tid == 0) sD[D_SEL] += t1 - t0;
         if (B.stop) break;
         if (k > a.npore) {   // every step invades its own centre: cannot happen
             if (tid == 0) B.stop = 3;
@@ -1202,10 +1223,13 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
                     // single-voxel ball: its shell is its six neighbours
                     Nb6 nb;
                     nb6(a, B.x[i], B.y[i], B.z[i], B.idx[i], nb);
-                    unsigned c = nb6_candidates(a, nb);
+                    const unsigned c = nb6_candidates(a, nb);
                     if (!c) return true;
-                    for (int slot = atomicAdd(&B.nA, __popc(c)); c; c &= c - 1, slot++) {
-                        const int q = __ffs(c) - 1;
+                    // static indices keep nb in registers
+                    int slot = atomicAdd(&B.nA, __popc(c));
+#pragma unroll
+                    for (int q = 0; q < 6; q++) {
+                        if (!((c >> q) & 1)) continue;
                         if (slot < kList) {
                             sLA[slot] = nb.v[q];
                             sLAi[slot] = (unsigned char)i;
@@ -1214,6 +1238,7 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
                             const int ru = __ldg(a.rank + nb.v[q]);
                             atomicMin(&B.J, max(i + 1, lower_rank(B, m, ru)));
                         }
+                        slot++;
                     }
                     return true;
                 }
@@ -1239,7 +1264,7 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
                 return true;
             });
             __syncthreads();
-            if (tid == 0) c_b1 += clock64() - t1;
+            if (PROF && tid == 0) sD[D_B1] += tclk<PROF>() - t1;
             // entries of items at or past J are never committed; the ranks
             // of up to four entries per thread are loaded together, and each
             // warp lowers J once
@@ -1264,8 +1289,8 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
             if (lane == 0) atomicMin(&B.J, jl);
         }
         __syncthreads();
-        long long t2 = clock64();
-        c_shell += t2 - t1;
+        long long t2 = tclk<PROF>();
+        if (PROF && tid == 0) sD[D_BOUND] += t2 - t1;
         long long tm1 = t2;
 
         // --------------------------------------------------------- commit
@@ -1331,8 +1356,8 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
             }
         }
         __syncthreads();
-        tm1 = clock64();
-        if (tid == 0) c_m1 += tm1 - t2;
+        tm1 = tclk<PROF>();
+        if (PROF && tid == 0) sD[D_M1] += tm1 - t2;
         if (!B.ovf) {
             // Stage 2 from the candidate list of the bound pass (complete for
             // every committed item, ranks already loaded): a listed voxel
@@ -1446,68 +1471,52 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
         }
         const int nk = __popcll(B.keep & jmask);
         k += nk;
-        iters++;
-        n_items += m;
-        n_commit_items += J;
-        n_units += B.upre[J];
-        n_shell_units += B.dpre[mcap];
-        n_listed += B.nA;
-        n_removed += B.nC;
-        if (tid == 0) B.mtarget = min(kM, max(16, 2 * J + 8));
-        const bool small = B.upre[J] == __popcll(B.keep & jmask) && B.r2[0] == 1;
+        int tr_rows = 0, tr_shell = 0, tr_listed = 0, tr_removed = 0;
+        bool small = false;
+        if (tid == 0) {
+            tr_rows = B.upre[J]; tr_shell = B.dpre[mcap]; tr_listed = B.nA; tr_removed = B.nC;
+            small = tr_rows == nk && B.r2[0] == 1;
+            B.mtarget = min(kM, max(16, 2 * J + 8));
+        }
         __syncthreads();
-        long long t3 = clock64();
-        c_commit += t3 - t2;
-        c_m2 += t3 - tm1;
-        if (tid == 0) trace_batch(a, ntr, k - nk, nk, t3 - t0, 0);
-        if (small) {
-            c_small += t3 - t0;
-            n_small++;
-            c_small_ph[0] += t1 - t0;
-            c_small_ph[1] += t2 - t1;
-            c_small_ph[2] += t3 - t2;
+        const long long t3 = tclk<PROF>();
+        if (tid == 0) {
+            sD[D_ITERS]++;
+            sD[D_ITEMS] += m;
+            sD[D_COMMITTED] += J;
+            sD[D_ROWS] += tr_rows;
+            sD[D_SHELL_UNITS] += tr_shell;
+            sD[D_LISTED] += tr_listed;
+            sD[D_REMOVED] += tr_removed;
+            if (PROF) {
+                sD[D_COMMIT] += t3 - t2;
+                sD[D_M2] += t3 - tm1;
+                trace_batch(a, sD[D_TRACE], k - nk, nk, t3 - t0, 0, m, tr_rows, tr_shell, tr_listed);
+            }
+            if (small) {
+                sD[D_SMALL_CYC] += t3 - t0;
+                sD[D_SMALL_N]++;
+                sD[D_SMALL_SEL] += t1 - t0;
+                sD[D_SMALL_BOUND] += t2 - t1;
+                sD[D_SMALL_COMMIT] += t3 - t2;
+            }
         }
     }
     if (tid == 0) {
+        sD[D_SPAN_CYC] = clock64() - span_c0;
+        sD[D_SPAN_NS] = (long long)(global_ns() - span_t0);
+        sD[D_B2] = sD[D_BOUND] - sD[D_B1];
+        for (int q = 2; q < kNOut; q++)
+            if (q != kFirst1Slot) a.out[q] = sD[q];
         a.out[0] = k;
         a.out[1] = (B.stop == 2) ? IBIP_ERR_STEP_LIMIT : (B.stop == 3 ? IBIP_ERR_BOUNDS : IBIP_OK);
-        a.out[2] = iters;
-        a.out[3] = c_sel;
-        a.out[4] = c_shell;
-        a.out[5] = c_commit;
-        a.out[6] = n_items;
-        a.out[7] = n_commit_items;
-        a.out[8] = n_stale;
-        a.out[9] = n_units;
-        a.out[10] = c_small;
-        a.out[11] = n_small;
-        for (int q = 0; q < 4; q++) a.out[12 + q] = c_sub[q];
-        for (int q = 0; q < 3; q++) a.out[16 + q] = c_small_ph[q];
-        a.out[22] = c_sub[4];
-        a.out[23] = c_sub[5];
-        a.out[24] = c_b1;
-        a.out[25] = c_shell - c_b1;
-        a.out[26] = c_m1;
-        a.out[27] = c_m2;
-        a.out[28] = c_tg;
-        a.out[29] = c_tb;
-        a.out[33] = c_tc;
-        a.out[36] = ntr;
-        a.out[39] = n_shell_units;
-        a.out[40] = n_listed;
-        a.out[41] = n_removed;
-        a.out[37] = clock64() - span_c0;
-        a.out[38] = (int64_t)(global_ns() - span_t0);
-        a.out[19] = n_tiny;
-        a.out[20] = n_tiny_steps;
-        a.out[21] = c_tiny;
     }
 }
 
-template <bool L1SMEM>
+template <bool L1SMEM, bool PROF>
 __global__ void __launch_bounds__(kNT, 1) k_invade(Inv a, FastDiv fd_nyz, FastDiv fd_nz, int *gC, int *gD)
 {
-    invade_body<L1SMEM>(a, fd_nyz, fd_nz, gC, gD);
+    invade_body<L1SMEM, PROF>(a, fd_nyz, fd_nz, gC, gD);
 }
 
 // One image per CTA: many invasions in one launch (all with level 1 of the
@@ -1538,7 +1547,7 @@ __global__ void k_plane_init_b(const InvJob *__restrict__ jobs, int n)
 __global__ void __launch_bounds__(kNT, 1) k_invade_batch(const InvJob *__restrict__ jobs, IbipBatchDone *rec)
 {
     const InvJob j = jobs[blockIdx.x];
-    invade_body<true>(j.a, j.fd_nyz, j.fd_nz, j.gC, j.gD);
+    invade_body<true, false>(j.a, j.fd_nyz, j.fd_nz, j.gC, j.gD);
     if (!rec) return;
     __threadfence();
     __syncthreads();
@@ -1770,14 +1779,25 @@ int ibip_invade_run(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, i
     ibip_prof_end(ctx, IBIP_K_RANK);
     const FastDiv fd_nyz = make_fastdiv((uint32_t)d.ny * (uint32_t)d.nz), fd_nz = make_fastdiv((uint32_t)d.nz);
     const bool l1smem = a.NL1 <= kSmemL1Max;
+    const bool prof = a.trace != nullptr;   // phase timers and the trace: a separate kernel
     const size_t dyn = invade_dyn_smem(a, l1smem);
     ibip_prof_begin(ctx, IBIP_K_INVADE);
     if (l1smem) {
-        allow_max_dyn_smem((const void *)k_invade<true>);
-        k_invade<true><<<1, kNT, dyn, s>>>(a, fd_nyz, fd_nz, mem.gl, mem.gl + npore);
+        if (prof) {
+            allow_max_dyn_smem((const void *)k_invade<true, true>);
+            k_invade<true, true><<<1, kNT, dyn, s>>>(a, fd_nyz, fd_nz, mem.gl, mem.gl + npore);
+        } else {
+            allow_max_dyn_smem((const void *)k_invade<true, false>);
+            k_invade<true, false><<<1, kNT, dyn, s>>>(a, fd_nyz, fd_nz, mem.gl, mem.gl + npore);
+        }
     } else {
-        allow_max_dyn_smem((const void *)k_invade<false>);
-        k_invade<false><<<1, kNT, dyn, s>>>(a, fd_nyz, fd_nz, mem.gl, mem.gl + npore);
+        if (prof) {
+            allow_max_dyn_smem((const void *)k_invade<false, true>);
+            k_invade<false, true><<<1, kNT, dyn, s>>>(a, fd_nyz, fd_nz, mem.gl, mem.gl + npore);
+        } else {
+            allow_max_dyn_smem((const void *)k_invade<false, false>);
+            k_invade<false, false><<<1, kNT, dyn, s>>>(a, fd_nyz, fd_nz, mem.gl, mem.gl + npore);
+        }
     }
     IBIP_LAUNCH(ctx);
     ibip_prof_end(ctx, IBIP_K_INVADE);

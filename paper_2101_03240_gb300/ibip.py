@@ -222,13 +222,14 @@ class Context:
         return dict(zip(keys, [int(x) for x in a]))
 
     def invade_trace(self, buf):
-        """Record one timing row per batch of later invade calls into `buf`
-        (CUDA int32 tensor of shape (n, 4): first step, steps, SM cycles,
-        loop), or stop recording (None).  See ibip_invade_trace."""
+        """Record one row per batch of later invade calls into `buf` (CUDA
+        int32 tensor of shape (n, 8): first step, steps, SM cycles, loop,
+        items, rows stamped, shell rows, shell candidates), or stop
+        recording (None).  See ibip_invade_trace."""
         if buf is None:
             st = _lib().ibip_invade_trace(self._h, None, 0)
         else:
-            assert buf.is_cuda and buf.dtype == torch.int32 and buf.dim() == 2 and buf.shape[1] == 4
+            assert buf.is_cuda and buf.dtype == torch.int32 and buf.dim() == 2 and buf.shape[1] == 8
             assert buf.is_contiguous()
             st = _lib().ibip_invade_trace(self._h, _ptr(buf), buf.shape[0])
         if st != OK:

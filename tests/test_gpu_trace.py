@@ -34,7 +34,7 @@ def test_trace_tiles_the_steps_and_changes_nothing(ctx, kind):
     d = ctx.edt(d_img)
     seq0, r20, c0, K0, _ = ctx.invade(d_img, d)
     seq0, r20, c0 = seq0.clone(), r20.clone(), c0.clone()
-    buf = torch.full((int(img.astype(bool).sum()) + 1, 4), -7, dtype=torch.int32, device="cuda")
+    buf = torch.full((int(img.astype(bool).sum()) + 1, 8), -7, dtype=torch.int32, device="cuda")
     ctx.invade_trace(buf)
     try:
         seq1, r21, c1, K1, _ = ctx.invade(d_img, d)
@@ -46,7 +46,12 @@ def test_trace_tiles_the_steps_and_changes_nothing(ctx, kind):
     assert 0 < n <= buf.shape[0]
     rec = buf.cpu().numpy().astype(np.int64)
     assert np.all(rec[n:] == -7)                       # nothing written past the records
-    rec = rec[:n]
+    rec, work = rec[:n, :4], rec[:n, 4:]
+    # items taken cover the steps; rows and shells are counted in the main loop only
+    assert np.all(work[:, 0] >= rec[:, 1]) and np.all(work[:, 0] <= 64)
+    main = rec[:, 3] == 0
+    assert np.all(work[main, 1] >= rec[main, 1]) and np.all(work[~main, 1] == rec[~main, 1])
+    assert np.all(work[main, 2] >= 1) and np.all(work[~main, 2:] == 0)
     assert rec[0, 0] == 0 and np.all(rec[1:, 0] == np.cumsum(rec[:, 1])[:-1])
     assert rec[:, 1].sum() == K1 and np.all(rec[:, 1] >= 1) and np.all(rec[:, 2] > 0)
     assert set(np.unique(rec[:, 3])) <= {0, 1}
@@ -71,7 +76,7 @@ def test_trace_capacity_counts_past_the_end(ctx):
     rng = np.random.default_rng(5)
     img = S.blobs((32, 32, 32), 2.0, 0.6, rng)
     d_img = torch.from_numpy(img).cuda()
-    big = torch.full((64, 4), -7, dtype=torch.int32, device="cuda")
+    big = torch.full((64, 8), -7, dtype=torch.int32, device="cuda")
     ctx.invade_trace(big[:3])   # capacity 3 inside a larger allocation
     try:
         _, _, _, K, _ = ctx.invade(d_img)
@@ -86,7 +91,7 @@ def test_trace_capacity_counts_past_the_end(ctx):
 def test_trace_rejects_bad_arguments(ctx):
     from paper_2101_03240_gb300 import ibip
     L = ibip._lib()
-    t = torch.zeros(16, dtype=torch.int32, device="cuda")
+    t = torch.zeros(32, dtype=torch.int32, device="cuda")
     assert L.ibip_invade_trace(None, C.c_void_p(t.data_ptr()), 2) == ibip.ERR_ARG
     assert L.ibip_invade_trace(ctx._h, C.c_void_p(t.data_ptr() + 4), 2) == ibip.ERR_ARG   # misaligned
     assert L.ibip_invade_trace(ctx._h, C.c_void_p(t.data_ptr()), -1) == ibip.ERR_ARG
