@@ -806,7 +806,7 @@ enum Diag {
     D_SMALL_CYC = 10, D_SMALL_N = 11, D_GATHER = 12, D_PAIRS = 14, D_TAIL = 15, D_SMALL_SEL = 16,
     D_SMALL_BOUND = 17, D_SMALL_COMMIT = 18, D_TINY_IT = 19, D_TINY_STEPS = 20, D_TINY_CYC = 21, D_S3_CONT = 22,
     D_S3_PREFIX = 23, D_B1 = 24, D_B2 = 25, D_M1 = 26, D_M2 = 27, D_TG = 28, D_TB = 29, D_TC = 33, D_TRACE = 36,
-    D_SPAN_CYC = 37, D_SPAN_NS = 38, D_SHELL_UNITS = 39, D_LISTED = 40, D_REMOVED = 41
+    D_SPAN_CYC = 37, D_SPAN_NS = 38, D_SHELL_UNITS = 39, D_LISTED = 40, D_REMOVED = 41, D_SINGLE = 42
 };
 
 // One timing record per batch (thread 0): first step (0-based), steps
@@ -823,6 +823,44 @@ __device__ __forceinline__ void trace_batch(const Inv &a, long long &ntr, int64_
         a.trace[2 * ntr + 1] = make_int4(items, rows, shell, listed);
     }
     ntr++;
+}
+
+// The lone item of a batch (ball larger than its centre), committed as step
+// `label`: per row of its one-voxel-dilated square, the voxels of its run
+// that are still uninvaded are stamped (those that were queued leave the
+// rank bitmap) and the uninvaded, never-queued voxels of the shell part of
+// the row are queued.  Rows are disjoint, so their words are too; nothing
+// else runs meanwhile.
+__device__ __forceinline__ void commit_single(const Inv &a, const Batch &B, u64 *s1, u64 *s2, u64 *s3, int tid,
+                                              int32_t label)
+{
+    for_units(B.dpre, 1, B.dpre[1], B.dx0, B.dy0, B.dwy, tid, [&](int, int, int x, int y) -> bool {
+        int za, zb, ra, rb;
+        if (!shell_row(a, B, 0, x, y, za, zb, ra, rb)) return true;
+        const int r0 = max(ra, 0), r1 = min(rb, a.nz - 1);   // the ball's run (empty when r0 > r1)
+        const int64_t row = (int64_t)x * a.ny + y;
+        const int64_t vb = row * a.nz;
+        for (int w = za >> 5; w <= (zb >> 5); w++) {
+            const int64_t rw = row * a.NW + w;
+            const uint32_t av = ldcg32(a.avail + rw), ad = ldcg32(a.added + rw);
+            const uint32_t ballm = r0 <= r1 ? span_mask(w, r0, r1) : 0u;
+            const uint32_t newly = av & ballm;
+            const uint32_t cand = av & ~ad & span_mask(w, za, zb) & ~ballm;
+            if (newly) atomicAnd(a.avail + rw, ~newly);
+            if (cand) atomicOr(a.added + rw, cand);
+            for (uint32_t n2 = newly; n2; n2 &= n2 - 1) a.seq[vb + w * 32 + __ffs(n2) - 1] = label;
+            for (uint32_t g = newly & ad; g; g &= g - 1) {
+                const int r = __ldg(a.rank + vb + w * 32 + __ffs(g) - 1);
+                atomicAnd(a.fb0 + (r >> 6), ~(1ull << (r & 63)));
+            }
+            for (uint32_t c = cand; c; c &= c - 1) {
+                const int r = __ldg(a.rank + vb + w * 32 + __ffs(c) - 1);
+                atomicOr(a.fb0 + (r >> 6), 1ull << (r & 63));
+                flag_rank(s1, s2, s3, (int *)&B.cur1, r);
+            }
+        }
+        return true;
+    });
 }
 
 // Single-voxel regime.  Once the best candidate has dt2 == 1 every candidate
@@ -1035,6 +1073,8 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
     if (tid == 0) {
         B.mtarget = kM;
         B.cur1 = 0;
+        B.upre[0] = 0;
+        B.dpre[0] = 0;
         B.isq.t = isq_t;
         B.isq.n = a.isq_n;
     }
@@ -1077,6 +1117,43 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
             k = B.kk;
             if (PROF && tid == 0) sD[D_TINY_CYC] += tclk<PROF>() - tt;
             if (B.stop) break;
+            continue;
+        }
+        if (B.m == 1) {
+            // A lone item is committed whatever its shell holds (the cut is
+            // never below one), so one pass over the rows of its dilated
+            // square stamps its ball and queues its shell: no pairwise
+            // tests, no bound, no lists.
+            const long long tf = tclk<PROF>();
+            if (a.max_steps - k < 1 || k > a.npore) {   // the same for every thread
+                if (tid == 0) B.stop = a.max_steps - k < 1 ? 2 : 3;
+                break;
+            }
+            commit_single(a, B, s1, s2, s3, tid, (int32_t)(k + 1));
+            if (tid == 0) {
+                if (k < a.cap) {
+                    a.step_r2[k] = B.r2[0];
+                    if (a.step_centre) a.step_centre[k] = B.idx[0];
+                }
+                B.mtarget = 16;
+            }
+            const int rows1 = B.upre[1], shell1 = B.dpre[1];
+            __syncthreads();
+            k += 1;
+            if (tid == 0) {
+                sD[D_ITERS]++;
+                sD[D_ITEMS] += 1;
+                sD[D_COMMITTED] += 1;
+                sD[D_ROWS] += rows1;
+                sD[D_SHELL_UNITS] += shell1;
+                sD[D_SINGLE]++;
+                if (PROF) {
+                    const long long te = tclk<PROF>();
+                    sD[D_SEL] += tf - t0;
+                    sD[D_COMMIT] += te - tf;
+                    trace_batch(a, sD[D_TRACE], k - 1, 1, te - t0, 0, 1, rows1, shell1, 0);
+                }
+            }
             continue;
         }
         // S2 (all threads): pairwise tests between every item j and every item
