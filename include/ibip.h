@@ -410,7 +410,8 @@ IBIP_API int ibip_profile_read(ibip_ctx *ctx, int cls, double *h_ms, int64_t *h_
  *   nanoseconds of the global timer (their ratio is the SM clock),
  *   39-41 shell rows, listed shell candidates and removed candidates,
  *   summed over the main loop's batches, 42 batches of one item committed
- *   by the single-pass path. */
+ *   by the single-pass path, 43-44 batches of the single-voxel loop formed
+ *   by merging (no bitmap gather) and their selection cycles. */
 IBIP_API int ibip_invade_stats(const ibip_ctx *ctx, int64_t *h_stats, int n);
 
 /* Per-batch timing trace of later ibip_invade / ibip_invade_ex calls on

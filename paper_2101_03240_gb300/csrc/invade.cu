@@ -440,6 +440,7 @@ struct Batch {
     u64 keep;
     Isq isq;
     u64 big;
+    int bigl[kM];      // the items of `big`, in order
     uint32_t cont32[kM][2], ovl32[kM][2];
     int m, mcap, J, stop, mtarget, tstop;
     int cur1;          // no level-1 summary word below this index is set
@@ -806,7 +807,8 @@ enum Diag {
     D_SMALL_CYC = 10, D_SMALL_N = 11, D_GATHER = 12, D_PAIRS = 14, D_TAIL = 15, D_SMALL_SEL = 16,
     D_SMALL_BOUND = 17, D_SMALL_COMMIT = 18, D_TINY_IT = 19, D_TINY_STEPS = 20, D_TINY_CYC = 21, D_S3_CONT = 22,
     D_S3_PREFIX = 23, D_B1 = 24, D_B2 = 25, D_M1 = 26, D_M2 = 27, D_TG = 28, D_TB = 29, D_TC = 33, D_TRACE = 36,
-    D_SPAN_CYC = 37, D_SPAN_NS = 38, D_SHELL_UNITS = 39, D_LISTED = 40, D_REMOVED = 41, D_SINGLE = 42
+    D_SPAN_CYC = 37, D_SPAN_NS = 38, D_SHELL_UNITS = 39, D_LISTED = 40, D_REMOVED = 41, D_SINGLE = 42,
+    D_TMERGE = 43, D_TMERGE_CYC = 44
 };
 
 // One timing record per batch (thread 0): first step (0-based), steps
@@ -973,6 +975,10 @@ __device__ void tiny_loop(const Inv &a, Batch &B, u64 *s1, u64 *s2, u64 *s3, con
         if (tid == 0) { B.nN = 0; B.novf = 0; }
         bar_sync_64();
         const long long tb = tclk<PROF>();
+        if (tid == 0 && !gather) {
+            sD[D_TMERGE]++;
+            if (PROF) sD[D_TMERGE_CYC] += tb - ta;
+        }
         if (PROF && tid == 0) sD[D_TG] += tb - ta;
         const int st = B.tstop;
         if (st) {
@@ -1099,7 +1105,11 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
         if (tid < 32) {
             const int m = gather_items<L1SMEM, true>(a, B, s1, s2, s3, lane, B.mtarget, fd_nyz, fd_nz, sD + D_STALE);
             const bool bg0 = lane < m && B.r2[lane] > 1, bg1 = lane + 32 < m && B.r2[lane + 32] > 1;
-            const u64 big = (u64)__ballot_sync(0xffffffffu, bg0) | ((u64)__ballot_sync(0xffffffffu, bg1) << 32);
+            const unsigned b0 = __ballot_sync(0xffffffffu, bg0), b1 = __ballot_sync(0xffffffffu, bg1);
+            const u64 big = (u64)b0 | ((u64)b1 << 32);
+            const unsigned below = (1u << lane) - 1;
+            if (bg0) B.bigl[__popc(b0 & below)] = lane;
+            if (bg1) B.bigl[__popc(b0) + __popc(b1 & below)] = lane + 32;
             if (lane == 0) {
                 B.m = m;
                 B.big = big;
@@ -1164,10 +1174,13 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
             const long long tb = tclk<PROF>();
             const int m = B.m;
             const u64 big = B.big;
-            const int npair = __popcll(big) * m;
+            // pair p: big item bigl[p >> sh] against item p & (2^sh - 1)
+            const int sh = m <= 32 ? 5 : 6;
+            const int npair = __popcll(big) << sh;
             for (int p = tid; p < npair; p += kNT) {
-                const int bi = p / m, j = p - bi * m;
-                const int b = nth_bit(big, bi);
+                const int j = p & ((1 << sh) - 1);
+                if (j >= m) continue;
+                const int b = B.bigl[p >> sh];
                 if (j == b) continue;
                 const int dx = B.x[j] - B.x[b], dy = B.y[j] - B.y[b], dz = B.z[j] - B.z[b];
                 if (b < j && (int64_t)dx * dx + (int64_t)dy * dy + (int64_t)dz * dz < (int64_t)B.r2[b])
@@ -1182,8 +1195,64 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
             if (PROF && tid == 0) sD[D_PAIRS] += tclk<PROF>() - tb;
         }
         // S3 (warp 0): skip covered items, apply the step limit and the row
-        // budget, number the steps, prefix-sum the row units.
-        if (tid < 32) {
+        // budget, number the steps, prefix-sum the row units.  Up to 32
+        // items: one per lane, 32-bit masks.
+        if (tid < 32 && B.m <= 32) {
+            const long long tc = tclk<PROF>();
+            const int m = B.m;
+            const bool act = lane < m;
+            // containers are earlier items, so all below 32
+            const uint32_t cont = act ? B.cont32[lane][0] : 0u;
+            if (act) B.ovl[lane] = (u64)B.ovl32[lane][0];
+            const uint32_t valid = m == 32 ? 0xffffffffu : ((1u << m) - 1);
+            const uint32_t has = __ballot_sync(0xffffffffu, cont != 0u);
+            uint32_t keep = valid & ~has, decided = ~(has & valid);
+            // an item is kept iff no kept earlier item's ball contains it
+            while (~decided) {
+                const bool rd = !((decided >> lane) & 1) && (cont & ~decided) == 0u;
+                const bool kp = rd && (cont & keep) == 0u;
+                decided |= __ballot_sync(0xffffffffu, rd);
+                keep |= __ballot_sync(0xffffffffu, kp);
+            }
+            int mcap = m;
+            const int64_t remain = a.max_steps - k;
+            if ((int64_t)__popc(keep) > remain) {
+                uint32_t t = keep;
+                for (int64_t q = 0; q < remain; q++) t &= t - 1;
+                mcap = __ffs(t) - 1;
+            }
+            const bool kj = act && lane < mcap && ((keep >> lane) & 1);
+            const int r = kj ? B.upre[lane + 1] : 0, d = kj ? B.dpre[lane + 1] : 0;
+            int inc = r, dinc = d;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, inc, o);
+                const int td = __shfl_up_sync(0xffffffffu, dinc, o);
+                if (lane >= o) { inc = min(inc + t, 1 << 30); dinc = min(dinc + td, 1 << 30); }
+            }
+            // the batch stops before the shell-row budget is exceeded
+            const unsigned ob = __ballot_sync(0xffffffffu, lane > 0 && dinc > kRowBudget);
+            if (ob) mcap = min(mcap, __ffs(ob) - 1);
+            const int src = max(mcap - 1, 0);
+            int last = __shfl_sync(0xffffffffu, inc, src), dlast = __shfl_sync(0xffffffffu, dinc, src);
+            if (mcap == 0) { last = 0; dlast = 0; }
+            if (act) {
+                B.step[lane] = ((keep >> lane) & 1) ? __popc(keep & ((1u << lane) - 1)) : -1;
+                B.upre[lane + 1] = lane < mcap ? inc : last;
+                B.dpre[lane + 1] = lane < mcap ? dinc : dlast;
+            }
+            __syncwarp();
+            if (lane == 0) {
+                B.upre[0] = 0;
+                B.dpre[0] = 0;
+                B.mcap = mcap;
+                B.J = mcap;
+                B.keep = keep;
+                B.stop = mcap == 0 ? 2 : 0;
+                B.nA = 0; B.nC = 0; B.nD = 0; B.ovf = 0;
+                if (PROF) sD[D_TAIL] += tclk<PROF>() - tc;
+            }
+        } else if (tid < 32) {
             const long long tc = tclk<PROF>();
             const int m = B.m;
             u64 cont[2];
