@@ -411,7 +411,8 @@ IBIP_API int ibip_profile_read(ibip_ctx *ctx, int cls, double *h_ms, int64_t *h_
  *   39-41 shell rows, listed shell candidates and removed candidates,
  *   summed over the main loop's batches, 42 batches of one item committed
  *   by the single-pass path, 43-44 batches of the single-voxel loop formed
- *   by merging (no bitmap gather) and their selection cycles. */
+ *   by merging (no bitmap gather) and their selection cycles, 45-46
+ *   rounds of the bitmap gathers and gathers. */
 IBIP_API int ibip_invade_stats(const ibip_ctx *ctx, int64_t *h_stats, int n);
 
 /* Per-batch timing trace of later ibip_invade / ibip_invade_ex calls on

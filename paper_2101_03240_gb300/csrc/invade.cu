@@ -620,6 +620,17 @@ __device__ __forceinline__ unsigned nb6_candidates(const Inv &a, const Nb6 &n)
     return c;
 }
 
+// Diagnostic counters of the invasion, kept by thread 0 in shared memory
+// (slot = index in the kernel's output, see ibip_invade_stats).
+enum Diag {
+    D_ITERS = 2, D_SEL = 3, D_BOUND = 4, D_COMMIT = 5, D_ITEMS = 6, D_COMMITTED = 7, D_STALE = 8, D_ROWS = 9,
+    D_SMALL_CYC = 10, D_SMALL_N = 11, D_GATHER = 12, D_PAIRS = 14, D_TAIL = 15, D_SMALL_SEL = 16,
+    D_SMALL_BOUND = 17, D_SMALL_COMMIT = 18, D_TINY_IT = 19, D_TINY_STEPS = 20, D_TINY_CYC = 21, D_S3_CONT = 22,
+    D_S3_PREFIX = 23, D_B1 = 24, D_B2 = 25, D_M1 = 26, D_M2 = 27, D_TG = 28, D_TB = 29, D_TC = 33, D_TRACE = 36,
+    D_SPAN_CYC = 37, D_SPAN_NS = 38, D_SHELL_UNITS = 39, D_LISTED = 40, D_REMOVED = 41, D_SINGLE = 42,
+    D_TMERGE = 43, D_TMERGE_CYC = 44, D_GROUNDS = 45, D_GATHERS = 46
+};
+
 // Warp-wide: the first (up to mt) set bits of the rank bitmap, i.e. the best
 // candidates in priority order, written to rank_out[0..m); returns m (0 when
 // no candidate is left).  Lane 0 walks the summary levels to the first
@@ -688,7 +699,10 @@ __device__ int gather_top(const Inv &a, u64 *s1, u64 *s2, u64 *s3, int *cur1, in
             atomicAnd(p, ~(1u << (c0 & 31)));
         }
         const unsigned stale = __ballot_sync(0xffffffffu, st);
-        if (lane == 0 && stale) *n_stale += __popc(stale);
+        if (lane == 0) {
+            if (stale) n_stale[0] += __popc(stale);
+            n_stale[D_GROUNDS - D_STALE]++;   // rounds of the gather
+        }
         const int cnt = __popcll(w0);
         int inc = cnt;
 #pragma unroll
@@ -732,6 +746,7 @@ __device__ int gather_items(const Inv &a, Batch &B, u64 *s1, u64 *s2, u64 *s3, i
                             const FastDiv &fd_nyz, const FastDiv &fd_nz, long long *n_stale)
 {
     const int m = gather_top<L1SMEM>(a, s1, s2, s3, &B.cur1, lane, mt, B.rank, n_stale);
+    if (lane == 0) n_stale[D_GATHERS - D_STALE]++;
     const uint32_t nyz = (uint32_t)a.ny * (uint32_t)a.nz;
 #pragma unroll
     for (int h = 0; h < 2; h++) {
@@ -800,16 +815,6 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
-// Diagnostic counters of the invasion, kept by thread 0 in shared memory
-// (slot = index in the kernel's output, see ibip_invade_stats).
-enum Diag {
-    D_ITERS = 2, D_SEL = 3, D_BOUND = 4, D_COMMIT = 5, D_ITEMS = 6, D_COMMITTED = 7, D_STALE = 8, D_ROWS = 9,
-    D_SMALL_CYC = 10, D_SMALL_N = 11, D_GATHER = 12, D_PAIRS = 14, D_TAIL = 15, D_SMALL_SEL = 16,
-    D_SMALL_BOUND = 17, D_SMALL_COMMIT = 18, D_TINY_IT = 19, D_TINY_STEPS = 20, D_TINY_CYC = 21, D_S3_CONT = 22,
-    D_S3_PREFIX = 23, D_B1 = 24, D_B2 = 25, D_M1 = 26, D_M2 = 27, D_TG = 28, D_TB = 29, D_TC = 33, D_TRACE = 36,
-    D_SPAN_CYC = 37, D_SPAN_NS = 38, D_SHELL_UNITS = 39, D_LISTED = 40, D_REMOVED = 41, D_SINGLE = 42,
-    D_TMERGE = 43, D_TMERGE_CYC = 44
-};
 
 // One timing record per batch (thread 0): first step (0-based), steps
 // committed, SM cycles from batch selection to the end of its commit, the

@@ -219,7 +219,7 @@ class Context:
                 "bound_ranks", "commit_stamp", "commit_queue", "tiny_gather", "tiny_bound", "mm_rounds",
                 "mm_activations", "mm_sweeps", "tiny_commit", "unused", "first_unit_rank", "trace_batches",
                 "span_cycles", "span_ns", "shell_units", "shell_listed", "removed", "single_batches",
-                "tiny_merged", "tiny_merge_cycles"]
+                "tiny_merged", "tiny_merge_cycles", "gather_rounds", "gathers"]
         return dict(zip(keys, [int(x) for x in a]))
 
     def invade_trace(self, buf):
