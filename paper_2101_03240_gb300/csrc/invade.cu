@@ -878,6 +878,7 @@ __device__ __forceinline__ void commit_single(const Inv &a, const Batch &B, u64 
 // 1) until the best candidate is no longer single-voxel, the front is empty
 // or the step limit is reached.
 constexpr int kNewCap = 6 * kM;   // candidates one single-voxel batch can queue
+constexpr int kTinyM = 32;       // batch size of the single-voxel loop
 constexpr int kMinMerge = 16;     // smaller merged batches are refilled from the bitmap
 
 template <bool L1SMEM, bool PROF>
@@ -938,7 +939,7 @@ __device__ void tiny_loop(const Inv &a, Batch &B, u64 *s1, u64 *s2, u64 *s3, con
                     if (pos < kM) { tR[pos] = key; tI[pos] = v; }
                 }
                 bar_sync_64();
-                const int m = min(T, kM);
+                const int m = min(T, kTinyM);
                 if (tid < m) {
                     const uint32_t v = (uint32_t)tI[tid];
                     const uint32_t x = fdiv(v, fd_nyz), rem = v - x * (uint32_t)a.ny * (uint32_t)a.nz;
@@ -949,7 +950,7 @@ __device__ void tiny_loop(const Inv &a, Batch &B, u64 *s1, u64 *s2, u64 *s3, con
                     B.x[tid] = (int)x; B.y[tid] = (int)y; B.z[tid] = (int)(rem - y * (uint32_t)a.nz);
                 }
                 if (tid == 0) {
-                    if (T > kM) B.Rk = tR[kM - 1];   // the truncated tail is still in the bitmap
+                    if (T > kTinyM) B.Rk = tR[kTinyM - 1];   // the truncated tail is still in the bitmap
                     int stop = 0, mcap = m;
                     const int64_t remain = a.max_steps - k;
                     if (remain < (int64_t)m) mcap = (int)max(remain, (int64_t)0);
@@ -962,7 +963,7 @@ __device__ void tiny_loop(const Inv &a, Batch &B, u64 *s1, u64 *s2, u64 *s3, con
             }
         }
         if (gather && tid < 32) {
-            const int m = gather_items<L1SMEM, false>(a, B, s1, s2, s3, lane, kM, fd_nyz, fd_nz, sD + D_STALE);
+            const int m = gather_items<L1SMEM, false>(a, B, s1, s2, s3, lane, kTinyM, fd_nyz, fd_nz, sD + D_STALE);
             if (lane == 0) {
                 int stop = 0, mcap = m;
                 const int64_t remain = a.max_steps - k;
