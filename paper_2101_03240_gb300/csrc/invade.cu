@@ -878,7 +878,7 @@ __device__ __forceinline__ void commit_single(const Inv &a, const Batch &B, u64 
 // 1) until the best candidate is no longer single-voxel, the front is empty
 // or the step limit is reached.
 constexpr int kNewCap = 6 * kM;   // candidates one single-voxel batch can queue
-constexpr int kTinyM = 32;       // batch size of the single-voxel loop
+constexpr int kTinyM = kM;       // batch size of the single-voxel loop
 constexpr int kMinMerge = 16;     // smaller merged batches are refilled from the bitmap
 
 template <bool L1SMEM, bool PROF>
