@@ -239,6 +239,52 @@ __device__ __forceinline__ int line_min_smem(const int32_t *col, int i, int n, i
     return best;
 }
 
+// The search for output i continued from distance d (dd = d * d), each
+// side while it is inside the line.
+__device__ __forceinline__ int line_min_smem_from(const int32_t *col, int i, int n, int best, int d, int dd)
+{
+    const int32_t *c = col + i * kStripW;
+    for (; dd < best && (d <= i || d <= n - 1 - i); d++) {
+        const int vl = d <= i ? c[-d * kStripW] : kNone;
+        const int vr = d <= n - 1 - i ? c[d * kStripW] : kNone;
+        best = min(best, min(vl, vr) + dd);
+        dd += 2 * d + 1;
+    }
+    return best;
+}
+
+// Four consecutive outputs i0 .. i0 + 3 (all inside the line) of the same
+// search.  The windows of the four outputs move together: at distance d,
+// output k needs f(i0 + k - d) and f(i0 + k + d), so the left ends
+// (L0..L3) and right ends (R0..R3) shift by one entry per step and each
+// step loads two entries for four outputs.  Past an end of the line each
+// output finishes alone.
+__device__ __forceinline__ void line_min4_smem(const int32_t *col, int i0, int n, int lim, int (&b)[4])
+{
+    const int32_t *c = col + i0 * kStripW;
+    int L0 = c[0], L1 = c[kStripW], L2 = c[2 * kStripW], L3 = c[3 * kStripW];
+    int R0 = L0, R1 = L1, R2 = L2, R3 = L3;
+    b[0] = min(L0, lim); b[1] = min(L1, lim); b[2] = min(L2, lim); b[3] = min(L3, lim);
+    const int both = min(i0, n - 4 - i0);
+    int d = 1, dd = 1;
+    int bmax = max(max(b[0], b[1]), max(b[2], b[3]));
+    for (; d <= both && dd < bmax; d++) {
+        L3 = L2; L2 = L1; L1 = L0; L0 = c[-d * kStripW];
+        R0 = R1; R1 = R2; R2 = R3; R3 = c[(3 + d) * kStripW];
+        b[0] = min(b[0], min(L0, R0) + dd);
+        b[1] = min(b[1], min(L1, R1) + dd);
+        b[2] = min(b[2], min(L2, R2) + dd);
+        b[3] = min(b[3], min(L3, R3) + dd);
+        dd += 2 * d + 1;
+        bmax = max(max(b[0], b[1]), max(b[2], b[3]));
+    }
+    if (dd < bmax) {
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            if (dd < b[k]) b[k] = line_min_smem_from(col, i0 + k, n, b[k], d, dd);
+    }
+}
+
 // pass y: strip = (x, all y, 32 z).  blockIdx.x = z strip, blockIdx.y = x.
 // Output: partial sums < cap2, kNone elsewhere.  The staged column holds
 // the squared pass-z distances.
@@ -269,7 +315,15 @@ __device__ __forceinline__ void edt_y_block_smem(const uint16_t *__restrict__ d1
         for (int y = w; y < ny; y += kStripWarps) g2[b + (int64_t)y * nz] = kNone;
         return;
     }
-    for (int y = w; y < ny; y += kStripWarps) {
+    // four consecutive outputs per warp and pass, the tail one at a time
+    const int ny4 = ny & ~3;
+    for (int y0 = 4 * w; y0 < ny4; y0 += 4 * kStripWarps) {
+        int v[4];
+        line_min4_smem(s_col + lane, y0, ny, lim, v);
+#pragma unroll
+        for (int k = 0; k < 4; k++) g2[b + (int64_t)(y0 + k) * nz] = v[k] >= lim ? kNone : v[k];
+    }
+    for (int y = ny4 + w; y < ny; y += kStripWarps) {
         const int v = line_min_smem(s_col + lane, y, ny, lim);
         g2[b + (int64_t)y * nz] = v >= lim ? kNone : v;
     }
@@ -346,11 +400,26 @@ __device__ __forceinline__ void edt_x_block_smem(const int32_t *__restrict__ g2,
     __syncthreads();
     if (!ok) return;
     const bool none = !s_anyx[lane];   // nothing within reach: every value is IBIP_INF32
-    for (int x = w; x < nx; x += kStripWarps) {
-        if (none) {
+    if (none) {
+        for (int x = w; x < nx; x += kStripWarps)
             if (epi.need(b + x * st)) epi(b + x * st, IBIP_INF32);
-            continue;
-        }
+        return;
+    }
+    // four consecutive outputs per warp and pass (skipped when none is
+    // wanted), the tail one at a time
+    const int nx4 = nx & ~3;
+    for (int x0 = 4 * w; x0 < nx4; x0 += 4 * kStripWarps) {
+        bool nd[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) nd[k] = epi.need(b + (int64_t)(x0 + k) * st);
+        if (!(nd[0] || nd[1] || nd[2] || nd[3])) continue;
+        int v[4];
+        line_min4_smem(s_colx + lane, x0, nx, lim, v);
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            if (nd[k]) epi(b + (int64_t)(x0 + k) * st, v[k] >= lim ? IBIP_INF32 : v[k]);
+    }
+    for (int x = nx4 + w; x < nx; x += kStripWarps) {
         if (!epi.need(b + x * st)) continue;
         const int v = line_min_smem(s_colx + lane, x, nx, lim);
         epi(b + x * st, v >= lim ? IBIP_INF32 : v);
