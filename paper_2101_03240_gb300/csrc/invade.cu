@@ -461,13 +461,16 @@ __device__ __forceinline__ uint32_t span_mask(int w, int a, int b)
     return m & (0xffffffffu << lo);
 }
 
+// Squared offsets fit in int32: dimensions are at most 16384, so
+// dx^2 + dy^2 + dz^2 < 2^30, and r2 - 1 - dx^2 - dy^2 >= -2^29 even for
+// r2 = INT32_MAX (an image without solid).
 // z-interval of ball i at row (x, y): returns false if the row misses it
 __device__ __forceinline__ bool ball_run(const Batch &B, int i, int x, int y, int &lo, int &hi)
 {
-    int dx = x - B.x[i], dy = y - B.y[i];
-    int64_t e = (int64_t)B.r2[i] - 1 - (int64_t)dx * dx - (int64_t)dy * dy;
+    const int dx = x - B.x[i], dy = y - B.y[i];
+    const int e = B.r2[i] - 1 - dx * dx - dy * dy;
     if (e < 0) return false;
-    int h = B.isq((int)e);
+    const int h = B.isq(e);
     lo = B.z[i] - h;
     hi = B.z[i] + h;
     return true;
@@ -480,8 +483,8 @@ __device__ __forceinline__ int run_hw(const Inv &a, const Batch &B, int i, int x
 {
     if (x < 0 || y < 0 || x >= a.nx || y >= a.ny) return -1;
     const int dx = x - B.x[i], dy = y - B.y[i];
-    const int64_t e = (int64_t)B.r2[i] - 1 - (int64_t)dx * dx - (int64_t)dy * dy;
-    return e < 0 ? -1 : B.isq((int)e);
+    const int e = B.r2[i] - 1 - dx * dx - dy * dy;
+    return e < 0 ? -1 : B.isq(e);
 }
 
 // The shell of ball i in row (x, y): voxels outside the ball with a face
@@ -716,22 +719,29 @@ __device__ int gather_top(const Inv &a, u64 *s1, u64 *s2, u64 *s3, int *cur1, in
             continue;
         }
         const int m = min(tot, mt);
-        // item p (p = lane, lane + 32) comes from the lane whose inclusive
-        // count first exceeds p
+        if (__reduce_max_sync(0xffffffffu, (unsigned)cnt) <= 4) {
+            // sparse words: each lane writes the items of its own word, in
+            // order, from the exclusive prefix of the counts on
+            u64 w = w0;
+            for (int p = inc - cnt; w && p < m; p++, w &= w - 1) rank_out[p] = c0 * 64 + __ffsll((long long)w) - 1;
+        } else {
+            // dense words: item p (p = lane, lane + 32) comes from the lane
+            // whose inclusive count first exceeds p
 #pragma unroll
-        for (int h = 0; h < 2; h++) {
-            const int p = lane + 32 * h;
-            int lo = 0;
+            for (int h = 0; h < 2; h++) {
+                const int p = lane + 32 * h;
+                int lo = 0;
 #pragma unroll
-            for (int step = 16; step; step >>= 1) {
-                int v = __shfl_sync(0xffffffffu, inc, lo + step - 1);
-                if (v <= p) lo += step;
+                for (int step = 16; step; step >>= 1) {
+                    int v = __shfl_sync(0xffffffffu, inc, lo + step - 1);
+                    if (v <= p) lo += step;
+                }
+                const int src = min(lo, 31);
+                const u64 w = __shfl_sync(0xffffffffu, w0, src);
+                const int ex = __shfl_sync(0xffffffffu, inc - cnt, src);
+                const int cw = __shfl_sync(0xffffffffu, c0, src);
+                if (p < m) rank_out[p] = cw * 64 + nth_bit(w, p - ex);
             }
-            const int src = min(lo, 31);
-            const u64 w = __shfl_sync(0xffffffffu, w0, src);
-            const int ex = __shfl_sync(0xffffffffu, inc - cnt, src);
-            const int cw = __shfl_sync(0xffffffffu, c0, src);
-            if (p < m) rank_out[p] = cw * 64 + nth_bit(w, p - ex);
         }
         __syncwarp();
         return m;
@@ -1189,7 +1199,7 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
                 const int b = B.bigl[p >> sh];
                 if (j == b) continue;
                 const int dx = B.x[j] - B.x[b], dy = B.y[j] - B.y[b], dz = B.z[j] - B.z[b];
-                if (b < j && (int64_t)dx * dx + (int64_t)dy * dy + (int64_t)dz * dz < (int64_t)B.r2[b])
+                if (b < j && dx * dx + dy * dy + dz * dz < B.r2[b])
                     atomicOr(&B.cont32[j][b >> 5], 1u << (b & 31));
                 const int lim = B.h[b] + B.h[j] + 1;
                 if (abs(dx) <= lim && abs(dy) <= lim && abs(dz) <= lim) {
