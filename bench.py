@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--rule", choices=["frontier", "paper"], default="frontier",
                     help="invasion rule: the frontier rule, or Section 2.1 as printed (all ties, trunc radius)")
     ap.add_argument("--mio-levels", type=int, default=40)
+    ap.add_argument("--autotune", action="store_true",
+                    help="tune the EDT tile shapes on the first call of each shape class (before warm-up)")
     return ap.parse_args()
 
 
@@ -153,6 +155,8 @@ def run_batch(args, rank, world):
     nvox_total = sum(a.size for a in imgs_h)
     imgs = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in imgs_h]
     ctx = ibip.Context(local)
+    if args.autotune:
+        ctx.set_autotune(True)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=dev)
 
     def batched():
@@ -295,6 +299,8 @@ def run_serve(args, rank, world):
     nvox_total = sum(a.size for a in imgs_h)
     imgs = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in imgs_h]
     ctx = ibip.Context(local)
+    if args.autotune:
+        ctx.set_autotune(True)
     budget = int(args.budget_gb * (1 << 30))
     srv = ibip.Server(ctx, budget, max_slots=args.slots)
     torch.cuda.synchronize()
@@ -474,6 +480,8 @@ def run_ours(args, rank, world):
     img_h = np.ascontiguousarray(w.image)
     N = img_h.size
     ctx = ibip.Context(local)
+    if args.autotune:
+        ctx.set_autotune(True)
     img_d = torch.from_numpy(img_h).to(dev)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=dev)
 
@@ -623,7 +631,8 @@ def run_ours(args, rank, world):
         "config": {"workload": w.name if args.rule == "frontier" else w.name + "_paper_rule",
                    "shape": list(img_h.shape), "porosity": float(npore / N),
                    "inlet": "x0", "outlet": "x1" if w.outlet is not None else None, "mio_levels": len(levels),
-                   "l2": "flushed between steps (256 MB write)", "parallelism": "replicas%d" % world},
+                   "l2": "flushed between steps (256 MB write)", "parallelism": "replicas%d" % world,
+                   "edt_tiles": list(ctx.edt_tiles(img_h.shape)), "autotune": bool(args.autotune)},
         "invasion_steps": K,
         "equal_saturation": {"levels": len(levels), "max_diff_frac": max(eq[1]) / npore,
                              "mean_diff_frac": sum(eq[1]) / len(eq[1]) / npore,

@@ -429,6 +429,28 @@ IBIP_API int ibip_invade_stats(const ibip_ctx *ctx, int64_t *h_stats, int n);
  * capacity or a misaligned array.  Batched calls are never traced. */
 IBIP_API int ibip_invade_trace(ibip_ctx *ctx, int32_t *d_trace, int64_t capacity_records);
 
+/* Tile-shape autotuning (a tuning aid around the method; the paper has no
+ * counterpart).  mode 1: the first squared EDT of each shape class (every
+ * dimension rounded up to a power of two, and the GPU's SM count) times
+ * every candidate tile shape on that call's own input -- the candidates
+ * compute the same dt2, so the call's result does not change -- and keeps
+ * the fastest for later calls of that class; mode 0 (the default) uses the
+ * built-in shape.  Results are shared by all contexts of the process.
+ * cache_path (may be null): a text file of earlier results, read now and
+ * appended to with each new result, one line "<key> <choice> <us>".
+ * Returns IBIP_ERR_ARG for another mode or a path of 512 bytes or more. */
+IBIP_API int ibip_set_autotune(ibip_ctx *ctx, int mode, const char *cache_path);
+
+/* Force the EDT tile shape of this context: z_warps rows per block in the
+ * z pass and strip_warps warps per block in the y and x passes, one of the
+ * candidates (8,16) (4,16) (16,16) (8,8) (4,8) (16,8); (0,0) returns to the
+ * tuned or built-in shape.  IBIP_ERR_ARG for any other pair. */
+IBIP_API int ibip_set_edt_tiles(ibip_ctx *ctx, int z_warps, int strip_warps);
+
+/* The tile shape an EDT of these dimensions uses on this context now
+ * (forced, tuned, or the built-in (8,16)). */
+IBIP_API int ibip_edt_tiles(ibip_ctx *ctx, ibip_dims dims, int *h_z_warps, int *h_strip_warps);
+
 /* Static text for a status code. */
 IBIP_API const char *ibip_status_string(int status);
 

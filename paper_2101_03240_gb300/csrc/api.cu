@@ -311,6 +311,32 @@ int ibip_invade_stats(const ibip_ctx *ctx, int64_t *h_stats, int n)
     return IBIP_OK;
 }
 
+int ibip_set_autotune(ibip_ctx *ctx, int mode, const char *cache_path)
+{
+    if (!ctx || (mode != 0 && mode != 1)) return IBIP_ERR_ARG;
+    if (cache_path && strlen(cache_path) >= sizeof(ctx->tune_path)) return IBIP_ERR_ARG;
+    ctx->autotune = mode;
+    ctx->tune_path[0] = 0;
+    if (cache_path) {
+        strcpy(ctx->tune_path, cache_path);
+        ibip_tune_load(cache_path);
+    }
+    return IBIP_OK;
+}
+
+int ibip_set_edt_tiles(ibip_ctx *ctx, int z_warps, int strip_warps)
+{
+    if (!ctx) return IBIP_ERR_ARG;
+    return ibip_edt_tile_set(ctx, z_warps, strip_warps);
+}
+
+int ibip_edt_tiles(ibip_ctx *ctx, ibip_dims dims, int *h_z_warps, int *h_strip_warps)
+{
+    if (!ctx || !h_z_warps || !h_strip_warps || !dims_ok(dims)) return IBIP_ERR_ARG;
+    ibip_edt_tile_get(ctx, dims, h_z_warps, h_strip_warps);
+    return IBIP_OK;
+}
+
 int ibip_invade_trace(ibip_ctx *ctx, int32_t *d_trace, int64_t capacity_records)
 {
     if (!ctx || (d_trace && (capacity_records < 0 || ((uintptr_t)d_trace & 15)))) return IBIP_ERR_ARG;

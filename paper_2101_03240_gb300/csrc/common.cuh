@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <string>
 #include <stdint.h>
 
 #include "../../include/ibip.h"
@@ -64,6 +65,10 @@ struct ibip_ctx {
     // records written by the invasion CTAs.
     cudaStream_t stream2;
     void *h_done, *d_done;
+    // Tile shapes: autotune (0 off, 1 on), a forced EDT tile (index + 1,
+    // 0 = automatic) and the file that keeps tuning results ("" = none).
+    int autotune, edt_tile;
+    char tune_path[512];
 };
 
 // Completion record of one image of a batched invasion (host-mapped).
@@ -202,3 +207,13 @@ __device__ __forceinline__ int d_isqrt(int e)
 
 // largest r >= 0 with r*r < r2 (r2 >= 1): the ball's half-width along an axis
 __device__ __forceinline__ int d_ball_hw(int r2) { return d_isqrt(r2 - 1); }
+
+// Tile-shape tuning results (tune.cu): keyed by kernel, shape class and SM
+// count; shared by the process, optionally persisted in a text file.
+bool ibip_tune_get(const std::string &key, int *choice);
+void ibip_tune_put(const std::string &key, int choice, double us, const char *path);
+int ibip_tune_load(const char *path);
+// EDT tile shapes (edt.cu): force one of the candidates (0, 0 = automatic),
+// and the shape an EDT of these dimensions would use now.
+int ibip_edt_tile_set(ibip_ctx *ctx, int z_warps, int strip_warps);
+void ibip_edt_tile_get(ibip_ctx *ctx, ibip_dims d, int *z_warps, int *strip_warps);

@@ -14,6 +14,8 @@
 // once (i-j)^2 alone reaches the best value (or the optional cap): exact,
 // integer-only, and proportional to the distance itself.
 #include <algorithm>
+#include <cstdio>
+#include <string>
 #include <vector>
 
 #include "common.cuh"
@@ -111,17 +113,17 @@ __global__ void k_first_level(const int32_t *__restrict__ W, int64_t N, const in
 // lane's nearest feature on the left (warp max-scan, carried across tiles),
 // then right to left for the nearest on the right (min-scan), writing the
 // distances as packed 16-byte stores.
-template <class Feat>
+template <class Feat, int ZW = kZWarps>
 __device__ __forceinline__ void edt_z_block(const Feat &feat, int blk, int nrows, int nz, int cap,
                                             uint16_t *__restrict__ d1)
 {
     extern __shared__ unsigned char s_zraw[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t row = (int64_t)blk * kZWarps + w;
+    const int64_t row = (int64_t)blk * ZW + w;
     if (row >= nrows) return;   // whole warps only; no block barrier follows
     const int ntile = (nz + 511) >> 9;
     uint16_t *s_m = (uint16_t *)s_zraw + (size_t)w * ntile * 32;
-    int *s_l = (int *)(s_zraw + (size_t)kZWarps * ntile * 64) + (size_t)w * ntile * 32;
+    int *s_l = (int *)(s_zraw + (size_t)ZW * ntile * 64) + (size_t)w * ntile * 32;
     const int64_t base = row * nz;
     const int NONE = 1 << 29;
     int carry = -NONE;
@@ -180,14 +182,13 @@ __device__ __forceinline__ void edt_z_block(const Feat &feat, int blk, int nrows
     }
 }
 
-template <class Feat>
-__global__ void __launch_bounds__(kZWarps * 32) k_edt_z(Feat feat, int nrows, int nz, int cap,
-                                                        uint16_t *__restrict__ d1)
+template <class Feat, int ZW = kZWarps>
+__global__ void __launch_bounds__(ZW * 32) k_edt_z(Feat feat, int nrows, int nz, int cap, uint16_t *__restrict__ d1)
 {
-    edt_z_block(feat, blockIdx.x, nrows, nz, cap, d1);
+    edt_z_block<Feat, ZW>(feat, blockIdx.x, nrows, nz, cap, d1);
 }
 
-size_t edt_z_smem(int nz) { return (size_t)kZWarps * ((nz + 511) >> 9) * 32 * 6; }
+size_t edt_z_smem(int nz, int zw = kZWarps) { return (size_t)zw * ((nz + 511) >> 9) * 32 * 6; }
 
 // Sentinel of the partial sums: larger than any squared distance of an image
 // within the dimension limits (3 * 16383^2 < 2^30), and small enough that
@@ -289,6 +290,7 @@ __device__ __forceinline__ void line_min4_smem(const int32_t *col, int i0, int n
 // Output: partial sums < cap2, kNone elsewhere.  The staged column holds
 // the squared pass-z distances.
 // the staged body of pass y for z strip `strip` of plane x
+template <int SW = kStripWarps>
 __device__ __forceinline__ void edt_y_block_smem(const uint16_t *__restrict__ d1, int ny, int nz, int cap2,
                                                  int32_t *__restrict__ g2, int strip, int x)
 {
@@ -303,7 +305,7 @@ __device__ __forceinline__ void edt_y_block_smem(const uint16_t *__restrict__ d1
     __syncthreads();
     bool any = false;
 #pragma unroll 8
-    for (int y = w; y < ny; y += kStripWarps) {
+    for (int y = w; y < ny; y += SW) {
         const int v = ok ? __ldg(d1 + b + (int64_t)y * nz) : 0xffff;
         any |= v != 0xffff;
         s_col[y * kStripW + lane] = v == 0xffff ? kNone : v * v;
@@ -312,29 +314,29 @@ __device__ __forceinline__ void edt_y_block_smem(const uint16_t *__restrict__ d1
     __syncthreads();
     if (!ok) return;
     if (!s_any[lane]) {   // no feature in the column: nothing within reach
-        for (int y = w; y < ny; y += kStripWarps) g2[b + (int64_t)y * nz] = kNone;
+        for (int y = w; y < ny; y += SW) g2[b + (int64_t)y * nz] = kNone;
         return;
     }
     // four consecutive outputs per warp and pass, the tail one at a time
     const int ny4 = ny & ~3;
-    for (int y0 = 4 * w; y0 < ny4; y0 += 4 * kStripWarps) {
+    for (int y0 = 4 * w; y0 < ny4; y0 += 4 * SW) {
         int v[4];
         line_min4_smem(s_col + lane, y0, ny, lim, v);
 #pragma unroll
         for (int k = 0; k < 4; k++) g2[b + (int64_t)(y0 + k) * nz] = v[k] >= lim ? kNone : v[k];
     }
-    for (int y = ny4 + w; y < ny; y += kStripWarps) {
+    for (int y = ny4 + w; y < ny; y += SW) {
         const int v = line_min_smem(s_col + lane, y, ny, lim);
         g2[b + (int64_t)y * nz] = v >= lim ? kNone : v;
     }
 }
 
-template <bool SMEM>
-__global__ void __launch_bounds__(kStripWarps * 32) k_edt_y(const uint16_t *__restrict__ d1, int ny,
-                                                            int nz, int cap2, int32_t *__restrict__ g2)
+template <bool SMEM, int SW = kStripWarps>
+__global__ void __launch_bounds__(SW * 32) k_edt_y(const uint16_t *__restrict__ d1, int ny, int nz, int cap2,
+                                                   int32_t *__restrict__ g2)
 {
     if (SMEM) {
-        edt_y_block_smem(d1, ny, nz, cap2, g2, blockIdx.x, blockIdx.y);
+        edt_y_block_smem<SW>(d1, ny, nz, cap2, g2, blockIdx.x, blockIdx.y);
         return;
     }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -347,7 +349,7 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_edt_y(const uint16_t *__re
         const int v = __ldg(d1 + b + (int64_t)j * nz);
         return v == 0xffff ? kNone : v * v;
     };
-    for (int y = w; y < ny; y += kStripWarps) {
+    for (int y = w; y < ny; y += SW) {
         const int v = line_min(g, y, ny, lim);
         g2[b + (int64_t)y * nz] = v >= lim ? kNone : v;
     }
@@ -375,7 +377,7 @@ struct EpiLevel {
 // pass x: strip = (y, all x, 32 z).  blockIdx.x = z strip, blockIdx.y = y.
 // Final values >= cap2 (or no feature at all) are reported as IBIP_INF32.
 // the staged body of pass x for z strip `strip` of row y
-template <class Epi>
+template <class Epi, int SW = kStripWarps>
 __device__ __forceinline__ void edt_x_block_smem(const int32_t *__restrict__ g2, int nx, int ny, int nz, int cap2,
                                                  const Epi &epi, int strip, int y)
 {
@@ -391,7 +393,7 @@ __device__ __forceinline__ void edt_x_block_smem(const int32_t *__restrict__ g2,
     __syncthreads();
     bool any = false;
 #pragma unroll 8
-    for (int x = w; x < nx; x += kStripWarps) {
+    for (int x = w; x < nx; x += SW) {
         const int v = ok ? __ldg(g2 + b + x * st) : kNone;
         any |= v != kNone;
         s_colx[x * kStripW + lane] = v;
@@ -401,14 +403,14 @@ __device__ __forceinline__ void edt_x_block_smem(const int32_t *__restrict__ g2,
     if (!ok) return;
     const bool none = !s_anyx[lane];   // nothing within reach: every value is IBIP_INF32
     if (none) {
-        for (int x = w; x < nx; x += kStripWarps)
+        for (int x = w; x < nx; x += SW)
             if (epi.need(b + x * st)) epi(b + x * st, IBIP_INF32);
         return;
     }
     // four consecutive outputs per warp and pass (skipped when none is
     // wanted), the tail one at a time
     const int nx4 = nx & ~3;
-    for (int x0 = 4 * w; x0 < nx4; x0 += 4 * kStripWarps) {
+    for (int x0 = 4 * w; x0 < nx4; x0 += 4 * SW) {
         bool nd[4];
 #pragma unroll
         for (int k = 0; k < 4; k++) nd[k] = epi.need(b + (int64_t)(x0 + k) * st);
@@ -419,19 +421,19 @@ __device__ __forceinline__ void edt_x_block_smem(const int32_t *__restrict__ g2,
         for (int k = 0; k < 4; k++)
             if (nd[k]) epi(b + (int64_t)(x0 + k) * st, v[k] >= lim ? IBIP_INF32 : v[k]);
     }
-    for (int x = nx4 + w; x < nx; x += kStripWarps) {
+    for (int x = nx4 + w; x < nx; x += SW) {
         if (!epi.need(b + x * st)) continue;
         const int v = line_min_smem(s_colx + lane, x, nx, lim);
         epi(b + x * st, v >= lim ? IBIP_INF32 : v);
     }
 }
 
-template <bool SMEM, class Epi>
-__global__ void __launch_bounds__(kStripWarps * 32) k_edt_x(const int32_t *__restrict__ g2, int nx,
-                                                            int ny, int nz, int cap2, Epi epi)
+template <bool SMEM, class Epi, int SW = kStripWarps>
+__global__ void __launch_bounds__(SW * 32) k_edt_x(const int32_t *__restrict__ g2, int nx, int ny, int nz, int cap2,
+                                                   Epi epi)
 {
     if (SMEM) {
-        edt_x_block_smem(g2, nx, ny, nz, cap2, epi, blockIdx.x, blockIdx.y);
+        edt_x_block_smem<Epi, SW>(g2, nx, ny, nz, cap2, epi, blockIdx.x, blockIdx.y);
         return;
     }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -442,7 +444,7 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_edt_x(const int32_t *__res
     const int lim = min(cap2, kNone);
     if (!ok) return;
     auto g = [&](int j) -> int { return __ldg(g2 + b + j * st); };
-    for (int x = w; x < nx; x += kStripWarps) {
+    for (int x = w; x < nx; x += SW) {
         if (!epi.need(b + x * st)) continue;
         const int v = line_min(g, x, nx, lim);
         epi(b + x * st, v >= lim ? IBIP_INF32 : v);
@@ -451,7 +453,7 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_edt_x(const int32_t *__res
 
 constexpr size_t kSmemBudget = 200 * 1024;
 
-template <class Feat, class Epi>
+template <class Feat, class Epi, int ZW = kZWarps, int SW = kStripWarps>
 int edt_passes(ibip_ctx *ctx, Feat feat, ibip_dims d, int cap, int cap2, Epi epi, int cls)
 {
     int64_t N = nvox(d);
@@ -461,24 +463,24 @@ int edt_passes(ibip_ctx *ctx, Feat feat, ibip_dims d, int cap, int cap2, Epi epi
     cudaStream_t s = ctx->stream;
     int nrows = d.nx * d.ny;
     ibip_prof_begin(ctx, cls);
-    k_edt_z<Feat><<<(nrows + kZWarps - 1) / kZWarps, kZWarps * 32, edt_z_smem(d.nz), s>>>(feat, nrows, d.nz, cap, d1);
+    k_edt_z<Feat, ZW><<<(nrows + ZW - 1) / ZW, ZW * 32, edt_z_smem(d.nz, ZW), s>>>(feat, nrows, d.nz, cap, d1);
     IBIP_LAUNCH(ctx);
     dim3 gy((d.nz + kStripW - 1) / kStripW, d.nx);
     size_t sy = (size_t)d.ny * kStripW * sizeof(int32_t);
     if (sy <= kSmemBudget) {
-        cudaFuncSetAttribute(k_edt_y<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget);
-        k_edt_y<true><<<gy, kStripWarps * 32, sy, s>>>(d1, d.ny, d.nz, cap2, g2);
+        cudaFuncSetAttribute(k_edt_y<true, SW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget);
+        k_edt_y<true, SW><<<gy, SW * 32, sy, s>>>(d1, d.ny, d.nz, cap2, g2);
     } else {
-        k_edt_y<false><<<gy, kStripWarps * 32, 0, s>>>(d1, d.ny, d.nz, cap2, g2);
+        k_edt_y<false, SW><<<gy, SW * 32, 0, s>>>(d1, d.ny, d.nz, cap2, g2);
     }
     IBIP_LAUNCH(ctx);
     dim3 gx((d.nz + kStripW - 1) / kStripW, d.ny);
     size_t sx = (size_t)d.nx * kStripW * sizeof(int32_t);
     if (sx <= kSmemBudget) {
-        cudaFuncSetAttribute(k_edt_x<true, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget);
-        k_edt_x<true, Epi><<<gx, kStripWarps * 32, sx, s>>>(g2, d.nx, d.ny, d.nz, cap2, epi);
+        cudaFuncSetAttribute(k_edt_x<true, Epi, SW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget);
+        k_edt_x<true, Epi, SW><<<gx, SW * 32, sx, s>>>(g2, d.nx, d.ny, d.nz, cap2, epi);
     } else {
-        k_edt_x<false, Epi><<<gx, kStripWarps * 32, 0, s>>>(g2, d.nx, d.ny, d.nz, cap2, epi);
+        k_edt_x<false, Epi, SW><<<gx, SW * 32, 0, s>>>(g2, d.nx, d.ny, d.nz, cap2, epi);
     }
     IBIP_LAUNCH(ctx);
     ibip_prof_end(ctx, cls);
@@ -529,9 +531,121 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_edt_x_b(const EdtJob *__re
 
 }  // namespace
 
+// ---- tile shapes of the squared EDT: rows per block of pass z and warps
+// per block of passes y and x.  Entry 0 is the built-in shape.
+namespace {
+
+struct EdtTile {
+    int zw, sw;
+};
+constexpr EdtTile kEdtTiles[] = {{8, 16}, {4, 16}, {16, 16}, {8, 8}, {4, 8}, {16, 8}};
+constexpr int kNEdtTiles = (int)(sizeof(kEdtTiles) / sizeof(kEdtTiles[0]));
+
+int edt_run_tile(ibip_ctx *ctx, int t, const uint8_t *image, ibip_dims d, int32_t *dt2)
+{
+    const FeatSolid f{image};
+    const EpiStore e{dt2};
+    switch (t) {
+    case 1: return edt_passes<FeatSolid, EpiStore, 4, 16>(ctx, f, d, 0xfffe, IBIP_INF32, e, IBIP_K_EDT);
+    case 2: return edt_passes<FeatSolid, EpiStore, 16, 16>(ctx, f, d, 0xfffe, IBIP_INF32, e, IBIP_K_EDT);
+    case 3: return edt_passes<FeatSolid, EpiStore, 8, 8>(ctx, f, d, 0xfffe, IBIP_INF32, e, IBIP_K_EDT);
+    case 4: return edt_passes<FeatSolid, EpiStore, 4, 8>(ctx, f, d, 0xfffe, IBIP_INF32, e, IBIP_K_EDT);
+    case 5: return edt_passes<FeatSolid, EpiStore, 16, 8>(ctx, f, d, 0xfffe, IBIP_INF32, e, IBIP_K_EDT);
+    default: return edt_passes<FeatSolid, EpiStore, 8, 16>(ctx, f, d, 0xfffe, IBIP_INF32, e, IBIP_K_EDT);
+    }
+}
+
+int ceil_log2(int v)
+{
+    int c = 0;
+    while ((1 << c) < v) c++;
+    return c;
+}
+
+// shape class: each dimension rounded up to a power of two, and the SM count
+std::string edt_key(const ibip_ctx *ctx, ibip_dims d)
+{
+    char k[96];
+    snprintf(k, sizeof(k), "edt:%d.%d.%d:sm%d", ceil_log2(d.nx), ceil_log2(d.ny), ceil_log2(d.nz), ctx->sm_count);
+    return k;
+}
+
+// Time every tile shape on this call's own input (each run writes the same
+// dt2) and keep the fastest: one warm-up run, then the best of three.
+int edt_tune(ibip_ctx *ctx, const uint8_t *image, ibip_dims d, int32_t *dt2, int *best_out, double *us_out)
+{
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return IBIP_ERR_CUDA;
+    if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return IBIP_ERR_CUDA;
+    }
+    int best = 0, st = IBIP_OK;
+    float best_ms = 1e30f;
+    for (int t = 0; t < kNEdtTiles && st == IBIP_OK; t++) {
+        st = edt_run_tile(ctx, t, image, d, dt2);
+        float ms_min = 1e30f;
+        for (int r = 0; r < 3 && st == IBIP_OK; r++) {
+            cudaEventRecord(a, ctx->stream);
+            st = edt_run_tile(ctx, t, image, d, dt2);
+            cudaEventRecord(b, ctx->stream);
+            if (st == IBIP_OK) st = ibip_cuda_status(cudaEventSynchronize(b));
+            float ms = 0.f;
+            if (st == IBIP_OK && cudaEventElapsedTime(&ms, a, b) == cudaSuccess) ms_min = std::min(ms_min, ms);
+        }
+        if (st == IBIP_OK && ms_min < best_ms) { best_ms = ms_min; best = t; }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    *best_out = best;
+    *us_out = best_ms * 1e3;
+    return st;
+}
+
+int edt_tile_for(ibip_ctx *ctx, ibip_dims d)
+{
+    if (ctx->edt_tile > 0) return ctx->edt_tile - 1;
+    int t = 0;
+    if (ctx->autotune && ibip_tune_get(edt_key(ctx, d), &t) && t >= 0 && t < kNEdtTiles) return t;
+    return 0;
+}
+
+}  // namespace
+
 int ibip_edt_launch(ibip_ctx *ctx, const uint8_t *image, ibip_dims d, int32_t *dt2)
 {
-    return edt_passes(ctx, FeatSolid{image}, d, 0xfffe, IBIP_INF32, EpiStore{dt2}, IBIP_K_EDT);
+    if (ctx->edt_tile == 0 && ctx->autotune) {
+        const std::string key = edt_key(ctx, d);
+        int t = 0;
+        if (!ibip_tune_get(key, &t)) {
+            double us = 0.0;
+            const int st = edt_tune(ctx, image, d, dt2, &t, &us);
+            if (st) return st;
+            ibip_tune_put(key, t, us, ctx->tune_path);
+        }
+    }
+    return edt_run_tile(ctx, edt_tile_for(ctx, d), image, d, dt2);
+}
+
+int ibip_edt_tile_set(ibip_ctx *ctx, int z_warps, int strip_warps)
+{
+    if (z_warps == 0 && strip_warps == 0) {
+        ctx->edt_tile = 0;
+        return IBIP_OK;
+    }
+    for (int t = 0; t < kNEdtTiles; t++)
+        if (kEdtTiles[t].zw == z_warps && kEdtTiles[t].sw == strip_warps) {
+            ctx->edt_tile = t + 1;
+            return IBIP_OK;
+        }
+    return IBIP_ERR_ARG;
+}
+
+void ibip_edt_tile_get(ibip_ctx *ctx, ibip_dims d, int *z_warps, int *strip_warps)
+{
+    const EdtTile &t = kEdtTiles[edt_tile_for(ctx, d)];
+    *z_warps = t.zw;
+    *strip_warps = t.sw;
 }
 
 int ibip_first_level_launch(ibip_ctx *ctx, const int32_t *W, ibip_dims d, const int32_t *T_dev, int L, uint8_t *fl)

@@ -83,6 +83,9 @@ def _lib():
                 "ibip_invade_batched": (C.c_int, [P, i32, P]),
                 "ibip_invade_stats": (C.c_int, [P, C.POINTER(i64), C.c_int]),
                 "ibip_invade_trace": (C.c_int, [P, P, i64]),
+                "ibip_set_autotune": (C.c_int, [P, C.c_int, C.c_char_p]),
+                "ibip_set_edt_tiles": (C.c_int, [P, C.c_int, C.c_int]),
+                "ibip_edt_tiles": (C.c_int, [P, Dims, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
                 "ibip_profile_read": (C.c_int, [P, C.c_int, C.POINTER(dbl), C.POINTER(i64)]),
                 "ibip_job_footprint": (i64, [Dims, C.c_int]),
                 "ibip_trapping_ex": (C.c_int, [P, P, Dims, C.c_int, P, P, P, i64, P, C.POINTER(i64)]),
@@ -221,6 +224,26 @@ class Context:
                 "span_cycles", "span_ns", "shell_units", "shell_listed", "removed", "single_batches",
                 "tiny_merged", "tiny_merge_cycles", "gather_rounds", "gathers"]
         return dict(zip(keys, [int(x) for x in a]))
+
+    def set_autotune(self, on: bool, cache_path: str | None = None):
+        """Tile-shape autotuning of the EDT (see ibip_set_autotune)."""
+        st = _lib().ibip_set_autotune(self._h, int(bool(on)), None if cache_path is None else cache_path.encode())
+        if st != OK:
+            raise IbipError("ibip_set_autotune", st)
+
+    def set_edt_tiles(self, z_warps: int, strip_warps: int):
+        """Force an EDT tile shape ((0, 0): automatic)."""
+        st = _lib().ibip_set_edt_tiles(self._h, int(z_warps), int(strip_warps))
+        if st != OK:
+            raise IbipError("ibip_set_edt_tiles", st)
+
+    def edt_tiles(self, shape) -> tuple:
+        """(z_warps, strip_warps) an EDT of this shape would use now."""
+        zw, sw = C.c_int(0), C.c_int(0)
+        st = _lib().ibip_edt_tiles(self._h, _dims(shape), C.byref(zw), C.byref(sw))
+        if st != OK:
+            raise IbipError("ibip_edt_tiles", st)
+        return int(zw.value), int(sw.value)
 
     def invade_trace(self, buf):
         """Record one row per batch of later invade calls into `buf` (CUDA
