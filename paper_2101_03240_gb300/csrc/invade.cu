@@ -221,6 +221,43 @@ __global__ void k_seq_pres_b(const SortJob *__restrict__ jobs, int n, int32_t *p
     }
 }
 
+// pore statistics of many images (as k_stats), kVoxBlock * kVoxPer voxels
+// per block; a block finds its image by binary search over first blocks
+struct StatJob {
+    const int32_t *dt2;
+    int64_t N;
+    int blk;
+};
+
+__global__ void k_stats_b(const StatJob *__restrict__ jobs, int n, int *stats)
+{
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (jobs[mid].blk <= (int)blockIdx.x) lo = mid; else hi = mid;
+    }
+    const StatJob &J = jobs[lo];
+    const int64_t v0 = (int64_t)(blockIdx.x - J.blk) * kVoxBlock * kVoxPer;
+    int mx = 0, np = 0, inf = 0;
+    for (int q = 0; q < kVoxPer; q++) {
+        const int64_t v = v0 + q * kVoxBlock + threadIdx.x;
+        if (v >= J.N) break;
+        const int d = J.dt2[v];
+        if (d > 0) {
+            np++;
+            if (d == IBIP_INF32) inf = 1; else mx = max(mx, d);
+        }
+    }
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    np = __reduce_add_sync(0xffffffffu, np);
+    inf = __reduce_or_sync(0xffffffffu, inf);
+    if ((threadIdx.x & 31) == 0 && (np | inf)) {
+        atomicMax(stats + 3 * lo, mx);
+        atomicAdd(stats + 3 * lo + 1, np);
+        atomicOr(stats + 3 * lo + 2, inf);
+    }
+}
+
 // after the flat inclusive scan of the presence pool: each image's base and
 // number of distinct values
 __global__ void k_pres_base_b(SortJob *jobs, int n, const int32_t *__restrict__ incl)
@@ -1987,14 +2024,23 @@ int ibip_invade_batch_run(ibip_ctx *ctx, int n, IbipBatchItem *it, IbipBatchEarl
     if (n > kMaxBatch) return IBIP_ERR_ARG;
     int *h = (int *)ctx->h_pinned;
     // pore statistics of every image, one synchronisation
-    int *st3 = (int *)ibip_scratch(ctx, SC_BSTAT, (size_t)3 * n * sizeof(int));
-    if (!st3) return IBIP_ERR_OOM;
+    // (one launch for all images: blocks find their image in a table)
+    const size_t st_bytes = ((size_t)3 * n * sizeof(int) + 255) / 256 * 256;
+    char *sbuf = (char *)ibip_scratch(ctx, SC_BSTAT, st_bytes + (size_t)n * sizeof(StatJob));
+    if (!sbuf) return IBIP_ERR_OOM;
+    int *st3 = (int *)sbuf;
+    StatJob *dsj = (StatJob *)(sbuf + st_bytes);
+    std::vector<StatJob> sjobs(n);
+    int blk_st = 0;
+    for (int j = 0; j < n; j++) {
+        sjobs[j] = StatJob{it[j].dt2, nvox(it[j].d), blk_st};
+        blk_st += (int)((nvox(it[j].d) + (int64_t)kVoxBlock * kVoxPer - 1) / ((int64_t)kVoxBlock * kVoxPer));
+    }
     ibip_prof_begin(ctx, IBIP_K_RANK);
     cudaMemsetAsync(st3, 0, (size_t)3 * n * sizeof(int), s);
-    for (int j = 0; j < n; j++) {
-        k_stats<<<ctx->sm_count * 2, 256, 0, s>>>(it[j].dt2, nvox(it[j].d), st3 + 3 * j);
-        IBIP_LAUNCH(ctx);
-    }
+    cudaMemcpyAsync(dsj, sjobs.data(), (size_t)n * sizeof(StatJob), cudaMemcpyHostToDevice, s);
+    k_stats_b<<<blk_st, kVoxBlock, 0, s>>>(dsj, n, st3);
+    IBIP_LAUNCH(ctx);
     cudaMemcpyAsync(h, st3, (size_t)3 * n * sizeof(int), cudaMemcpyDeviceToHost, s);
     if (cudaStreamSynchronize(s) != cudaSuccess) return IBIP_ERR_CUDA;
     std::vector<int> maxd(n), npore(n), hasinf(n);
