@@ -66,7 +66,8 @@ def parse():
     ap.add_argument("--config", choices=["spheres200", "blobs48", "blobs512", "batch256", "serve"],
                     default="spheres200")
     ap.add_argument("--requests", type=int, default=64, help="serve: requests in the Poisson stream")
-    ap.add_argument("--budget-gb", type=float, default=64.0, help="serve: device arena of the server")
+    ap.add_argument("--budget-gb", type=float, default=20.0,
+                    help="serve: device arena of the server (20 GB: below the stream's peak demand, so admission binds)")
     ap.add_argument("--slots", type=int, default=64, help="serve: worker slots")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rule", choices=["frontier", "paper"], default="frontier",
