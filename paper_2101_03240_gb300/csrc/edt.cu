@@ -33,11 +33,10 @@ __device__ __forceinline__ uint32_t byte_bits(uint32_t x)
     return (x & 1u) | ((x >> 7) & 2u) | ((x >> 14) & 4u) | ((x >> 21) & 8u);
 }
 
-// The feature tests of a pass-z row: operator() for one voxel, bits16 for the
+// The feature tests of a pass-z row: bits16 for the
 // 16 voxels base+z0 .. base+z0+15 (bit k = voxel z0+k; none past nz).
 struct FeatSolid {
     const uint8_t *img;
-    __device__ bool operator()(int64_t v) const { return __ldg(img + v) == 0; }
     __device__ uint32_t bits16(int64_t base, int z0, int nz) const
     {
         const uint8_t *p = img + base + z0;
@@ -54,7 +53,6 @@ struct FeatSolid {
 struct FeatAtLeast {
     const int32_t *w;
     int32_t t;
-    __device__ bool operator()(int64_t v) const { return __ldg(w + v) >= t; }
     __device__ uint32_t bits16(int64_t base, int z0, int nz) const
     {
         const int32_t *p = w + base + z0;
@@ -77,7 +75,6 @@ struct FeatAtLeast {
 struct FeatFirstLevel {
     const uint8_t *fl;
     int i;
-    __device__ bool operator()(int64_t v) const { return __ldg(fl + v) <= i; }
     __device__ uint32_t bits16(int64_t base, int z0, int nz) const
     {
         const uint8_t *p = fl + base + z0;
@@ -177,7 +174,9 @@ __device__ __forceinline__ void edt_z_block(const Feat &feat, int blk, int nrows
             o4[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
             o4[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
         } else {
-            for (int k = 0; k < 16 && z0 + k < nz; k++) o[k] = (uint16_t)(packed[k >> 1] >> ((k & 1) * 16));
+#pragma unroll
+            for (int k = 0; k < 16; k++)   // static indices keep packed[] in registers
+                if (z0 + k < nz) o[k] = (uint16_t)(packed[k >> 1] >> ((k & 1) * 16));
         }
     }
 }
