@@ -56,7 +56,7 @@ typedef enum {
     IBIP_ERR_OOM = -3,           /* scratch allocation failed */
     IBIP_ERR_STEP_LIMIT = -4,    /* invasion stopped at max_steps with candidates left */
     IBIP_ERR_NOT_CONVERGED = -5, /* propagation hit its round limit */
-    IBIP_ERR_CANCELLED = -6,     /* reserved */
+    IBIP_ERR_CANCELLED = -6,     /* the invasion stopped at a cancel request (ibip_cancel) */
     IBIP_ERR_BOUNDS = -7,        /* a device-side index check failed */
     IBIP_ERR_TOO_LARGE = -8      /* image larger than ibip_edt_noalloc's fixed scratch */
 } ibip_status;
@@ -450,6 +450,29 @@ IBIP_API int ibip_set_edt_tiles(ibip_ctx *ctx, int z_warps, int strip_warps);
 /* The tile shape an EDT of these dimensions uses on this context now
  * (forced, tuned, or the built-in (8,16)). */
 IBIP_API int ibip_edt_tiles(ibip_ctx *ctx, ibip_dims dims, int *h_z_warps, int *h_strip_warps);
+
+/* Cancel (on = 1) the invasion running on this context, or the next one
+ * it starts; on = 0 withdraws the request.  Safe to call from another host
+ * thread while ibip_invade / ibip_invade_ex / ibip_invade_batched block.
+ * The flag lives in host-mapped memory; the invasion kernel reads it every
+ * 16 batches of its main loop and every 64 of its single-voxel loop, and
+ * stops before committing the next batch: the call returns
+ * IBIP_ERR_CANCELLED with *h_n_steps = k, and seq, step_r2 and step_centre
+ * hold a valid invasion of k steps, which ibip_invade_ex(resume = 1)
+ * continues to the same result as an uninterrupted call.  Serving the
+ * request clears the flag; the context stays usable.  An invasion that
+ * ends before it reads the flag returns normally and leaves the flag set
+ * (withdraw it with on = 0).  The paper has no counterpart (a control path
+ * around the method). */
+IBIP_API int ibip_cancel(ibip_ctx *ctx, int on);
+
+/* Test hook (fault injection on the host): the nth scratch allocation of
+ * this context from now that needs new device memory fails, so the call
+ * that makes it returns IBIP_ERR_OOM (its outputs are then undefined, as
+ * after any error); later calls allocate again and the context stays
+ * usable.  nth = 0 turns the hook off; a negative nth is IBIP_ERR_ARG.
+ * The paper has no counterpart. */
+IBIP_API int ibip_debug_fail_alloc(ibip_ctx *ctx, int nth);
 
 /* Static text for a status code. */
 IBIP_API const char *ibip_status_string(int status);

@@ -106,6 +106,7 @@ void *ibip_scratch(ibip_ctx *ctx, int slot, size_t bytes)
 {
     if (bytes == 0) bytes = 16;
     if (ctx->slot_bytes[slot] >= bytes) return ctx->slot[slot];
+    if (ctx->fail_alloc > 0 && --ctx->fail_alloc == 0) return nullptr;   // injected failure
     if (ctx->arena) {
         const size_t b = (bytes + 255) & ~(size_t)255;
         if (ctx->arena_used + b > ctx->arena_size) return nullptr;
@@ -258,14 +259,20 @@ int ibip_create(ibip_ctx **out, int device, void *cuda_stream)
         delete c;
         return IBIP_ERR_CUDA;
     }
+    void *hc = nullptr, *dc = nullptr;
     if (cudaHostAlloc(&c->h_done, (size_t)kMaxBatch * sizeof(IbipBatchDone), cudaHostAllocMapped) != cudaSuccess ||
-        cudaHostGetDevicePointer(&c->d_done, c->h_done, 0) != cudaSuccess) {
+        cudaHostGetDevicePointer(&c->d_done, c->h_done, 0) != cudaSuccess ||
+        cudaHostAlloc(&hc, 64, cudaHostAllocMapped) != cudaSuccess || cudaHostGetDevicePointer(&dc, hc, 0) != cudaSuccess) {
         cudaGetLastError();
+        if (hc) cudaFreeHost(hc);
         if (c->h_done) cudaFreeHost(c->h_done);
         cudaFreeHost(c->h_pinned);
         delete c;
         return IBIP_ERR_CUDA;
     }
+    c->h_cancel = (volatile int *)hc;
+    c->d_cancel = (int *)dc;
+    *c->h_cancel = 0;
     *out = c;
     return IBIP_OK;
 }
@@ -283,6 +290,7 @@ int ibip_destroy(ibip_ctx *ctx)
         cudaStreamDestroy(ctx->stream2);
     }
     if (ctx->h_done) cudaFreeHost(ctx->h_done);
+    if (ctx->h_cancel) cudaFreeHost((void *)ctx->h_cancel);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
     delete ctx;
     return IBIP_OK;
@@ -308,6 +316,20 @@ int ibip_invade_stats(const ibip_ctx *ctx, int64_t *h_stats, int n)
 {
     if (!ctx || !h_stats || n < 0) return IBIP_ERR_ARG;
     for (int i = 0; i < n && i < kInvStats; i++) h_stats[i] = ctx->inv_stats[i];
+    return IBIP_OK;
+}
+
+int ibip_cancel(ibip_ctx *ctx, int on)
+{
+    if (!ctx || (on != 0 && on != 1) || !ctx->h_cancel) return IBIP_ERR_ARG;
+    *ctx->h_cancel = on;
+    return IBIP_OK;
+}
+
+int ibip_debug_fail_alloc(ibip_ctx *ctx, int nth)
+{
+    if (!ctx || nth < 0) return IBIP_ERR_ARG;
+    ctx->fail_alloc = nth;
     return IBIP_OK;
 }
 
@@ -624,6 +646,8 @@ int ibip_invade_batched(ibip_ctx *ctx, int32_t n, ibip_job *jobs)
     if (st) return st;
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return ibip_cuda_status(e);
+    for (int j = 0; j < n; j++)
+        if (jobs[j].status == IBIP_ERR_CANCELLED && ctx->h_cancel) *ctx->h_cancel = 0;   // the request is served
     if (P.early_err) return P.early_err;
     for (int j = 0; j < n; j++)
         if (jobs[j].status != IBIP_OK) return jobs[j].status;

@@ -69,6 +69,12 @@ struct ibip_ctx {
     // 0 = automatic) and the file that keeps tuning results ("" = none).
     int autotune, edt_tile;
     char tune_path[512];
+    // Cancellation: a host-mapped flag the invasion kernels poll (host and
+    // device addresses), and a test hook that fails the n-th scratch
+    // allocation from now (0 = off).
+    volatile int *h_cancel;
+    int *d_cancel;
+    int fail_alloc;
 };
 
 // Completion record of one image of a batched invasion (host-mapped).

@@ -376,6 +376,7 @@ struct Inv {
     int resume;            // seq holds an earlier run's steps 1..k0 on entry
     int64_t k0;            // steps already taken (resume), else 0
     int4 *trace;           // per-batch records (two int4 each, see trace_batch), or null
+    const int *cancel;     // host-mapped cancel flag, polled every few batches, or null
     int64_t trace_cap;     // records that fit in trace
 };
 
@@ -935,6 +936,7 @@ __device__ void tiny_loop(const Inv &a, Batch &B, u64 *s1, u64 *s2, u64 *s3, con
 {
     const int lane = tid & 31;
     const int first1 = (int)a.out[kFirst1Slot];   // ranks below it hold dt2 > 1
+    int tpoll = 0;   // batches since the last cancel poll (thread 0)
     if (tid == 0) { B.tmerge = 0; B.nN = 0; B.novf = 0; }
     bar_sync_64();
     for (;;) {
@@ -1025,7 +1027,12 @@ __device__ void tiny_loop(const Inv &a, Batch &B, u64 *s1, u64 *s2, u64 *s3, con
                 B.Rk = m > 0 ? B.rank[m - 1] : INT_MAX;
             }
         }
-        if (tid == 0) { B.nN = 0; B.novf = 0; }
+        if (tid == 0) {
+            B.nN = 0;
+            B.novf = 0;
+            // every 64th batch: the host's cancel flag (stop before committing)
+            if (a.cancel && (tpoll++ & 63) == 0 && B.tstop == 0 && *(const volatile int *)a.cancel) B.tstop = 5;
+        }
         bar_sync_64();
         const long long tb = tclk<PROF>();
         if (tid == 0 && !gather) {
@@ -1144,6 +1151,7 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
     int64_t k = a.k0;
     // diagnostics (thread 0): cycles per phase, items, stale summary bits, ...
     __shared__ long long sD[kNOut];
+    int poll = 0;   // batches since the last cancel poll (lane 0 of warp 0)
     if (tid == 0)
         for (int q = 0; q < kNOut; q++) sD[q] = 0;
     for (;;) {
@@ -1156,6 +1164,10 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
         // ones, and takes the leading set bits as the batch.
         // S1 (warp 0): the batch items and their data.
         if (tid < 32) {
+            // every 16th batch, lane 0 reads the host's cancel flag (issued
+            // before the gather, used after it)
+            int cz = 0;
+            if (lane == 0 && a.cancel && (poll++ & 15) == 0) cz = *(const volatile int *)a.cancel;
             const int m = gather_items<L1SMEM, true>(a, B, s1, s2, s3, lane, B.mtarget, fd_nyz, fd_nz, sD + D_STALE);
             const bool bg0 = lane < m && B.r2[lane] > 1, bg1 = lane + 32 < m && B.r2[lane + 32] > 1;
             const unsigned b0 = __ballot_sync(0xffffffffu, bg0), b1 = __ballot_sync(0xffffffffu, bg1);
@@ -1166,7 +1178,7 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
             if (lane == 0) {
                 B.m = m;
                 B.big = big;
-                B.stop = m == 0 ? 1 : 0;
+                B.stop = m == 0 ? 1 : (cz ? 5 : 0);   // 5: cancelled, before this batch commits
                 if (PROF) sD[D_GATHER] += tclk<PROF>() - t0;
             }
         }
@@ -1708,7 +1720,9 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
         for (int q = 2; q < kNOut; q++)
             if (q != kFirst1Slot) a.out[q] = sD[q];
         a.out[0] = k;
-        a.out[1] = (B.stop == 2) ? IBIP_ERR_STEP_LIMIT : (B.stop == 3 ? IBIP_ERR_BOUNDS : IBIP_OK);
+        a.out[1] = B.stop == 2 ? IBIP_ERR_STEP_LIMIT
+                   : B.stop == 3 ? IBIP_ERR_BOUNDS
+                   : B.stop == 5 ? IBIP_ERR_CANCELLED : IBIP_OK;
     }
 }
 
@@ -1849,6 +1863,7 @@ Inv make_inv(const int32_t *dt2, ibip_dims d, int inlet, int64_t max_steps, int3
     a.isq_n = std::min(maxd + 1, 16384);
     a.trace = nullptr;
     a.trace_cap = 0;
+    a.cancel = nullptr;
     return a;
 }
 
@@ -1975,6 +1990,7 @@ int ibip_invade_run(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, i
     if (st) return st;
     a.trace = (int4 *)ctx->trace;
     a.trace_cap = ctx->trace ? ctx->trace_cap : 0;
+    a.cancel = ctx->d_cancel;
     ibip_prof_end(ctx, IBIP_K_RANK);
     const FastDiv fd_nyz = make_fastdiv((uint32_t)d.ny * (uint32_t)d.nz), fd_nz = make_fastdiv((uint32_t)d.nz);
     const bool l1smem = a.NL1 <= kSmemL1Max;
@@ -2005,6 +2021,7 @@ int ibip_invade_run(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, i
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return ibip_cuda_status(e);
     for (int i = 0; i < kNOut; i++) h_out[i] = ho[i];
+    if (h_out[1] == IBIP_ERR_CANCELLED && ctx->h_cancel) *ctx->h_cancel = 0;   // the request is served
     return IBIP_OK;
 }
 
@@ -2143,6 +2160,7 @@ int ibip_invade_batch_run(ibip_ctx *ctx, int n, IbipBatchItem *it, IbipBatchEarl
         InvJob J;
         J.a = make_inv(it[j].dt2, it[j].d, it[j].inlet, it[j].max_steps, it[j].seq, it[j].step_r2, it[j].step_centre,
                        it[j].cap, maxd[j], npore[j], mem, nullptr, 0, 0);
+        J.a.cancel = ctx->d_cancel;
         cudaMemsetAsync(mem.fb, 0, fb_words(J.a) * sizeof(u64), s);
         J.fd_nyz = make_fastdiv((uint32_t)it[j].d.ny * (uint32_t)it[j].d.nz);
         J.fd_nz = make_fastdiv((uint32_t)it[j].d.nz);

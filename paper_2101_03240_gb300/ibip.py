@@ -22,6 +22,7 @@ ERR_CUDA = -2
 ERR_OOM = -3
 ERR_STEP_LIMIT = -4
 ERR_NOT_CONVERGED = -5
+ERR_CANCELLED = -6
 
 FACES = {"x0": 0, "x1": 1, "y0": 2, "y1": 3, "z0": 4, "z1": 5}
 
@@ -84,6 +85,8 @@ def _lib():
                 "ibip_invade_stats": (C.c_int, [P, C.POINTER(i64), C.c_int]),
                 "ibip_invade_trace": (C.c_int, [P, P, i64]),
                 "ibip_set_autotune": (C.c_int, [P, C.c_int, C.c_char_p]),
+                "ibip_cancel": (C.c_int, [P, C.c_int]),
+                "ibip_debug_fail_alloc": (C.c_int, [P, C.c_int]),
                 "ibip_set_edt_tiles": (C.c_int, [P, C.c_int, C.c_int]),
                 "ibip_edt_tiles": (C.c_int, [P, Dims, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
                 "ibip_profile_read": (C.c_int, [P, C.c_int, C.POINTER(dbl), C.POINTER(i64)]),
@@ -224,6 +227,19 @@ class Context:
                 "span_cycles", "span_ns", "shell_units", "shell_listed", "removed", "single_batches",
                 "tiny_merged", "tiny_merge_cycles", "gather_rounds", "gathers"]
         return dict(zip(keys, [int(x) for x in a]))
+
+    def cancel(self, on: bool = True):
+        """Request (or withdraw) cancellation of this context's invasion
+        (see ibip_cancel); callable from another thread."""
+        st = _lib().ibip_cancel(self._h, int(bool(on)))
+        if st != OK:
+            raise IbipError("ibip_cancel", st)
+
+    def debug_fail_alloc(self, nth: int):
+        """Test hook: fail the nth scratch allocation from now (0: off)."""
+        st = _lib().ibip_debug_fail_alloc(self._h, int(nth))
+        if st != OK:
+            raise IbipError("ibip_debug_fail_alloc", st)
 
     def set_autotune(self, on: bool, cache_path: str | None = None):
         """Tile-shape autotuning of the EDT (see ibip_set_autotune)."""
