@@ -57,7 +57,8 @@ typedef enum {
     IBIP_ERR_STEP_LIMIT = -4,    /* invasion stopped at max_steps with candidates left */
     IBIP_ERR_NOT_CONVERGED = -5, /* propagation hit its round limit */
     IBIP_ERR_CANCELLED = -6,     /* the invasion stopped at a cancel request (ibip_cancel) */
-    IBIP_ERR_BOUNDS = -7,        /* a device-side index check failed */
+    IBIP_ERR_BOUNDS = -7,        /* a device-side index check failed (progress guard; any
+                                    index of the invasion loop in a build with IBIP_CHECKED) */
     IBIP_ERR_TOO_LARGE = -8      /* image larger than ibip_edt_noalloc's fixed scratch */
 } ibip_status;
 

@@ -14,7 +14,11 @@ from concurrent.futures import ThreadPoolExecutor
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
-OUT = os.path.join(HERE, "_build")
+# IBIP_CHECKED=1 selects the checked build (every global index of the
+# invasion loop compared with its array's extent; a violation is reported
+# as IBIP_ERR_BOUNDS, nothing traps), built beside the normal one.
+CHECKED = os.environ.get("IBIP_CHECKED", "") == "1"
+OUT = os.path.join(HERE, "_build_checked" if CHECKED else "_build")
 LIB = os.path.join(OUT, "libibip.so")
 ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
@@ -40,7 +44,7 @@ def _compile(src: str, extra: list[str], verbose: bool) -> str:
     obj = os.path.join(OUT, os.path.basename(src) + ".o")
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(src), _deps_mtime()):
         return obj
-    cmd = [nvcc(), *ARCH, *FLAGS, *extra, "-c", src, "-o", obj + ".tmp"]
+    cmd = [nvcc(), *ARCH, *FLAGS, *(["-DIBIP_CHECKED"] if CHECKED else []), *extra, "-c", src, "-o", obj + ".tmp"]
     if verbose:
         print(" ".join(cmd), flush=True)
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -61,7 +65,7 @@ def build(verbose: bool = False, extra: list[str] | None = None) -> str:
     if os.path.exists(LIB) and os.path.getmtime(LIB) >= max(os.path.getmtime(o) for o in objs):
         return LIB
     cmd = [nvcc(), *ARCH, "-shared", "-cudart", "shared", "-o", LIB + ".tmp", *objs,
-           "-Xlinker", "-rpath,/usr/local/cuda/lib64"]
+           "-ldl", "-Xlinker", "-rpath,/usr/local/cuda/lib64"]
     if verbose:
         print(" ".join(cmd), flush=True)
     r = subprocess.run(cmd, capture_output=True, text=True)

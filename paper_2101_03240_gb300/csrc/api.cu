@@ -7,6 +7,18 @@
 #include <vector>
 
 #include "common.cuh"
+#include <nvtx3/nvToolsExt.h>
+
+namespace {
+// An NVTX range around each compute call of the ABI (visible to nsys and to
+// ncu --nvtx; the calls cost nothing when no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+}  // namespace
 
 int ibip_invade_run(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, int64_t max_steps,
                     int32_t *seq, int32_t *step_r2, int32_t *step_centre, int64_t cap, int64_t *h_out,
@@ -405,6 +417,7 @@ int ibip_profile_read(ibip_ctx *ctx, int cls, double *h_ms, int64_t *h_spans)
 
 int ibip_edt(ibip_ctx *ctx, const uint8_t *image, ibip_dims dims, int32_t *dt2)
 {
+    NvtxRange nvtx_range("ibip_edt");
     if (!ctx || !image || !dt2 || !dims_ok(dims)) return IBIP_ERR_ARG;
     DeviceGuard g(ctx->device);
     return ibip_edt_launch(ctx, image, dims, dt2);
@@ -414,6 +427,7 @@ int ibip_invade(ibip_ctx *ctx, const uint8_t *image, const int32_t *dt2, ibip_di
                 int64_t max_steps, int32_t *seq, int32_t *step_r2, int32_t *step_centre, int64_t capacity_steps,
                 int64_t *h_n_steps)
 {
+    NvtxRange nvtx_range("ibip_invade");
     if (!ctx || !image || !seq || !h_n_steps || !dims_ok(dims) || !face_ok(inlet) || max_steps < 0 ||
         capacity_steps < 0 || (capacity_steps > 0 && !step_r2))
         return IBIP_ERR_ARG;
@@ -441,6 +455,7 @@ int ibip_invade_ex(ibip_ctx *ctx, const uint8_t *image, const int32_t *dt2, ibip
                    const uint8_t *inlet_mask, int resume, int64_t max_steps, int32_t *seq, int32_t *step_r2,
                    int32_t *step_centre, int64_t capacity_steps, int64_t *h_n_steps)
 {
+    NvtxRange nvtx_range("ibip_invade_ex");
     if (!ctx || !image || !seq || !h_n_steps || !dims_ok(dims) || (!inlet_mask && !face_ok(inlet)) ||
         max_steps < 0 || capacity_steps < 0 || (capacity_steps > 0 && !step_r2) || (resume != 0 && resume != 1))
         return IBIP_ERR_ARG;
@@ -469,6 +484,7 @@ int ibip_invade_literal(ibip_ctx *ctx, const uint8_t *image, const int32_t *dt2,
                         int64_t max_steps, int32_t *seq, int32_t *cstep, int32_t *step_r2, int32_t *step_count,
                         int64_t capacity_steps, int64_t *h_n_steps)
 {
+    NvtxRange nvtx_range("ibip_invade_literal");
     if (!ctx || !image || !seq || !cstep || !h_n_steps || !dims_ok(dims) || !face_ok(inlet) || max_steps < 0 ||
         capacity_steps < 0 || (capacity_steps > 0 && (!step_r2 || !step_count)))
         return IBIP_ERR_ARG;
@@ -494,6 +510,7 @@ int ibip_invade_literal(ibip_ctx *ctx, const uint8_t *image, const int32_t *dt2,
 int ibip_trapping(ibip_ctx *ctx, const int32_t *seq, ibip_dims dims, int outlet, int rerank, uint8_t *trapped,
                   int32_t *seq_out)
 {
+    NvtxRange nvtx_range("ibip_trapping");
     if (!ctx || !seq || !trapped || !dims_ok(dims) || !face_ok(outlet)) return IBIP_ERR_ARG;
     DeviceGuard g(ctx->device);
     int32_t *M = (int32_t *)ibip_scratch(ctx, SC_MM, (size_t)nvox(dims) * sizeof(int32_t));
@@ -509,6 +526,7 @@ int ibip_trapping_ex(ibip_ctx *ctx, const int32_t *seq, ibip_dims dims, int outl
                      int32_t *seq_out, const int32_t *step_r2, int64_t n_steps, int32_t *step_r2_out,
                      int64_t *h_n_steps_out)
 {
+    NvtxRange nvtx_range("ibip_trapping_ex");
     if (!ctx || !seq || !trapped || !seq_out || !h_n_steps_out || !dims_ok(dims) || !face_ok(outlet) ||
         n_steps < 0 || (n_steps > 0 && (!step_r2 || !step_r2_out)))
         return IBIP_ERR_ARG;
@@ -525,6 +543,7 @@ int ibip_trapping_ex(ibip_ctx *ctx, const int32_t *seq, ibip_dims dims, int outl
 int ibip_size_image(ibip_ctx *ctx, const int32_t *seq, ibip_dims dims, const int32_t *step_r2, int64_t n_steps,
                     int32_t *r2_image)
 {
+    NvtxRange nvtx_range("ibip_size_image");
     if (!ctx || !seq || !r2_image || !dims_ok(dims) || n_steps < 0 || (n_steps > 0 && !step_r2))
         return IBIP_ERR_ARG;
     DeviceGuard g(ctx->device);
@@ -534,6 +553,7 @@ int ibip_size_image(ibip_ctx *ctx, const int32_t *seq, ibip_dims dims, const int
 int ibip_morph_drainage(ibip_ctx *ctx, const uint8_t *image, const int32_t *dt2, ibip_dims dims, int inlet,
                         const int32_t *h_r2_levels, int32_t n_levels, int32_t *level, int64_t *h_counts)
 {
+    NvtxRange nvtx_range("ibip_morph_drainage");
     if (!ctx || !image || !dt2 || !level || !h_counts || !dims_ok(dims) || !face_ok(inlet) || n_levels < 0 ||
         n_levels > 8192 ||
         (n_levels > 0 && !h_r2_levels))
@@ -578,6 +598,7 @@ int ibip_morph_drainage(ibip_ctx *ctx, const uint8_t *image, const int32_t *dt2,
 
 int ibip_invade_batched(ibip_ctx *ctx, int32_t n, ibip_job *jobs)
 {
+    NvtxRange nvtx_range("ibip_invade_batched");
     if (!ctx || !jobs || n < 1 || n > kMaxBatch) return IBIP_ERR_ARG;
     int64_t need_dt2 = 0;
     for (int j = 0; j < n; j++) {
@@ -657,6 +678,7 @@ int ibip_invade_batched(ibip_ctx *ctx, int32_t n, ibip_job *jobs)
 int ibip_equal_saturation(ibip_ctx *ctx, const int32_t *seq, const int32_t *level, ibip_dims dims,
                           int64_t n_steps, int32_t n_levels, int64_t *h_steps, int64_t *h_diff, int64_t *h_count)
 {
+    NvtxRange nvtx_range("ibip_equal_saturation");
     if (!ctx || !seq || !level || !h_diff || !dims_ok(dims) || n_steps < 0 || n_steps >= (1ll << 31) ||
         n_levels < 1 || n_levels > 254)
         return IBIP_ERR_ARG;
@@ -668,6 +690,7 @@ int ibip_pc_curve(ibip_ctx *ctx, const int32_t *seq, ibip_dims dims, const int32
                   double voxel_m, double sigma, double theta_deg, float *sat_per_step, float *pc_per_step,
                   float *sat_image)
 {
+    NvtxRange nvtx_range("ibip_pc_curve");
     if (!ctx || !seq || !dims_ok(dims) || n_steps < 0 || n_steps >= (1ll << 31) ||
         (n_steps > 0 && (!step_r2 || !sat_per_step || !pc_per_step)) || (sat_image && !sat_per_step) ||
         !(voxel_m > 0.0))

@@ -380,6 +380,59 @@ struct Inv {
     int64_t trace_cap;     // records that fit in trace
 };
 
+// Global accesses of the invasion loop.  In a checked build (IBIP_CHECKED)
+// each index is compared with its array's extent first: an index outside
+// it is counted in out[kErrSlot] and the access is skipped (a load gives a
+// neutral value), and the call returns IBIP_ERR_BOUNDS; nothing traps.  In
+// the normal build they are the plain accesses.
+constexpr int kErrSlot = 34;
+__device__ __forceinline__ bool in_range(const Inv &a, int64_t i, int64_t n)
+{
+#ifdef IBIP_CHECKED
+    if (i >= 0 && i < n) return true;
+    atomicAdd((unsigned long long *)(a.out + kErrSlot), 1ull);
+    return false;
+#else
+    (void)a; (void)i; (void)n;
+    return true;
+#endif
+}
+__device__ __forceinline__ int64_t n_vox(const Inv &a) { return (int64_t)a.nx * a.ny * a.nz; }
+__device__ __forceinline__ int64_t n_words(const Inv &a) { return (int64_t)a.nx * a.ny * a.NW; }
+__device__ __forceinline__ void seq_put(const Inv &a, int64_t v, int32_t label)
+{
+    if (in_range(a, v, n_vox(a))) a.seq[v] = label;
+}
+__device__ __forceinline__ int rank_at(const Inv &a, int64_t v)
+{
+    return in_range(a, v, n_vox(a)) ? __ldg(a.rank + v) : 0;
+}
+__device__ __forceinline__ void fb0_set(const Inv &a, int r)
+{
+    if (in_range(a, r >> 6, a.NL0)) atomicOr(a.fb0 + (r >> 6), 1ull << (r & 63));
+}
+__device__ __forceinline__ void fb0_clear(const Inv &a, int r)
+{
+    if (in_range(a, r >> 6, a.NL0)) atomicAnd(a.fb0 + (r >> 6), ~(1ull << (r & 63)));
+}
+__device__ __forceinline__ uint32_t plane_ld(const Inv &a, const uint32_t *pl, int64_t w)
+{
+    return in_range(a, w, n_words(a)) ? ldcg32(pl + w) : 0u;
+}
+__device__ __forceinline__ void plane_and(const Inv &a, uint32_t *pl, int64_t w, uint32_t m)
+{
+    if (in_range(a, w, n_words(a))) atomicAnd(pl + w, m);
+}
+// returns the word before the OR (all ones when out of range: nothing new)
+__device__ __forceinline__ uint32_t plane_or(const Inv &a, uint32_t *pl, int64_t w, uint32_t m)
+{
+    return in_range(a, w, n_words(a)) ? atomicOr(pl + w, m) : 0xffffffffu;
+}
+__device__ __forceinline__ void list_put(const Inv &a, int *g, int64_t i, int v)
+{
+    if (in_range(a, i, a.npore)) g[i] = v;
+}
+
 __global__ void k_seq_init(const int32_t *__restrict__ dt2, int64_t N, int32_t *seq)
 {
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (int64_t)gridDim.x * blockDim.x)
@@ -415,7 +468,7 @@ __device__ void plane_word(const Inv &a, int64_t w)
         if (cand) {
             ad |= 1u << b;
             int r = a.rank[v];
-            atomicOr(a.fb0 + (r >> 6), 1ull << (r & 63));
+            fb0_set(a, r);
             atomicOr(a.fb1 + (r >> 12), 1ull << ((r >> 6) & 63));
             atomicOr(a.fb2 + (r >> 18), 1ull << ((r >> 12) & 63));
             atomicOr(a.fb3 + (r >> 24), 1ull << ((r >> 18) & 63));
@@ -651,8 +704,8 @@ __device__ __forceinline__ unsigned nb6_candidates(const Inv &a, const Nb6 &n)
     uint32_t av[6], ad[6];
 #pragma unroll
     for (int q = 0; q < 6; q++) {
-        av[q] = n.ok[q] ? ldcg32(a.avail + n.word[q]) : 0u;
-        ad[q] = n.ok[q] ? ldcg32(a.added + n.word[q]) : 0u;
+        av[q] = n.ok[q] ? plane_ld(a, a.avail, n.word[q]) : 0u;
+        ad[q] = n.ok[q] ? plane_ld(a, a.added, n.word[q]) : 0u;
     }
     unsigned c = 0;
 #pragma unroll
@@ -897,20 +950,20 @@ __device__ __forceinline__ void commit_single(const Inv &a, const Batch &B, u64 
         const int64_t vb = row * a.nz;
         for (int w = za >> 5; w <= (zb >> 5); w++) {
             const int64_t rw = row * a.NW + w;
-            const uint32_t av = ldcg32(a.avail + rw), ad = ldcg32(a.added + rw);
+            const uint32_t av = plane_ld(a, a.avail, rw), ad = plane_ld(a, a.added, rw);
             const uint32_t ballm = r0 <= r1 ? span_mask(w, r0, r1) : 0u;
             const uint32_t newly = av & ballm;
             const uint32_t cand = av & ~ad & span_mask(w, za, zb) & ~ballm;
-            if (newly) atomicAnd(a.avail + rw, ~newly);
-            if (cand) atomicOr(a.added + rw, cand);
-            for (uint32_t n2 = newly; n2; n2 &= n2 - 1) a.seq[vb + w * 32 + __ffs(n2) - 1] = label;
+            if (newly) plane_and(a, a.avail, rw, ~newly);
+            if (cand) plane_or(a, a.added, rw, cand);
+            for (uint32_t n2 = newly; n2; n2 &= n2 - 1) seq_put(a, vb + w * 32 + __ffs(n2) - 1, label);
             for (uint32_t g = newly & ad; g; g &= g - 1) {
-                const int r = __ldg(a.rank + vb + w * 32 + __ffs(g) - 1);
-                atomicAnd(a.fb0 + (r >> 6), ~(1ull << (r & 63)));
+                const int r = rank_at(a, vb + w * 32 + __ffs(g) - 1);
+                fb0_clear(a, r);
             }
             for (uint32_t c = cand; c; c &= c - 1) {
-                const int r = __ldg(a.rank + vb + w * 32 + __ffs(c) - 1);
-                atomicOr(a.fb0 + (r >> 6), 1ull << (r & 63));
+                const int r = rank_at(a, vb + w * 32 + __ffs(c) - 1);
+                fb0_set(a, r);
                 flag_rank(s1, s2, s3, (int *)&B.cur1, r);
             }
         }
@@ -1056,7 +1109,7 @@ __device__ void tiny_loop(const Inv &a, Batch &B, u64 *s1, u64 *s2, u64 *s3, con
             int best = INT_MAX;
 #pragma unroll
             for (int q = 0; q < 6; q++) {
-                rr[q] = ((cand >> q) & 1) ? __ldg(a.rank + nb.v[q]) : INT_MAX;
+                rr[q] = ((cand >> q) & 1) ? rank_at(a, nb.v[q]) : INT_MAX;
                 best = min(best, rr[q]);
             }
             if (cand) jl = max(j + 1, lower_rank(B, m, best));
@@ -1069,10 +1122,10 @@ __device__ void tiny_loop(const Inv &a, Batch &B, u64 *s1, u64 *s2, u64 *s3, con
         const int J = B.J;
         if (j < J) {
             const int x = B.x[j], y = B.y[j], z = B.z[j];
-            atomicAnd(a.avail + ((int64_t)x * a.ny + y) * a.NW + (z >> 5), ~(1u << (z & 31)));
-            a.seq[B.idx[j]] = (int32_t)(k + 1 + j);
+            plane_and(a, a.avail, ((int64_t)x * a.ny + y) * a.NW + (z >> 5), ~(1u << (z & 31)));
+            seq_put(a, B.idx[j], (int32_t)(k + 1 + j));
             const int r = B.rank[j];
-            atomicAnd(a.fb0 + (r >> 6), ~(1ull << (r & 63)));
+            fb0_clear(a, r);
             if (k + j < a.cap) {
                 a.step_r2[k + j] = 1;
                 if (a.step_centre) a.step_centre[k + j] = B.idx[j];
@@ -1080,7 +1133,7 @@ __device__ void tiny_loop(const Inv &a, Batch &B, u64 *s1, u64 *s2, u64 *s3, con
             uint32_t got[6];
 #pragma unroll
             for (int q = 0; q < 6; q++)
-                got[q] = ((cand >> q) & 1) ? atomicOr(a.added + nb.word[q], nb.bit[q]) : nb.bit[q];
+                got[q] = ((cand >> q) & 1) ? plane_or(a, a.added, nb.word[q], nb.bit[q]) : nb.bit[q];
             unsigned fr = 0;
 #pragma unroll
             for (int q = 0; q < 6; q++)
@@ -1091,7 +1144,7 @@ __device__ void tiny_loop(const Inv &a, Batch &B, u64 *s1, u64 *s2, u64 *s3, con
                 for (int q = 0; q < 6; q++) {
                     if (!((fr >> q) & 1)) continue;
                     const int rq = rr[q];
-                    atomicOr(a.fb0 + (rq >> 6), 1ull << (rq & 63));
+                    fb0_set(a, rq);
                     flag_rank(s1, s2, s3, &B.cur1, rq);
                     if (slot < kNewCap) { sNr[slot] = rq; sNv[slot] = nb.v[q]; }
                     else B.novf = 1;
@@ -1137,6 +1190,7 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
     int *isq_t = (int *)(s3 + a.NL3);
     for (int e = tid; e < a.isq_n; e += kNT) isq_t[e] = d_isqrt(e);
     if (tid == 0) {
+        a.out[kErrSlot] = 0;
         B.mtarget = kM;
         B.cur1 = 0;
         B.upre[0] = 0;
@@ -1446,7 +1500,7 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
                             sLAi[slot] = (unsigned char)i;
                         } else {
                             B.ovf = 1;
-                            const int ru = __ldg(a.rank + nb.v[q]);
+                            const int ru = rank_at(a, nb.v[q]);
                             atomicMin(&B.J, max(i + 1, lower_rank(B, m, ru)));
                         }
                         slot++;
@@ -1457,7 +1511,7 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
                 if (!shell_row(a, B, i, x, y, za, zb, ra, rbz)) return true;
                 const int64_t row = (int64_t)x * a.ny + y;
                 for (int w = za >> 5; w <= (zb >> 5); w++) {
-                    uint32_t cand = ldcg32(a.avail + row * a.NW + w) & ~ldcg32(a.added + row * a.NW + w) &
+                    uint32_t cand = plane_ld(a, a.avail, row * a.NW + w) & ~plane_ld(a, a.added, row * a.NW + w) &
                                     span_mask(w, za, zb) & ~span_mask(w, ra, rbz);
                     if (!cand) continue;
                     for (int slot = atomicAdd(&B.nA, __popc(cand)); cand; cand &= cand - 1, slot++) {
@@ -1467,7 +1521,7 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
                             sLAi[slot] = (unsigned char)i;
                         } else {
                             B.ovf = 1;
-                            const int ru = __ldg(a.rank + row * a.nz + z);
+                            const int ru = rank_at(a, row * a.nz + z);
                             atomicMin(&B.J, max(i + 1, lower_rank(B, m, ru)));
                         }
                     }
@@ -1487,7 +1541,7 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
                 for (int q = 0; q < 4; q++) {
                     const int e = e0 + q * kNT;
                     it[q] = e < n ? sLAi[e] : kM;
-                    ru[q] = it[q] < jl ? __ldg(a.rank + sLA[e]) : 0;
+                    ru[q] = it[q] < jl ? rank_at(a, sLA[e]) : 0;
                 }
 #pragma unroll
                 for (int q = 0; q < 4; q++) {
@@ -1522,10 +1576,10 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
                     // lower ball covers: it owns its voxel and its rank is known
                     const int z = B.z[i];
                     const int64_t w = ((int64_t)B.x[i] * a.ny + B.y[i]) * a.NW + (z >> 5);
-                    atomicAnd(a.avail + w, ~(1u << (z & 31)));
-                    a.seq[B.idx[i]] = (int32_t)(k1 + B.step[i]);
+                    plane_and(a, a.avail, w, ~(1u << (z & 31)));
+                    seq_put(a, B.idx[i], (int32_t)(k1 + B.step[i]));
                     const int r = B.rank[i];
-                    atomicAnd(a.fb0 + (r >> 6), ~(1ull << (r & 63)));
+                    fb0_clear(a, r);
                     return true;
                 }
                 int lo, hi;
@@ -1543,16 +1597,16 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
                     }
                     if (!own) continue;
                     // `added` does not change during this stage: load it with `avail`
-                    const uint32_t av = ldcg32(a.avail + rb + w), ad = ldcg32(a.added + rb + w);
+                    const uint32_t av = plane_ld(a, a.avail, rb + w), ad = plane_ld(a, a.added, rb + w);
                     const uint32_t newly = av & own;
                     if (!newly) continue;
-                    atomicAnd(a.avail + rb + w, ~newly);
+                    plane_and(a, a.avail, rb + w, ~newly);
                     uint32_t gone = newly & ad;
-                    for (uint32_t n2 = newly; n2; n2 &= n2 - 1) a.seq[vb + w * 32 + __ffs(n2) - 1] = label;
+                    for (uint32_t n2 = newly; n2; n2 &= n2 - 1) seq_put(a, vb + w * 32 + __ffs(n2) - 1, label);
                     if (!gone) continue;
                     for (int slot = atomicAdd(&B.nC, __popc(gone)); gone; gone &= gone - 1, slot++) {
                         const int v = (int)(vb + w * 32 + __ffs(gone) - 1);
-                        if (slot < kList) sLC[slot] = v; else gC[slot - kList] = v;
+                        if (slot < kList) sLC[slot] = v; else list_put(a, gC, slot - kList, v);
                     }
                 }
                 return true;
@@ -1593,27 +1647,27 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
                             wd[q] = (int64_t)row * a.NW + (z >> 5);
                             bt[q] = 1u << (z & 31);
                             rr[q] = sLAr[e];
-                            got[q] = ldcg32(a.avail + wd[q]);
+                            got[q] = plane_ld(a, a.avail, wd[q]);
                         }
                     } else if (e < tot) {
                         const int f = e - n;
-                        rr[q] = __ldg(a.rank + (f < kList ? sLC[f] : gC[f - kList]));
+                        rr[q] = rank_at(a, (f < kList ? sLC[f] : gC[f - kList]));
                     }
                 }
 #pragma unroll
                 for (int q = 0; q < 4; q++) {
                     if (wd[q] >= 0) {
                         // still uninvaded after the stamping: queue it once
-                        got[q] = (got[q] & bt[q]) && !(atomicOr(a.added + wd[q], bt[q]) & bt[q]);
+                        got[q] = (got[q] & bt[q]) && !(plane_or(a, a.added, wd[q], bt[q]) & bt[q]);
                     } else if (rr[q] >= 0) {
-                        atomicAnd(a.fb0 + (rr[q] >> 6), ~(1ull << (rr[q] & 63)));
+                        fb0_clear(a, rr[q]);
                     }
                 }
 #pragma unroll
                 for (int q = 0; q < 4; q++) {
                     if (wd[q] < 0 || !got[q]) continue;
                     const int r = rr[q];
-                    atomicOr(a.fb0 + (r >> 6), 1ull << (r & 63));
+                    fb0_set(a, r);
                     flag_rank(s1, s2, s3, &B.cur1, r);
                 }
             }
@@ -1631,15 +1685,15 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
 #pragma unroll
                     for (int q = 0; q < 6; q++)
                         if ((c >> q) & 1)
-                            if (!(atomicOr(a.added + nb.word[q], nb.bit[q]) & nb.bit[q])) fr |= 1u << q;
+                            if (!(plane_or(a, a.added, nb.word[q], nb.bit[q]) & nb.bit[q])) fr |= 1u << q;
                     int rr[6];
 #pragma unroll
-                    for (int q = 0; q < 6; q++) rr[q] = ((fr >> q) & 1) ? __ldg(a.rank + nb.v[q]) : -1;
+                    for (int q = 0; q < 6; q++) rr[q] = ((fr >> q) & 1) ? rank_at(a, nb.v[q]) : -1;
 #pragma unroll
                     for (int q = 0; q < 6; q++) {
                         const int r = rr[q];
                         if (r < 0) continue;
-                        atomicOr(a.fb0 + (r >> 6), 1ull << (r & 63));
+                        fb0_set(a, r);
                         flag_rank(s1, s2, s3, &B.cur1, r);
                     }
                     return true;
@@ -1648,14 +1702,14 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
                 if (!shell_row(a, B, i, x, y, za, zb, ra, rbz)) return true;
                 const int64_t row = (int64_t)x * a.ny + y;
                 for (int w = za >> 5; w <= (zb >> 5); w++) {
-                    const uint32_t cand = ldcg32(a.avail + row * a.NW + w) & ~ldcg32(a.added + row * a.NW + w) &
+                    const uint32_t cand = plane_ld(a, a.avail, row * a.NW + w) & ~plane_ld(a, a.added, row * a.NW + w) &
                                           span_mask(w, za, zb) & ~span_mask(w, ra, rbz);
                     if (!cand) continue;
-                    uint32_t fresh = cand & ~atomicOr(a.added + row * a.NW + w, cand);
+                    uint32_t fresh = cand & ~plane_or(a, a.added, row * a.NW + w, cand);
                     for (; fresh; fresh &= fresh - 1) {
                         const int v = (int)(row * a.nz + w * 32 + __ffs(fresh) - 1);
                         const int slot = atomicAdd(&B.nD, 1);
-                        if (slot < kList) sLD[slot] = v; else gD[slot - kList] = v;
+                        if (slot < kList) sLD[slot] = v; else list_put(a, gD, slot - kList, v);
                     }
                 }
                 return true;
@@ -1668,13 +1722,13 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
             for (int e = tid; e < nC + nD; e += kNT) {
                 if (e < nC) {
                     int v = e < kList ? sLC[e] : gC[e - kList];
-                    int r = __ldg(a.rank + v);
-                    atomicAnd(a.fb0 + (r >> 6), ~(1ull << (r & 63)));
+                    int r = rank_at(a, v);
+                    fb0_clear(a, r);
                 } else {
                     int f = e - nC;
                     int v = f < kList ? sLD[f] : gD[f - kList];
-                    int r = __ldg(a.rank + v);
-                    atomicOr(a.fb0 + (r >> 6), 1ull << (r & 63));
+                    int r = rank_at(a, v);
+                    fb0_set(a, r);
                     flag_rank(s1, s2, s3, &B.cur1, r);
                 }
             }
@@ -1718,11 +1772,12 @@ __device__ __forceinline__ void invade_body(const Inv &a, const FastDiv &fd_nyz,
         sD[D_SPAN_NS] = (long long)(global_ns() - span_t0);
         sD[D_B2] = sD[D_BOUND] - sD[D_B1];
         for (int q = 2; q < kNOut; q++)
-            if (q != kFirst1Slot) a.out[q] = sD[q];
+            if (q != kFirst1Slot && q != kErrSlot) a.out[q] = sD[q];
         a.out[0] = k;
         a.out[1] = B.stop == 2 ? IBIP_ERR_STEP_LIMIT
                    : B.stop == 3 ? IBIP_ERR_BOUNDS
                    : B.stop == 5 ? IBIP_ERR_CANCELLED : IBIP_OK;
+        if (*(volatile int64_t *)(a.out + kErrSlot)) a.out[1] = IBIP_ERR_BOUNDS;   // checked build only
     }
 }
 
