@@ -405,7 +405,8 @@ IBIP_API int ibip_profile_read(ibip_ctx *ctx, int cls, double *h_ms, int64_t *h_
  *   30-32 rounds, tile activations and relaxation sweeps of the context's
  *   last widest-path propagation (trapping or the opening's trim,
  *   one-launch form),
- *   34 unused, 35 rank of the first voxel with the smallest dt2,
+ *   34 out-of-range accesses counted by a checked build (IBIP_CHECKED),
+ *   35 rank of the first voxel with the smallest dt2,
  *   36 batches seen by the trace (ibip_invade_trace; counted beyond its
  *   capacity), 37 the kernel's span in SM cycles, 38 the same span in
  *   nanoseconds of the global timer (their ratio is the SM clock),

@@ -223,7 +223,7 @@ class Context:
                 "sel_gather", "sel_items", "sel_pairs", "sel_tail", "small_select", "small_bound", "small_commit",
                 "tiny_iterations", "tiny_steps", "cycles_tiny", "s3_cont", "s3_prefix", "bound_list",
                 "bound_ranks", "commit_stamp", "commit_queue", "tiny_gather", "tiny_bound", "mm_rounds",
-                "mm_activations", "mm_sweeps", "tiny_commit", "unused", "first_unit_rank", "trace_batches",
+                "mm_activations", "mm_sweeps", "tiny_commit", "bounds_violations", "first_unit_rank", "trace_batches",
                 "span_cycles", "span_ns", "shell_units", "shell_listed", "removed", "single_batches",
                 "tiny_merged", "tiny_merge_cycles", "gather_rounds", "gathers"]
         return dict(zip(keys, [int(x) for x in a]))
