@@ -246,6 +246,7 @@ def run_batch(args, rank, world):
                      "peak_source": "measured" if pk else "fallback",
                      "note": "one latency-bound CTA per image; bytes are the algorithmic minimum"},
         "kernels": kinfo, "clocks": ck,
+        "gpu": torch.cuda.get_device_name(dev), "host_cores": os.cpu_count(), "seed": 4,
     }
     if world == 1 and not args.no_cpu_baseline:
         import oracle as O
@@ -399,6 +400,7 @@ def run_serve(args, rank, world):
                 "d2h_bytes_per_step": int(4 * nvox_total)},
         "gpu_launches": int(launches),
         "clocks": ck,
+        "gpu": torch.cuda.get_device_name(dev), "host_cores": os.cpu_count(), "seed": 5,
     }
     if world == 1 and not args.no_cpu_baseline:
         import oracle as O
@@ -651,6 +653,11 @@ def run_ours(args, rank, world):
         "kernels": kinfo,
         "clocks": ck,
         "wall_s_timed": t_wall,
+        "gpu": torch.cuda.get_device_name(dev),
+        "host_cores": os.cpu_count(),
+        "seed": {"spheres200": 2, "blobs48": 1, "blobs512": 3}.get(w.name),
+        "paper_context": "about 5 steps/s for the first 3,000 steps of a 250^3 blob image on a laptop CPU "
+                         "(Python/SciPy, Fig. 4 caption); context, not a target",
     }
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args, w, levels)
