@@ -151,6 +151,16 @@ bool ibip_job_valid(const ibip_job &J)
            ((J.sat_per_step != nullptr) == (J.pc_per_step != nullptr)) && (!J.sat_per_step || J.voxel_m > 0.0);
 }
 
+// The invasion's counters become the context's, except entries 30-32,
+// which belong to the last widest-path propagation.
+void keep_invade_stats(ibip_ctx *ctx, const int64_t *out)
+{
+    int64_t mm[3];
+    memcpy(mm, ctx->inv_stats + 30, sizeof(mm));
+    memcpy(ctx->inv_stats, out, kInvStats * sizeof(int64_t));
+    memcpy(ctx->inv_stats + 30, mm, sizeof(mm));
+}
+
 int ibip_run_job(ibip_ctx *ctx, ibip_job &J)
 {
     J.n_steps = 0;
@@ -444,7 +454,7 @@ int ibip_invade(ibip_ctx *ctx, const uint8_t *image, const int32_t *dt2, ibip_di
     int64_t out[kInvStats] = {0};
     int st = ibip_invade_run(ctx, d, dims, inlet, max_steps, seq, step_r2, step_centre, capacity_steps, out);
     if (st) return st;
-    memcpy(ctx->inv_stats, out, sizeof(out));
+    keep_invade_stats(ctx, out);
     *h_n_steps = out[0];
     if (out[1] != IBIP_OK) return (int)out[1];
     if (out[0] > capacity_steps) return IBIP_ERR_ARG;
@@ -473,7 +483,7 @@ int ibip_invade_ex(ibip_ctx *ctx, const uint8_t *image, const int32_t *dt2, ibip
     int st = ibip_invade_run(ctx, d, dims, inlet_mask ? 0 : inlet, max_steps, seq, step_r2, step_centre,
                              capacity_steps, out, inlet_mask, resume);
     if (st) return st;
-    memcpy(ctx->inv_stats, out, sizeof(out));
+    keep_invade_stats(ctx, out);
     *h_n_steps = out[0];
     if (out[1] != IBIP_OK) return (int)out[1];
     if (out[0] > capacity_steps) return IBIP_ERR_ARG;
