@@ -591,7 +591,7 @@ def run_ours(args, rank, world):
     tot = sum(v[0] for v in prof.values()) or 1.0
     dom = max(prof, key=lambda c: prof[c][0])
     npore = int(img_h.astype(bool).sum())
-    # algorithmic bytes per launch of each class
+    # algorithmic bytes per launch of each class: the minimum each must move
     alg = {
         "edt": 5 * N,                                   # read image, write dt2
         "invade": 8 * N + 8 * K,                        # read dt2, write seq, r2+centre per step
