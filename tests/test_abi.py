@@ -65,3 +65,19 @@ def test_oracle_and_cuda_path_share_nothing():
     for f in ("ibip.py", "build_lib.py", "synth.py", "__init__.py"):
         txt = open(os.path.join(ROOT, "paper_2101_03240_gb300", f)).read()
         assert "import oracle" not in txt and "from oracle" not in txt, f
+
+
+def test_checked_build_compiles_and_exports_every_symbol(lib):
+    """The bounds-checked build (IBIP_CHECKED=1) is a separate library in
+    _build_checked/; it must keep compiling and export the same calls."""
+    import subprocess
+    import sys
+    env = dict(os.environ, IBIP_CHECKED="1")
+    r = subprocess.run([sys.executable, "-c", "from paper_2101_03240_gb300 import build_lib; print(build_lib.build())"],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=1800)
+    assert r.returncode == 0, r.stderr[-3000:]
+    path = r.stdout.strip().splitlines()[-1]
+    assert "_build_checked" in path and os.path.exists(path)
+    checked = C.CDLL(path)
+    for n in declared_symbols():
+        assert hasattr(checked, n), n
