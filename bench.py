@@ -116,24 +116,31 @@ class Clocks:
         except Exception:
             self.p.kill()
         self.f.flush()
-        rows = [l.split(",") for l in open(self.f.name).read().strip().splitlines() if l.strip()]
+        text = open(self.f.name).read()
         os.unlink(self.f.name)
-        sm, mx, reasons = [], 0.0, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in rows:
-            r = [x.strip() for x in r]
-            try:
-                sm.append(float(r[1]))
-                mx = max(mx, float(r[2]))
-            except (ValueError, IndexError):
-                continue
-            for n, v in zip(names, r[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(n)
-        if not sm:
-            return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return parse_clock_samples(text)
+
+
+def parse_clock_samples(text):
+    """Median SM clock, the largest max clock and the throttle reasons seen
+    in nvidia-smi CSV samples (fields as in Clocks.Q, no header or units);
+    None when no sample parses."""
+    rows = [l.split(",") for l in text.strip().splitlines() if l.strip()]
+    sm, mx, reasons = [], 0.0, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for r in rows:
+        r = [x.strip() for x in r]
+        try:
+            sm.append(float(r[1]))
+            mx = max(mx, float(r[2]))
+        except (ValueError, IndexError):
+            continue
+        for n, v in zip(names, r[5:9]):
+            if v.lower().startswith("active"):
+                reasons.add(n)
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
 # ------------------------------------------------------------- batched ----

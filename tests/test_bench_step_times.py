@@ -33,3 +33,19 @@ def test_records_that_do_not_tile_the_steps_are_rejected():
     assert bench.step_time_stats([[0, 2, 10, 0], [3, 2, 10, 0]], r2, 4, 1, 1) is None   # gap
     assert bench.step_time_stats([[0, 2, 10, 0]], r2, 3, 1, 1) is None                  # short
     assert bench.step_time_stats([], r2, 0, 1, 1) is None
+
+
+def test_clock_samples_report_median_and_throttle_reasons():
+    text = "\n".join([
+        "0, 2070, 2070, 900.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 2055, 2070, 1350.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 1980, 2070, 1390.2, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "garbage line",
+        "0, [N/A], 2070, 1.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+    ])
+    c = bench.parse_clock_samples(text)
+    assert c["samples"] == 3 and c["sm_mhz"] == 2055.0 and c["sm_max_mhz"] == 2070.0
+    assert c["reasons"] == ["sw_power_cap"]
+    hot = bench.parse_clock_samples("0, 1500, 2070, 1400, 0x40, Not Active, Active, Not Active, Not Active")
+    assert hot["reasons"] == ["hw_thermal_slowdown"]
+    assert bench.parse_clock_samples("") is None
