@@ -24,3 +24,16 @@ def test_reference_arm_prints_one_contract_line():
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["config"]["workload"] == "blobs48"
+
+
+def test_reference_arm_under_two_ranks_prints_once():
+    base = [sys.executable, "bench.py", "--impl", "reference", "--config", "blobs48", "--steps", "1", "--warmup", "0",
+            "--gpus", "2"]
+    outs = []
+    for rank in (0, 1):
+        env = dict(os.environ, RANK=str(rank), WORLD_SIZE="2", LOCAL_RANK=str(rank))
+        r = subprocess.run(base, cwd=ROOT, capture_output=True, text=True, timeout=600, env=env)
+        assert r.returncode == 0, r.stderr[-2000:]
+        outs.append([ln for ln in r.stdout.splitlines() if ln.strip().startswith("{")])
+    assert len(outs[0]) == 1 and outs[1] == []
+    assert json.loads(outs[0][0])["n_gpus"] == 2
