@@ -70,16 +70,28 @@ typedef struct { int32_t nx, ny, nz; } ibip_dims;
 typedef struct ibip_ctx ibip_ctx;
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
- * to queue work on, or NULL to use the device's legacy default stream.
- * Writes the new context to *out.  Returns IBIP_OK, IBIP_ERR_ARG or
- * IBIP_ERR_CUDA. */
+ * to queue work on (the caller keeps owning it), or NULL: the context then
+ * creates a non-blocking stream of its own, which it destroys in
+ * ibip_destroy, so that its work never serialises against unrelated work on
+ * the legacy default stream.  To queue on the legacy default stream itself,
+ * pass cudaStreamLegacy ((void *)0x1); cudaStreamPerThread ((void *)0x2)
+ * works the same way.  Writes the new context to *out.  Returns IBIP_OK,
+ * IBIP_ERR_ARG or IBIP_ERR_CUDA. */
 IBIP_API int ibip_create(ibip_ctx **out, int device, void *cuda_stream);
 
-/* Release the context and its scratch memory (synchronises its stream). */
+/* Release the context, its scratch memory and its own stream (if it has
+ * one); synchronises the streams first. */
 IBIP_API int ibip_destroy(ibip_ctx *ctx);
 
-/* Change the stream later calls queue on (NULL = legacy default stream). */
+/* Change the stream later calls queue on: a cudaStream_t (cudaStreamLegacy
+ * for the legacy default stream), or NULL for the context's own
+ * non-blocking stream (created here if the context has none yet).  Work
+ * queued earlier is not waited for: order the two streams yourself. */
 IBIP_API int ibip_set_stream(ibip_ctx *ctx, void *cuda_stream);
+
+/* The stream calls currently queue on (*h_stream; never NULL: the legacy
+ * default stream reads as cudaStreamLegacy only if it was given as such). */
+IBIP_API int ibip_get_stream(const ibip_ctx *ctx, void **h_stream);
 
 /* Squared Euclidean distance transform of the pore space (Section 2.1,
  * Figure 2b).

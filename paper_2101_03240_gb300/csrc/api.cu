@@ -275,9 +275,20 @@ int ibip_create(ibip_ctx **out, int device, void *cuda_stream)
     memset(c, 0, sizeof(*c));
     c->device = device;
     c->stream = (cudaStream_t)cuda_stream;
+    if (!cuda_stream) {
+        // no stream given: the context's own, which does not serialise
+        // against unrelated work on the legacy default stream
+        if (cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            delete c;
+            return IBIP_ERR_CUDA;
+        }
+        c->stream = c->own_stream;
+    }
     if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
         cudaMallocHost(&c->h_pinned, 65536) != cudaSuccess) {
         cudaGetLastError();
+        if (c->own_stream) cudaStreamDestroy(c->own_stream);
         delete c;
         return IBIP_ERR_CUDA;
     }
@@ -289,6 +300,7 @@ int ibip_create(ibip_ctx **out, int device, void *cuda_stream)
         if (hc) cudaFreeHost(hc);
         if (c->h_done) cudaFreeHost(c->h_done);
         cudaFreeHost(c->h_pinned);
+        if (c->own_stream) cudaStreamDestroy(c->own_stream);
         delete c;
         return IBIP_ERR_CUDA;
     }
@@ -311,6 +323,10 @@ int ibip_destroy(ibip_ctx *ctx)
         cudaStreamSynchronize(ctx->stream2);
         cudaStreamDestroy(ctx->stream2);
     }
+    if (ctx->own_stream) {
+        cudaStreamSynchronize(ctx->own_stream);
+        cudaStreamDestroy(ctx->own_stream);
+    }
     if (ctx->h_done) cudaFreeHost(ctx->h_done);
     if (ctx->h_cancel) cudaFreeHost((void *)ctx->h_cancel);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
@@ -321,7 +337,23 @@ int ibip_destroy(ibip_ctx *ctx)
 int ibip_set_stream(ibip_ctx *ctx, void *cuda_stream)
 {
     if (!ctx) return IBIP_ERR_ARG;
-    ctx->stream = (cudaStream_t)cuda_stream;
+    if (!cuda_stream && !ctx->own_stream) {
+        // back to a stream of the context's own, created on first need
+        DeviceGuard g(ctx->device);
+        if (cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            ctx->own_stream = nullptr;
+            return IBIP_ERR_CUDA;
+        }
+    }
+    ctx->stream = cuda_stream ? (cudaStream_t)cuda_stream : ctx->own_stream;
+    return IBIP_OK;
+}
+
+int ibip_get_stream(const ibip_ctx *ctx, void **h_stream)
+{
+    if (!ctx || !h_stream) return IBIP_ERR_ARG;
+    *h_stream = (void *)ctx->stream;
     return IBIP_OK;
 }
 

@@ -43,6 +43,9 @@ constexpr int kInvStats = 48;
 struct ibip_ctx {
     int device;
     cudaStream_t stream;
+    // The non-blocking stream the context created for itself (ibip_create
+    // with no stream), destroyed with the context; null when none.
+    cudaStream_t own_stream;
     int sm_count;
     int64_t launches;
     void *slot[SC_NSLOTS];

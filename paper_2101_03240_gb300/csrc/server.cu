@@ -191,6 +191,9 @@ void slot_main(ibip_server *S, int slot)
         ctx->arena_used = 0;
         for (int i = 0; i < SC_NSLOTS; i++) { ctx->slot[i] = nullptr; ctx->slot_bytes[i] = 0; }
         const int st = ibip_run_job(ctx, job);
+        // an early error return may leave kernels queued that still write
+        // into this job's piece: drain the stream before the piece is freed
+        cudaStreamSynchronize(ctx->stream);
         if (st == IBIP_ERR_CUDA) cudaGetLastError();
         const int64_t t_end = now_ns();
         const int64_t used = (int64_t)ctx->arena_used;

@@ -24,6 +24,9 @@ ERR_STEP_LIMIT = -4
 ERR_NOT_CONVERGED = -5
 ERR_CANCELLED = -6
 
+# cudaStreamLegacy: the explicit handle of CUDA's legacy default stream
+CUDA_STREAM_LEGACY = 1
+
 FACES = {"x0": 0, "x1": 1, "y0": 2, "y1": 3, "z0": 4, "z1": 5}
 
 
@@ -72,6 +75,7 @@ def _lib():
                 "ibip_create": (C.c_int, [C.POINTER(P), C.c_int, P]),
                 "ibip_destroy": (C.c_int, [P]),
                 "ibip_set_stream": (C.c_int, [P, P]),
+                "ibip_get_stream": (C.c_int, [P, C.POINTER(P)]),
                 "ibip_edt": (C.c_int, [P, P, Dims, P]),
                 "ibip_invade": (C.c_int, [P, P, P, Dims, C.c_int, i64, P, P, P, i64, C.POINTER(i64)]),
                 "ibip_trapping": (C.c_int, [P, P, Dims, C.c_int, C.c_int, P, P]),
@@ -192,8 +196,11 @@ class Context:
             pass
 
     def _stream(self):
+        # PyTorch's default stream has handle 0, the legacy default stream;
+        # the ABI reads NULL as the context's own stream, so pass the legacy
+        # stream's explicit handle instead
         s = torch.cuda.current_stream(self.device)
-        _lib().ibip_set_stream(self._h, C.c_void_p(s.cuda_stream))
+        _lib().ibip_set_stream(self._h, C.c_void_p(s.cuda_stream or CUDA_STREAM_LEGACY))
 
     @property
     def launches(self) -> int:

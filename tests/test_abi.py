@@ -53,6 +53,11 @@ def test_null_arguments_rejected_on_host(lib):
     assert lib.ibip_create(None, 0, None) == -1
     lib.ibip_destroy.argtypes = [C.c_void_p]
     assert lib.ibip_destroy(None) == -1
+    lib.ibip_get_stream.argtypes = [C.c_void_p, C.c_void_p]
+    out = C.c_void_p()
+    assert lib.ibip_get_stream(None, C.byref(out)) == -1
+    lib.ibip_set_stream.argtypes = [C.c_void_p, C.c_void_p]
+    assert lib.ibip_set_stream(None, None) == -1
 
 
 def test_oracle_and_cuda_path_share_nothing():

@@ -34,7 +34,9 @@ def test_size_image_and_rerank(ctx, seed):
     d = O.edt(img)
     dev = cuda(img)
     seq, r2, cen, K, st = ctx.invade(dev, cuda(d), inlet=seed % 6)
-    sref, r2ref = seq.cpu().numpy(), r2.cpu().numpy()
+    # every expected value below chains oracle to oracle from the image
+    sref, r2ref, _, _, Kref = O.invade(img, d, inlet=seed % 6)
+    assert K == Kref and np.array_equal(seq.cpu().numpy(), sref) and np.array_equal(r2.cpu().numpy(), r2ref)
     assert np.array_equal(ctx.size_image(seq, r2).cpu().numpy(), O.size_image(sref, r2ref))
     outlet = (seed + 1) % 6
     tr, so, r2o = ctx.trapping_rerank(seq, r2, outlet)
@@ -54,6 +56,8 @@ def test_trapping_of_opening_levels(ctx, seed):
     T = S.mio_levels(int(d[img > 0].max()), 20)
     dev = cuda(img)
     lev, cnt = ctx.morph_drainage(dev, cuda(d), T, inlet=0)
+    lev_ref, cnt_ref = O.morph_drainage(img, d, T, inlet=0)
+    assert np.array_equal(lev.cpu().numpy(), lev_ref) and cnt == cnt_ref.tolist()
     tr, so = ctx.trapping(lev, 1)
-    rtr, rso = O.trapping(lev.cpu().numpy(), 1)
+    rtr, rso = O.trapping(lev_ref, 1)
     assert np.array_equal(tr.cpu().numpy(), rtr) and np.array_equal(so.cpu().numpy(), rso)

@@ -60,7 +60,8 @@ def test_edt_random(ctx, seed):
     assert np.array_equal(host(ctx.edt(dev(img))), O.edt(img))
 
 
-@pytest.mark.parametrize("shape", [(1, 1, 1), (1, 1, 70), (70, 1, 1), (1, 70, 1), (33, 2, 65), (5, 129, 31)])
+@pytest.mark.parametrize("shape", [(1, 1, 1), (1, 1, 70), (70, 1, 1), (1, 70, 1), (33, 2, 65), (5, 129, 31),
+                                   (1, 1700, 3), (1700, 2, 3)])
 def test_edt_thin_and_degenerate(ctx, shape):
     rng = np.random.default_rng(sum(shape))
     for img in (S.random_image(shape, 0.8, rng), np.ones(shape, np.uint8), np.zeros(shape, np.uint8)):

@@ -49,9 +49,12 @@ def test_noalloc_matches_edt_on_two_calls(lib):
     torch.cuda.set_device(0)
     ctx = ibip.Context(0)
     rng = np.random.default_rng(2024)
-    # the largest accepted size first, then a smaller ragged one: the second
-    # call runs on scratch still holding the first call's values
-    images = [S.blobs((128, 128, 128), 3.0, 0.6, rng), S.sphere_pack((37, 61, 29), 5, 0.45, rng)]
+    # the largest accepted size first, then a smaller ragged one, then lines
+    # too long to stage in shared memory (along y, then along x: those passes
+    # read global memory instead); each call runs on scratch that still holds
+    # the previous call's values
+    images = [S.blobs((128, 128, 128), 3.0, 0.6, rng), S.sphere_pack((37, 61, 29), 5, 0.45, rng),
+              S.random_image((1, 2048, 1000), 0.9, rng), S.random_image((2048, 1, 1000), 0.9, rng)]
     for img in images:
         d = torch.from_numpy(img).cuda()
         st, got = noalloc_edt(lib, d)
