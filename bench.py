@@ -5,15 +5,23 @@ One step = the whole path on one synthetic image held in HBM:
   squared EDT -> rank + invasion (sequence image, radius per step)
   -> trapping (outlet face) -> saturation / Pc curve -> morphological-opening
   drainage at 40 radii.
-Workload (default): 200^3 overlapping solid spheres of radius 8 voxels,
-porosity 0.40 (seed 2), inlet x=0, outlet x=199, voxel 5 um, sigma 0.072 N/m,
-theta 180 deg.  Results are bit-exact with the CPU oracle (tests/).
+Workload (default): 512^3 anisotropic blobs (noise smoothed with sigma
+(4, 8, 4) voxels, porosity 0.60, seed 3), inlet x=0, outlet x=511, voxel
+5 um, sigma 0.072 N/m, theta 180 deg -- the largest single-image
+configuration, standing in for the 250^3 60 %-porosity blobs of the paper's
+Fig. 4.  --config spheres200 / blobs48 select the smaller images.  Results
+are bit-exact with the CPU oracle (tests/).
 
 value  = voxels per second through the whole path (device-resident inputs);
 e2e    = the same through the public API with the image copied from pinned
          host memory and seq_out + Pc curve copied back inside the timing;
-roofline = the dominant kernel class, timed live with CUDA events;
-cpu_baseline = the plain C oracle on this host's cores (rank 0, N=1).
+roofline = the dominant kernel class (the invasion: a latency-bound loop on
+         one CTA, whose figure of merit is its step latency), with
+         roofline.hbm_kernels giving every HBM-bound class (EDT, rank sort,
+         widest path, trapped mask, Pc, opening dilation) as algorithmic
+         bytes / live CUDA-event time / measured HBM copy bandwidth;
+cpu_baseline = the plain C oracle on this host's cores (rank 0, N=1), on a
+         bounded sample when a full pass would take minutes.
 
 Multi-GPU: one process per GPU (torchrun), each an independent replica of
 the same workload (the invasion is serial per image and does not shard);
@@ -37,6 +45,35 @@ sys.path.insert(0, ROOT)
 
 L2_BYTES = 129 * 1024 * 1024
 CLASS_NAMES = ["edt", "rank", "invade", "maximin", "trap", "pc", "dilate"]
+
+# DRAM traffic per voxel and launch of each kernel class, from ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum summed over the class's
+# kernels in one launch of a smaller image of the same kind, divided by its
+# voxels; the profiles/ summary named in "capture" gives the command and the
+# figures).  "src" lists the sources the counters were taken on with the
+# first 16 hex digits of their SHA-256: when one has changed since, the
+# class reports traffic null.
+NCU_TRAFFIC = {}
+
+
+def source_sha16(rel):
+    import hashlib
+    with open(os.path.join(ROOT, rel), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def traffic_per_launch(cls, units):
+    """ncu DRAM bytes of one launch of class `cls` scaled to `units` voxels,
+    or None when not captured or captured on sources that changed since."""
+    t = NCU_TRAFFIC.get(cls)
+    if not t:
+        return None
+    try:
+        if any(source_sha16(f) != h for f, h in t["src"].items()):
+            return None
+    except OSError:
+        return None
+    return t["bytes_per_voxel"] * units
 
 
 def max_over_ranks(x, world, device):
@@ -64,7 +101,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", choices=["spheres200", "blobs48", "blobs512", "batch256", "serve"],
-                    default="spheres200")
+                    default="blobs512")
     ap.add_argument("--requests", type=int, default=64, help="serve: requests in the Poisson stream")
     ap.add_argument("--budget-gb", type=float, default=20.0,
                     help="serve: device arena of the server (20 GB: below the stream's peak demand, so admission binds)")
@@ -592,13 +629,14 @@ def run_ours(args, rank, world):
     if rank != 0:
         return None
 
-    # ---- roofline of the dominant kernel class
+    # ---- roofline of the dominant kernel class, and of every HBM-bound one
     pk = peaks()
     hbm_peak = pk["hbm_gbs"] if pk else 6800.0
     tot = sum(v[0] for v in prof.values()) or 1.0
     dom = max(prof, key=lambda c: prof[c][0])
     npore = int(img_h.astype(bool).sum())
-    # algorithmic bytes per launch of each class: the minimum each must move
+    # algorithmic bytes per launch (one profiled span) of each class: the
+    # minimum each must move
     alg = {
         "edt": 5 * N,                                   # read image, write dt2
         "invade": 8 * N + 8 * K,                        # read dt2, write seq, r2+centre per step
@@ -615,13 +653,25 @@ def run_ours(args, rank, world):
         per = tms / spans
         kinfo[c] = {"ms_per_step": tms / args.steps, "share": tms / tot, "spans": spans // args.steps,
                     "ms_per_span": per, "algorithmic_GBps": alg[c] / (per * 1e-3) / 1e9}
+    hbm_kernels = {}
+    for c in ("edt", "rank", "maximin", "trap", "pc", "dilate"):
+        if c not in kinfo:
+            continue
+        ach = kinfo[c]["algorithmic_GBps"]
+        hbm_kernels[c] = {"bound": "hbm", "achieved": round(ach, 3), "peak": hbm_peak, "unit": "GB/s",
+                          "frac": ach / hbm_peak, "traffic": traffic_per_launch(c, N),
+                          "algorithmic_bytes_per_launch": int(alg[c]),
+                          "ms_per_launch": kinfo[c]["ms_per_span"], "launches_per_step": kinfo[c]["spans"]}
     per_launch = prof[dom][0] / max(prof[dom][1], 1)
     achieved = alg[dom] / (per_launch * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 3), "peak": hbm_peak,
-                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
+                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic_per_launch(dom, N),
                 "peak_source": "measured" if pk else "fallback",
-                "note": "invasion is a serial, latency-bound loop on one CTA; HBM bytes are the "
-                        "algorithmic minimum (dt2 read + seq write + step arrays)"}
+                "note": "the invasion is a serial, latency-bound loop on one CTA: its HBM bytes are the "
+                        "algorithmic minimum (dt2 read + seq write + step arrays) and its figure of merit is "
+                        "the step latency (invasion_step_times, invasion_us_per_step); hbm_kernels holds the "
+                        "HBM-bound classes against the measured copy bandwidth",
+                "hbm_kernels": hbm_kernels}
     us_per_step = prof["invade"][0] / max(args.steps, 1) * 1e3 / max(K, 1)
 
     value = job_rate(N, world, ms_step * 1e-3)
@@ -667,7 +717,7 @@ def run_ours(args, rank, world):
                          "(Python/SciPy, Fig. 4 caption); context, not a target",
     }
     if world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args, w, levels)
+        out["cpu_baseline"] = cpu_baseline(args, w, args.mio_levels)
     return out
 
 
@@ -686,14 +736,50 @@ def oracle_pass(w, levels, rule="frontier"):
     return K
 
 
-def cpu_baseline(args, w, levels):
-    t = time.perf_counter()
-    oracle_pass(w, levels, args.rule)
-    t = time.perf_counter() - t
-    return {"value": w.image.size / t, "unit": "voxels/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": "one full pass of the %s workload (EDT-sep, %s, trap-UF, Pc, "
-                      "opening by EDT at %d radii); the invasion and trap-UF are single-threaded, "
-                      "the EDT passes use OpenMP on all cores" % (w.name, "literal-queue" if args.rule == "paper" else "invade-heap", len(levels)),
+# a full oracle pass over more voxels than this takes minutes: time a cube
+# cut from the image's corner instead (same generator, same statistics)
+ORACLE_FULL_MAX_VOXELS = 32 * 1024 * 1024
+ORACLE_CROP_EDGE = 128
+
+
+def oracle_sample(w, n_levels):
+    """(workload, opening radii, description) of the oracle's timed sample:
+    the whole image when small enough, else its corner cube [0, 128)^3 with
+    the same faces; the radii (A9) come from the sample's own largest
+    squared distance."""
+    import numpy as np
+
+    import oracle as O
+    from paper_2101_03240_gb300 import synth
+    if w.image.size <= ORACLE_FULL_MAX_VOXELS:
+        img, name, desc = w.image, w.name, "one full pass of the %s workload" % w.name
+    else:
+        e = ORACLE_CROP_EDGE
+        img = np.ascontiguousarray(w.image[:e, :e, :e])
+        name = "%s_corner%d" % (w.name, e)
+        desc = ("one pass over the corner cube [0,%d)^3 of the %s image (%d voxels, its own opening radii); "
+                "a full pass over all %d voxels takes minutes" % (e, w.name, img.size, w.image.size))
+    sw = synth.Workload(name, img, w.inlet, w.outlet, w.mio_levels, w.voxel_m, w.sigma, w.theta_deg)
+    d = O.edt(img)
+    maxd = int(d[img > 0].max()) if img.any() else 1
+    return sw, synth.mio_levels(maxd, n_levels), desc
+
+
+def cpu_baseline(args, w, mio_levels):
+    """The oracle as it stands on the host cores: passes over the bounded
+    sample until at least 10 s of work (at least one pass)."""
+    sw, levels, desc = oracle_sample(w, mio_levels)
+    n, t0 = 0, time.perf_counter()
+    while True:
+        oracle_pass(sw, levels, args.rule)
+        n += 1
+        t = time.perf_counter() - t0
+        if t >= 10.0:
+            break
+    return {"value": sw.image.size * n / t, "unit": "voxels/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "%s, %d time(s) (EDT-sep, %s, trap-UF, Pc, opening by EDT at %d radii); the invasion and "
+                      "trap-UF are single-threaded, the EDT passes use OpenMP on all cores"
+                      % (desc, n, "literal-queue" if args.rule == "paper" else "invade-heap", len(levels)),
             "seconds": t}
 
 
@@ -750,29 +836,27 @@ def run_reference(args, rank, world):
         return None
     if args.config in ("batch256", "serve"):
         return run_reference_images(args, world)
-    import oracle as O
-    from paper_2101_03240_gb300 import synth
     w = workload(args.config)
-    maxd = int(O.edt(w.image)[w.image == 1].max())
-    levels = synth.mio_levels(maxd, args.mio_levels)
+    sw, levels, desc = oracle_sample(w, args.mio_levels)
     for _ in range(args.warmup):
-        oracle_pass(w, levels, args.rule)
+        oracle_pass(sw, levels, args.rule)
     ts = []
     for _ in range(args.steps):
         t = time.perf_counter()
-        K = oracle_pass(w, levels, args.rule)
+        K = oracle_pass(sw, levels, args.rule)
         ts.append(time.perf_counter() - t)
     s = sum(ts) / len(ts)
-    v = w.image.size / s
+    v = sw.image.size / s
     return {"impl": "reference", "metric": "invasion voxels/s (EDT+rank+invasion+trapping+Pc+opening, "
             "bit-exact vs oracle)", "value": v, "unit": "voxels/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": s * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": w.name if args.rule == "frontier" else w.name + "_paper_rule",
-                       "shape": list(w.image.shape), "mio_levels": len(levels)},
+                       "shape": list(w.image.shape), "mio_levels": len(levels),
+                       "sample_shape": list(sw.image.shape)},
             "invasion_steps": K,
             "cpu_baseline": {"value": v, "unit": "voxels/s", "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": "one full pass of the %s workload per step" % w.name},
+                             "sample": desc + " per step"},
             "e2e": {"value": v, "unit": "voxels/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 

@@ -37,3 +37,24 @@ def test_reference_arm_under_two_ranks_prints_once():
         outs.append([ln for ln in r.stdout.splitlines() if ln.strip().startswith("{")])
     assert len(outs[0]) == 1 and outs[1] == []
     assert json.loads(outs[0][0])["n_gpus"] == 2
+
+
+def test_oracle_sample_is_a_corner_cube_of_large_images(monkeypatch):
+    """Images above the full-pass limit are timed on their corner cube, with
+    the workload's faces and radii of the cube's own largest distance."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+
+    import bench
+    import oracle as O
+    from paper_2101_03240_gb300 import synth
+    w = synth.c1_blobs48()
+    sw, levels, desc = bench.oracle_sample(w, 40)
+    assert sw.image is w.image and "full pass" in desc
+    monkeypatch.setattr(bench, "ORACLE_FULL_MAX_VOXELS", 1000)
+    monkeypatch.setattr(bench, "ORACLE_CROP_EDGE", 20)
+    sw, levels, desc = bench.oracle_sample(w, 40)
+    assert sw.image.shape == (20, 20, 20) and np.array_equal(sw.image, w.image[:20, :20, :20])
+    assert sw.inlet == w.inlet and sw.outlet == w.outlet and sw.name == "blobs48_corner20"
+    d = O.edt(sw.image)
+    assert levels == synth.mio_levels(int(d[sw.image > 0].max()), 40)
