@@ -61,6 +61,8 @@ def lib():
                 "or_count_unconnected": (i64, [P, i32, i32, i32, i32]),
                 "or_mio_plain": (None, [P, P, i32, i32, i32, i32, P, i32, P, P]),
                 "or_mio_edt": (None, [P, P, i32, i32, i32, i32, P, i32, P, P]),
+                "or_mio_plain_td": (None, [P, P, i32, i32, i32, i32, P, P, i32, P, P]),
+                "or_mio_edt_td": (None, [P, P, i32, i32, i32, i32, P, P, i32, P, P]),
                 "or_pc_curve": (None, [P, i64, P, i64, dbl, dbl, dbl, P, P, P]),
                 "or_abi_version": (i32, []),
             }
@@ -171,16 +173,19 @@ def count_unconnected(seq, inlet=0):
     return int(lib().or_count_unconnected(_p(s), *s.shape, int(inlet)))
 
 
-def morph_drainage(image, dt2, levels, inlet=0, method="edt"):
-    """Morphological-opening drainage (Section 2.4.1).  Returns (level int32,
-    counts int64[L])."""
+def morph_drainage(image, dt2, levels, inlet=0, method="edt", dilate_levels=None):
+    """Morphological-opening drainage (Section 2.4.1).  Level i erodes at
+    dt2 >= levels[i] and dilates by the ball d^2 < dilate_levels[i] (default:
+    the same bound).  Returns (level int32, counts int64[L])."""
     a = _img(image)
     d = np.ascontiguousarray(dt2, dtype=np.int32)
     T = np.ascontiguousarray(levels, dtype=np.int32)
+    Td = T if dilate_levels is None else np.ascontiguousarray(dilate_levels, dtype=np.int32)
+    assert Td.shape == T.shape
     lev = np.empty(a.shape, np.int32)
     cnt = np.zeros(max(len(T), 1), np.int64)
-    f = lib().or_mio_edt if method == "edt" else lib().or_mio_plain
-    f(_p(a), _p(d), *a.shape, int(inlet), _p(T), len(T), _p(lev), _p(cnt))
+    f = lib().or_mio_edt_td if method == "edt" else lib().or_mio_plain_td
+    f(_p(a), _p(d), *a.shape, int(inlet), _p(T), _p(Td), len(T), _p(lev), _p(cnt))
     return lev, cnt[:len(T)].copy()
 
 
@@ -223,6 +228,31 @@ def equal_saturation(seq, level, n_levels):
         ns.append(n)
         diffs.append(int(np.count_nonzero(in_mio != in_ibip)))
     return np.array(ks, np.int64), np.array(diffs, np.int64), np.array(ns, np.int64)
+
+
+def pc_envelope(seq, step_r2, levels):
+    """The drainage envelope of the invasion at the opening's pressures
+    (Section 2.2.2 and Section 3.1.1: the envelope of the invasion's peak
+    pressures is the opening's capillary-pressure curve).  Pc falls as the
+    sphere radius grows, so the running peak of Pc up to step k is the Pc of
+    the smallest step_r2 so far; at the opening's pressure of level i
+    (squared radius levels[i]) the invasion has taken every step before its
+    running-minimum r2 first drops below levels[i].  Returns (kstar, n):
+    kstar[i] = that number of steps (the first step j with step_r2[j] <
+    levels[i], minus one; K if none) and n[i] = voxels with
+    1 <= seq <= kstar[i], as int64 arrays -- to be compared with the
+    opening's cumulative counts at the same levels."""
+    s = np.asarray(seq).ravel()
+    r2 = np.asarray(step_r2, dtype=np.int64).ravel()
+    K = r2.size
+    cum = np.cumsum(np.bincount(s[(s >= 1) & (s <= K)], minlength=K + 1))   # cum[k] = voxels with 1 <= seq <= k
+    ks, ns = [], []
+    for T in levels:
+        below = np.nonzero(r2 < int(T))[0]
+        k = int(below[0]) if below.size else K    # steps 1..k all have r2 >= T
+        ks.append(k)
+        ns.append(int(cum[k]))
+    return np.array(ks, np.int64), np.array(ns, np.int64)
 
 
 def rerank_radii(seq, step_r2, outlet=1):

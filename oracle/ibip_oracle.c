@@ -546,6 +546,14 @@ int64_t or_count_unconnected(const int32_t *seq, int nx, int ny, int nz, int inl
  *   D_i = {p : exists c in trimmed E_i with |p - c|^2 < T_i}   (dilation)
  * level[p] = i+1 for the first level i with p in D_i; -1 pore never reached;
  * 0 solid.  counts[i] = number of voxels with 1 <= level <= i+1.
+ *
+ * The *_td variants take the dilation's bound separately: D_i = {p : exists
+ * c in trimmed E_i with |p - c|^2 < Td_i} (Td = T gives the above).  With
+ * T_i = R^2 and Td_i = R^2 + 1 for integer radii R the opening uses the ball
+ * |p - c|^2 <= R^2, the structuring element of the paper-literal invasion
+ * (Section 2.1, footnote 1: integer radius), so that the two can be compared
+ * at equal saturation with the structuring element held fixed (Section
+ * 3.1.1).
  * ---------------------------------------------------------------------- */
 
 static void mio_trim(const uint8_t *img, const int32_t *dt2, int nx, int ny, int nz, int inlet,
@@ -582,18 +590,18 @@ static void mio_counts(const int32_t *level, int64_t N, int32_t L, int64_t *coun
 }
 
 /* MIO-plain: dilation by stamping the ball around every trimmed voxel. */
-void or_mio_plain(const uint8_t *img, const int32_t *dt2, int nx, int ny, int nz, int inlet,
-                  const int32_t *T, int32_t L, int32_t *level, int64_t *counts)
+void or_mio_plain_td(const uint8_t *img, const int32_t *dt2, int nx, int ny, int nz, int inlet,
+                     const int32_t *T, const int32_t *Td, int32_t L, int32_t *level, int64_t *counts)
 {
     int64_t N = (int64_t)nx * ny * nz;
     uint8_t *trim = malloc(N ? N : 1), *dil = malloc(N ? N : 1);
     int64_t *q = malloc(sizeof(int64_t) * (N ? N : 1));
     for (int64_t v = 0; v < N; v++) level[v] = img[v] ? -1 : 0;
     for (int32_t i = 0; i < L; i++) {
-        int64_t t = T[i];
+        int64_t t = T[i], td = Td[i];
         mio_trim(img, dt2, nx, ny, nz, inlet, t, trim, q);
         memset(dil, 0, N);
-        int64_t r = ball_halfwidth(t);
+        int64_t r = ball_halfwidth(td);
         for (int64_t c = 0; c < N; c++) {
             if (!trim[c]) continue;
             int64_t cx, cy, cz;
@@ -602,7 +610,7 @@ void or_mio_plain(const uint8_t *img, const int32_t *dt2, int nx, int ny, int nz
                 for (int64_t y = cy - r; y <= cy + r; y++)
                     for (int64_t z = cz - r; z <= cz + r; z++) {
                         if (x < 0 || y < 0 || z < 0 || x >= nx || y >= ny || z >= nz) continue;
-                        if ((x - cx) * (x - cx) + (y - cy) * (y - cy) + (z - cz) * (z - cz) < t)
+                        if ((x - cx) * (x - cx) + (y - cy) * (y - cy) + (z - cz) * (z - cz) < td)
                             dil[lin(x, y, z, ny, nz)] = 1;
                     }
         }
@@ -612,11 +620,17 @@ void or_mio_plain(const uint8_t *img, const int32_t *dt2, int nx, int ny, int nz
     free(trim); free(dil); free(q);
 }
 
+void or_mio_plain(const uint8_t *img, const int32_t *dt2, int nx, int ny, int nz, int inlet,
+                  const int32_t *T, int32_t L, int32_t *level, int64_t *counts)
+{
+    or_mio_plain_td(img, dt2, nx, ny, nz, inlet, T, T, L, level, counts);
+}
+
 /* MIO-edt: identical result; the dilation of the trimmed set by the ball
- * d^2 < T is the set where the squared distance to the trimmed set is < T,
- * computed with EDT-sep taken to the trimmed voxels. */
-void or_mio_edt(const uint8_t *img, const int32_t *dt2, int nx, int ny, int nz, int inlet,
-                const int32_t *T, int32_t L, int32_t *level, int64_t *counts)
+ * d^2 < Td is the set where the squared distance to the trimmed set is
+ * < Td, computed with EDT-sep taken to the trimmed voxels. */
+void or_mio_edt_td(const uint8_t *img, const int32_t *dt2, int nx, int ny, int nz, int inlet,
+                   const int32_t *T, const int32_t *Td, int32_t L, int32_t *level, int64_t *counts)
 {
     int64_t N = (int64_t)nx * ny * nz;
     uint8_t *trim = malloc(N ? N : 1);
@@ -626,10 +640,16 @@ void or_mio_edt(const uint8_t *img, const int32_t *dt2, int nx, int ny, int nz, 
     for (int32_t i = 0; i < L; i++) {
         mio_trim(img, dt2, nx, ny, nz, inlet, T[i], trim, q);
         edt_sep_core(trim, nx, ny, nz, d);
-        for (int64_t v = 0; v < N; v++) if (d[v] < T[i] && level[v] == -1) level[v] = i + 1;
+        for (int64_t v = 0; v < N; v++) if (d[v] < Td[i] && level[v] == -1) level[v] = i + 1;
     }
     mio_counts(level, N, L, counts);
     free(trim); free(q); free(d);
+}
+
+void or_mio_edt(const uint8_t *img, const int32_t *dt2, int nx, int ny, int nz, int inlet,
+                const int32_t *T, int32_t L, int32_t *level, int64_t *counts)
+{
+    or_mio_edt_td(img, dt2, nx, ny, nz, inlet, T, T, L, level, counts);
 }
 
 /* ------------------------------------------------------------------------

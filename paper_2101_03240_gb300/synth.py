@@ -200,4 +200,13 @@ def mio_levels(max_dt2: int, n_levels: int = 40) -> list[int]:
     return out
 
 
+def integer_radius_levels(max_dt2: int) -> tuple[list[int], list[int]]:
+    """Opening levels with the structuring element of the paper-literal
+    invasion (integer radius R, ball |d|^2 <= R^2): for R = floor(sqrt(
+    max_dt2)) down to 1, erosion bound R^2 and dilation bound R^2 + 1
+    (|d|^2 <= R^2 is |d|^2 < R^2 + 1 for integer d)."""
+    R = math.isqrt(max(int(max_dt2), 1))
+    return [r * r for r in range(R, 0, -1)], [r * r + 1 for r in range(R, 0, -1)]
+
+
 FACES = {"x0": 0, "x1": 1, "y0": 2, "y1": 3, "z0": 4, "z1": 5}
