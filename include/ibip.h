@@ -243,6 +243,20 @@ IBIP_API int ibip_morph_drainage(ibip_ctx *ctx, const uint8_t *image, const int3
                         int inlet, const int32_t *h_r2_levels, int32_t n_levels, int32_t *level,
                         int64_t *h_counts);
 
+/* ibip_morph_drainage with the dilation's bound given separately: level i
+ * erodes to dt2 >= h_r2_levels[i] and dilates by the ball
+ * d^2 < h_dilate_r2[i] (host int32[n_levels], each >= 1; NULL = the same
+ * bounds as the erosion, i.e. ibip_morph_drainage).  With h_r2_levels[i] =
+ * R^2 and h_dilate_r2[i] = R^2 + 1 for integer radii R the structuring
+ * element is the closed ball |d|^2 <= R^2 of the paper-literal invasion
+ * (Section 2.1, footnote 1: integer radius; ibip_invade_literal), so the
+ * two can be compared at equal saturation with the element held fixed
+ * (Section 3.1.1).  Other arguments, errors and synchronisation as
+ * ibip_morph_drainage. */
+IBIP_API int ibip_morph_drainage_ex(ibip_ctx *ctx, const uint8_t *image, const int32_t *dt2, ibip_dims dims,
+                                   int inlet, const int32_t *h_r2_levels, const int32_t *h_dilate_r2,
+                                   int32_t n_levels, int32_t *level, int64_t *h_counts);
+
 /* Equal-saturation comparison of an invasion with morphological-opening
  * drainage (Section 3.1.1, Figure 8), by integer counts.  For opening level
  * i (0-based): n_i = voxels with 1 <= level <= i + 1; k_i = the smallest
@@ -366,6 +380,53 @@ IBIP_API int ibip_server_wait(ibip_server *srv, uint64_t ticket, int64_t timeout
  * arena bytes, peak jobs running at once, peak arena bytes in use, kernel
  * launches queued by the slots]; n <= 9. */
 IBIP_API int ibip_server_stats(ibip_server *srv, int64_t *h_stats, int n);
+
+/* ---- serving replicas on several GPUs ----------------------------------
+ * The invasion of one image is a serial chain of steps (Section 2.1: each
+ * step's sphere depends on the previous stamp), so several GPUs serve a
+ * request stream by taking whole requests.  A router holds one server
+ * (above) per replica -- a device, which may be listed more than once --
+ * and sends each request to the replica with the least outstanding work:
+ * the voxels of the jobs submitted to it and not yet seen complete, among
+ * the replicas whose arena can hold the job (ibip_job_footprint); ties go
+ * to the lowest replica index.  No collective and no peer memory: a job
+ * runs on its replica's device alone. */
+typedef struct ibip_router ibip_router;
+
+/* The routing rule by itself (host only, no device): the index i with the
+ * smallest h_load[i] among those with h_capacity[i] >= footprint, the
+ * lowest such index on ties; IBIP_ERR_OOM when none can hold it,
+ * IBIP_ERR_ARG for n < 1, NULL arrays or footprint < 0. */
+IBIP_API int ibip_route_pick(int n, const int64_t *h_load, const int64_t *h_capacity, int64_t footprint);
+
+/* One server of mem_budget bytes and max_slots slots per entry of
+ * h_devices[n] (1 <= n <= 64), each with a context of its own.  Errors as
+ * ibip_server_create. */
+IBIP_API int ibip_router_create(ibip_router **out, int n, const int *h_devices, size_t mem_budget,
+                                int max_slots);
+
+/* Waits for every submitted job and frees every replica. */
+IBIP_API int ibip_router_destroy(ibip_router *router);
+
+/* The replica (and its device, if h_device is not NULL) that a job of these
+ * dimensions should go to now (with_dt2: the job gives no dt2 buffer, as
+ * for ibip_job_footprint).  Place the job's buffers on that device, then
+ * call ibip_router_submit.  Thread-safe. */
+IBIP_API int ibip_router_route(ibip_router *router, ibip_dims dims, int with_dt2, int *h_replica,
+                               int *h_device);
+
+/* Queues a job on replica `replica` (as ibip_server_submit; its buffers
+ * must be on that replica's device) and returns a router ticket. */
+IBIP_API int ibip_router_submit(ibip_router *router, int replica, const ibip_job *job, uint64_t *h_ticket);
+
+/* As ibip_server_wait for a router ticket; *h_replica (if not NULL) gets the
+ * replica that ran it. */
+IBIP_API int ibip_router_wait(ibip_router *router, uint64_t ticket, int64_t timeout_us, int *h_done,
+                              ibip_result *h_result, int *h_replica);
+
+/* Counters of one replica: [device, jobs routed to it, outstanding voxels,
+ * then the 9 counters of ibip_server_stats]; n <= 12. */
+IBIP_API int ibip_router_stats(ibip_router *router, int replica, int64_t *h_stats, int n);
 
 /* Wait for everything queued on the context's stream; returns the first
  * error seen. */

@@ -104,47 +104,101 @@ void or_edt_brute(const uint8_t *img, int nx, int ny, int nz, int32_t *dt2)
 }
 
 /* One 1-D min-plus pass  g'(i) = min_j g(j) + (i-j)^2  along a line of n
- * values with stride s.  INT64_MAX marks "no solid seen on this line".  The
- * search walks j outward from i and stops once (i-j)^2 alone is no smaller
- * than the best value found: every later term is at least that large. */
-static void minplus_line(const int64_t *g, int64_t *out, int64_t n, int64_t s)
+ * values with stride s.  INT32_MAX marks "no feature seen on this line"
+ * (every real value is below 2^30, a squared offset below 2^28, so sums
+ * stay below INT32_MAX).  The search walks j outward from i and stops once
+ * (i-j)^2 alone is no smaller than the best value found, or than `limit`:
+ * every later term is at least that large.  Values below `limit` are
+ * therefore exact; at or above it the output is only known to be >= limit
+ * (INT64_MAX = no limit). */
+static void minplus_line(const int32_t *g, int32_t *out, int64_t n, int64_t s, int64_t limit)
 {
     for (int64_t i = 0; i < n; i++) {
         int64_t best = g[i * s];
         for (int64_t d = 1; d < n; d++) {
-            if (best != INT64_MAX && d * d >= best) break;
+            if (best != INT32_MAX && d * d >= best) break;
+            if (d * d >= limit) break;
             int64_t j0 = i - d, j1 = i + d;
             if (j0 < 0 && j1 >= n) break;
-            if (j0 >= 0 && g[j0 * s] != INT64_MAX && g[j0 * s] + d * d < best) best = g[j0 * s] + d * d;
-            if (j1 < n && g[j1 * s] != INT64_MAX && g[j1 * s] + d * d < best) best = g[j1 * s] + d * d;
+            if (j0 >= 0 && g[j0 * s] != INT32_MAX && g[j0 * s] + d * d < best) best = g[j0 * s] + d * d;
+            if (j1 < n && g[j1 * s] != INT32_MAX && g[j1 * s] + d * d < best) best = g[j1 * s] + d * d;
         }
-        out[i * s] = best;
+        out[i * s] = (int32_t)best;
+    }
+}
+
+/* The same pass over m neighbouring lines at once: element i of line k is
+ * g[i * s + k] (k = 0..m-1 contiguous in memory), so every step of the
+ * search reads m consecutive values.  The search for output row i stops
+ * once (i-j)^2 is no smaller than every line's best value, or than
+ * `limit`. */
+static void minplus_rows(const int32_t *g, int32_t *out, int64_t n, int64_t s, int64_t m, int64_t limit,
+                         int64_t *best)
+{
+    for (int64_t i = 0; i < n; i++) {
+        int64_t worst = 0;
+        for (int64_t k = 0; k < m; k++) {
+            best[k] = g[i * s + k];
+            if (best[k] > worst) worst = best[k];
+        }
+        for (int64_t d = 1; d < n; d++) {
+            if (worst != INT32_MAX && d * d >= worst) break;
+            if (d * d >= limit) break;
+            int64_t j0 = i - d, j1 = i + d;
+            if (j0 < 0 && j1 >= n) break;
+            worst = 0;
+            for (int64_t k = 0; k < m; k++) {
+                if (j0 >= 0 && g[j0 * s + k] != INT32_MAX && g[j0 * s + k] + d * d < best[k])
+                    best[k] = g[j0 * s + k] + d * d;
+                if (j1 < n && g[j1 * s + k] != INT32_MAX && g[j1 * s + k] + d * d < best[k])
+                    best[k] = g[j1 * s + k] + d * d;
+                if (best[k] > worst) worst = best[k];
+            }
+        }
+        for (int64_t k = 0; k < m; k++) out[i * s + k] = (int32_t)best[k];
     }
 }
 
 /* EDT-sep: the squared EDT is separable (a sum of squared per-axis offsets),
  * so three 1-D min-plus passes give the same value as EDT-brute.  `feat`
  * marks the feature voxels the distance is taken to (solid for the pore
- * EDT).  Output INT32_MAX where no feature exists in the whole image. */
-static void edt_sep_core(const uint8_t *feat, int nx, int ny, int nz, int32_t *out)
+ * EDT).  Output INT32_MAX where no feature exists in the whole image.
+ * Outputs below `limit` are exact; the others are only >= limit (a term
+ * at or above the limit in one pass stays at or above it in the next, since
+ * every pass adds a non-negative square).  a, b: work arrays of N int32. */
+static void edt_sep_work(const uint8_t *feat, int nx, int ny, int nz, int32_t *out, int64_t limit, int32_t *a,
+                         int32_t *b)
 {
     int64_t N = (int64_t)nx * ny * nz;
-    int64_t *a = malloc(sizeof(int64_t) * (N ? N : 1));
-    int64_t *b = malloc(sizeof(int64_t) * (N ? N : 1));
-    for (int64_t v = 0; v < N; v++) a[v] = feat[v] ? 0 : INT64_MAX;
+#pragma omp parallel for schedule(static)
+    for (int64_t v = 0; v < N; v++) a[v] = feat[v] ? 0 : INT32_MAX;
     /* along z */
 #pragma omp parallel for schedule(dynamic, 16)
-    for (int64_t r = 0; r < (int64_t)nx * ny; r++) minplus_line(a + r * nz, b + r * nz, nz, 1);
-    /* along y */
-#pragma omp parallel for schedule(dynamic, 16)
-    for (int64_t q = 0; q < (int64_t)nx * nz; q++) {
-        int64_t x = q / nz, z = q % nz;
-        minplus_line(b + x * ny * nz + z, a + x * ny * nz + z, ny, nz);
+    for (int64_t r = 0; r < (int64_t)nx * ny; r++) minplus_line(a + r * nz, b + r * nz, nz, 1, limit);
+    /* along y: the nz lines of one x slab together */
+#pragma omp parallel
+    {
+        int64_t *best = malloc(sizeof(int64_t) * (nz > 0 ? nz : 1));
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t x = 0; x < nx; x++) minplus_rows(b + x * ny * nz, a + x * ny * nz, ny, nz, nz, limit, best);
+        free(best);
     }
-    /* along x */
-#pragma omp parallel for schedule(dynamic, 16)
-    for (int64_t q = 0; q < (int64_t)ny * nz; q++) minplus_line(a + q, b + q, nx, (int64_t)ny * nz);
-    for (int64_t v = 0; v < N; v++) out[v] = b[v] == INT64_MAX ? OR_INF32 : (int32_t)b[v];
+    /* along x: the nz lines of one y row together, into the output */
+#pragma omp parallel
+    {
+        int64_t *best = malloc(sizeof(int64_t) * (nz > 0 ? nz : 1));
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t y = 0; y < ny; y++) minplus_rows(a + y * nz, out + y * nz, nx, (int64_t)ny * nz, nz, limit, best);
+        free(best);
+    }
+}
+
+static void edt_sep_core(const uint8_t *feat, int nx, int ny, int nz, int32_t *out, int64_t limit)
+{
+    int64_t N = (int64_t)nx * ny * nz;
+    int32_t *a = malloc(sizeof(int32_t) * (N ? N : 1));
+    int32_t *b = malloc(sizeof(int32_t) * (N ? N : 1));
+    edt_sep_work(feat, nx, ny, nz, out, limit, a, b);
     free(a);
     free(b);
 }
@@ -154,7 +208,7 @@ void or_edt_sep(const uint8_t *img, int nx, int ny, int nz, int32_t *dt2)
     int64_t N = (int64_t)nx * ny * nz;
     uint8_t *solid = malloc(N ? N : 1);
     for (int64_t v = 0; v < N; v++) solid[v] = img[v] == 0;
-    edt_sep_core(solid, nx, ny, nz, dt2);
+    edt_sep_core(solid, nx, ny, nz, dt2, INT64_MAX);
     free(solid);
 }
 
@@ -628,7 +682,8 @@ void or_mio_plain(const uint8_t *img, const int32_t *dt2, int nx, int ny, int nz
 
 /* MIO-edt: identical result; the dilation of the trimmed set by the ball
  * d^2 < Td is the set where the squared distance to the trimmed set is
- * < Td, computed with EDT-sep taken to the trimmed voxels. */
+ * < Td, computed with EDT-sep taken to the trimmed voxels (exact below Td,
+ * which is all the membership test reads). */
 void or_mio_edt_td(const uint8_t *img, const int32_t *dt2, int nx, int ny, int nz, int inlet,
                    const int32_t *T, const int32_t *Td, int32_t L, int32_t *level, int64_t *counts)
 {
@@ -636,14 +691,19 @@ void or_mio_edt_td(const uint8_t *img, const int32_t *dt2, int nx, int ny, int n
     uint8_t *trim = malloc(N ? N : 1);
     int64_t *q = malloc(sizeof(int64_t) * (N ? N : 1));
     int32_t *d = malloc(sizeof(int32_t) * (N ? N : 1));
+    int32_t *wa = malloc(sizeof(int32_t) * (N ? N : 1)), *wb = malloc(sizeof(int32_t) * (N ? N : 1));
     for (int64_t v = 0; v < N; v++) level[v] = img[v] ? -1 : 0;
     for (int32_t i = 0; i < L; i++) {
         mio_trim(img, dt2, nx, ny, nz, inlet, T[i], trim, q);
-        edt_sep_core(trim, nx, ny, nz, d);
+        int any = 0;
+        for (int64_t v = 0; v < N && !any; v++) any = trim[v];
+        if (!any) continue;   /* nothing trimmed: the dilation is empty */
+        edt_sep_work(trim, nx, ny, nz, d, Td[i], wa, wb);
+#pragma omp parallel for schedule(static)
         for (int64_t v = 0; v < N; v++) if (d[v] < Td[i] && level[v] == -1) level[v] = i + 1;
     }
     mio_counts(level, N, L, counts);
-    free(trim); free(q); free(d);
+    free(trim); free(q); free(d); free(wa); free(wb);
 }
 
 void or_mio_edt(const uint8_t *img, const int32_t *dt2, int nx, int ny, int nz, int inlet,

@@ -592,16 +592,18 @@ int ibip_size_image(ibip_ctx *ctx, const int32_t *seq, ibip_dims dims, const int
     return ibip_size_launch(ctx, seq, dims, step_r2, n_steps, r2_image);
 }
 
-int ibip_morph_drainage(ibip_ctx *ctx, const uint8_t *image, const int32_t *dt2, ibip_dims dims, int inlet,
-                        const int32_t *h_r2_levels, int32_t n_levels, int32_t *level, int64_t *h_counts)
+int ibip_morph_drainage_ex(ibip_ctx *ctx, const uint8_t *image, const int32_t *dt2, ibip_dims dims, int inlet,
+                           const int32_t *h_r2_levels, const int32_t *h_dilate_r2, int32_t n_levels, int32_t *level,
+                           int64_t *h_counts)
 {
     NvtxRange nvtx_range("ibip_morph_drainage");
     if (!ctx || !image || !dt2 || !level || !h_counts || !dims_ok(dims) || !face_ok(inlet) || n_levels < 0 ||
         n_levels > 8192 ||
         (n_levels > 0 && !h_r2_levels))
         return IBIP_ERR_ARG;
+    const int32_t *Td = h_dilate_r2 ? h_dilate_r2 : h_r2_levels;
     for (int i = 0; i < n_levels; i++) {
-        if (h_r2_levels[i] < 1) return IBIP_ERR_ARG;
+        if (h_r2_levels[i] < 1 || Td[i] < 1) return IBIP_ERR_ARG;
         if (i > 0 && h_r2_levels[i] >= h_r2_levels[i - 1]) return IBIP_ERR_ARG;
     }
     DeviceGuard g(ctx->device);
@@ -626,16 +628,22 @@ int ibip_morph_drainage(ibip_ctx *ctx, const uint8_t *image, const int32_t *dt2,
         st = ibip_first_level_launch(ctx, W, dims, T_dev, n_levels, fl);
         if (st) return st;
         for (int i = first; i < n_levels; i++) {
-            st = ibip_dilate_first_level_launch(ctx, fl, h_r2_levels[i], i, dims, level);
+            st = ibip_dilate_first_level_launch(ctx, fl, Td[i], i, dims, level);
             if (st) return st;
         }
     } else {
         for (int i = first; i < n_levels; i++) {
-            st = ibip_dilate_level_launch(ctx, W, h_r2_levels[i], i + 1, dims, level);
+            st = ibip_dilate_level_launch(ctx, W, h_r2_levels[i], Td[i], i + 1, dims, level);
             if (st) return st;
         }
     }
     return ibip_level_counts(ctx, level, dims, n_levels, h_counts);
+}
+
+int ibip_morph_drainage(ibip_ctx *ctx, const uint8_t *image, const int32_t *dt2, ibip_dims dims, int inlet,
+                        const int32_t *h_r2_levels, int32_t n_levels, int32_t *level, int64_t *h_counts)
+{
+    return ibip_morph_drainage_ex(ctx, image, dt2, dims, inlet, h_r2_levels, nullptr, n_levels, level, h_counts);
 }
 
 int ibip_invade_batched(ibip_ctx *ctx, int32_t n, ibip_job *jobs)

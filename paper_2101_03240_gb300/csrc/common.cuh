@@ -139,8 +139,8 @@ int ibip_edt_launch(ibip_ctx *ctx, const uint8_t *image, ibip_dims d, int32_t *d
 int ibip_edt_batch_launch(ibip_ctx *ctx, int n, const uint8_t *const *images, const ibip_dims *dims,
                           int32_t *const *dt2);
 // MIO helper: for feature = (W >= T), marks level[v] = lvl where level[v] == -1
-// and the squared distance to the feature set is < T.
-int ibip_dilate_level_launch(ibip_ctx *ctx, const int32_t *W, int32_t T, int32_t lvl, ibip_dims d,
+// and the squared distance to the feature set is < Td.
+int ibip_dilate_level_launch(ibip_ctx *ctx, const int32_t *W, int32_t T, int32_t Td, int32_t lvl, ibip_dims d,
                              int32_t *level);
 // MIO with a per-voxel first level (uint8, L <= 254): fl[v] = first i with
 // W[v] >= T[i]; then level i's trimmed set is {fl <= i}.

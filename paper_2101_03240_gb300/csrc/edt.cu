@@ -661,14 +661,14 @@ int ibip_dilate_first_level_launch(ibip_ctx *ctx, const uint8_t *fl, int32_t T, 
     return edt_passes(ctx, FeatFirstLevel{fl, i}, d, cap, T, EpiLevel{level, T, i + 1}, IBIP_K_DILATE);
 }
 
-int ibip_dilate_level_launch(ibip_ctx *ctx, const int32_t *W, int32_t T, int32_t lvl, ibip_dims d,
+int ibip_dilate_level_launch(ibip_ctx *ctx, const int32_t *W, int32_t T, int32_t Td, int32_t lvl, ibip_dims d,
                              int32_t *level)
 {
-    // Only squared distances < T matter: a 1-D distance r with r*r >= T is
-    // as good as none, and every partial sum >= T is capped.
+    // Only squared distances < Td matter: a 1-D distance r with r*r >= Td
+    // is as good as none, and every partial sum >= Td is capped.
     int cap = 0;
-    while ((int64_t)(cap + 1) * (cap + 1) < T && cap < 0xfffe) cap++;
-    return edt_passes(ctx, FeatAtLeast{W, T}, d, cap, T, EpiLevel{level, T, lvl}, IBIP_K_DILATE);
+    while ((int64_t)(cap + 1) * (cap + 1) < Td && cap < 0xfffe) cap++;
+    return edt_passes(ctx, FeatAtLeast{W, T}, d, cap, Td, EpiLevel{level, Td, lvl}, IBIP_K_DILATE);
 }
 
 // ------------------------------------------------------------------------

@@ -80,6 +80,7 @@ def _lib():
                 "ibip_invade": (C.c_int, [P, P, P, Dims, C.c_int, i64, P, P, P, i64, C.POINTER(i64)]),
                 "ibip_trapping": (C.c_int, [P, P, Dims, C.c_int, C.c_int, P, P]),
                 "ibip_morph_drainage": (C.c_int, [P, P, P, Dims, C.c_int, P, i32, P, P]),
+                "ibip_morph_drainage_ex": (C.c_int, [P, P, P, Dims, C.c_int, P, P, i32, P, P]),
                 "ibip_pc_curve": (C.c_int, [P, P, Dims, P, i64, dbl, dbl, dbl, P, P, P]),
                 "ibip_synchronize": (C.c_int, [P]),
                 "ibip_launch_count": (i64, [P]),
@@ -422,17 +423,25 @@ class Context:
             raise IbipError("ibip_size_image", st)
         return out
 
-    def morph_drainage(self, image, dt2, levels, inlet=0):
+    def morph_drainage(self, image, dt2, levels, inlet=0, dilate_levels=None):
+        """Opening drainage: level i erodes at dt2 >= levels[i] and dilates by
+        d^2 < dilate_levels[i] (default: the same bounds).  Returns (level,
+        counts)."""
         _need(image, torch.uint8, "image")
         _need(dt2, torch.int32, "dt2")
         T = (C.c_int32 * max(len(levels), 1))(*[int(t) for t in levels])
+        Td = None
+        if dilate_levels is not None:
+            if len(dilate_levels) != len(levels):
+                raise ValueError("dilate_levels must have one bound per level")
+            Td = (C.c_int32 * max(len(levels), 1))(*[int(t) for t in dilate_levels])
         cnt = (C.c_int64 * max(len(levels), 1))()
         lev = torch.empty(image.shape, dtype=torch.int32, device=image.device)
         self._stream()
-        st = _lib().ibip_morph_drainage(self._h, _ptr(image), _ptr(dt2), _dims(image.shape), int(inlet), T,
-                                        len(levels), _ptr(lev), cnt)
+        st = _lib().ibip_morph_drainage_ex(self._h, _ptr(image), _ptr(dt2), _dims(image.shape), int(inlet), T, Td,
+                                           len(levels), _ptr(lev), cnt)
         if st != OK:
-            raise IbipError("ibip_morph_drainage", st)
+            raise IbipError("ibip_morph_drainage_ex", st)
         return lev, [int(c) for c in cnt[:len(levels)]]
 
     def invade_batched(self, images, inlets=0, outlets=1, trapping=True, curve=True, voxel_m=5e-6, sigma=0.072,

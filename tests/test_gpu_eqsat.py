@@ -66,3 +66,29 @@ def test_equal_saturation_edges(ctx):
     k, diff, n = ctx.equal_saturation(seq, seq.clone(), 0, 3)
     assert k == [0, 0, 0] and diff == [0, 0, 0] and n == [0, 0, 0]
     compare(ctx, np.ones((5, 4, 7), np.uint8), 0, 5, "frontier")
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_matched_opening_random(ctx, seed):
+    """The opening with the paper-literal closed ball (ibip_morph_drainage_ex,
+    erosion R^2, dilation |d|^2 <= R^2 for integer R) against the oracle."""
+    rng = np.random.default_rng(900 + seed)
+    shape = tuple(int(x) for x in rng.integers(6, 44, 3))
+    img = S.blobs(shape, rng.uniform(1.5, 3.0), rng.uniform(0.5, 0.75), rng) if seed % 2 else \
+        S.sphere_pack(shape, int(rng.integers(2, 6)), rng.uniform(0.35, 0.5), rng)
+    d = O.edt(img)
+    Te, Td = S.integer_radius_levels(int(d[img > 0].max()) if img.any() else 1)
+    dev = torch.from_numpy(img).cuda()
+    lev, cnt = ctx.morph_drainage(dev, torch.from_numpy(d).cuda(), Te, inlet=seed % 6, dilate_levels=Td)
+    rlev, rcnt = O.morph_drainage(img, d, Te, inlet=seed % 6, dilate_levels=Td)
+    assert np.array_equal(lev.cpu().numpy(), rlev) and cnt == rcnt.tolist()
+
+
+def test_matched_opening_spheres200(ctx):
+    w = S.c2_spheres200()
+    d = O.edt(w.image)
+    Te, Td = S.integer_radius_levels(int(d[w.image > 0].max()))
+    lev, cnt = ctx.morph_drainage(torch.from_numpy(w.image).cuda(), torch.from_numpy(d).cuda(), Te, inlet=0,
+                                  dilate_levels=Td)
+    rlev, rcnt = O.morph_drainage(w.image, d, Te, inlet=0, dilate_levels=Td)
+    assert np.array_equal(lev.cpu().numpy(), rlev) and cnt == rcnt.tolist()
