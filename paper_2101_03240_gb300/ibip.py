@@ -108,6 +108,14 @@ def _lib():
                 "ibip_server_poll": (C.c_int, [P, C.c_uint64, C.POINTER(C.c_int), C.POINTER(Result)]),
                 "ibip_server_wait": (C.c_int, [P, C.c_uint64, i64, C.POINTER(C.c_int), C.POINTER(Result)]),
                 "ibip_server_stats": (C.c_int, [P, C.POINTER(i64), C.c_int]),
+                "ibip_route_pick": (C.c_int, [C.c_int, C.POINTER(i64), C.POINTER(i64), i64]),
+                "ibip_router_create": (C.c_int, [C.POINTER(P), C.c_int, C.POINTER(C.c_int), C.c_size_t, C.c_int]),
+                "ibip_router_destroy": (C.c_int, [P]),
+                "ibip_router_route": (C.c_int, [P, Dims, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+                "ibip_router_submit": (C.c_int, [P, C.c_int, C.POINTER(Job), C.POINTER(C.c_uint64)]),
+                "ibip_router_wait": (C.c_int, [P, C.c_uint64, i64, C.POINTER(C.c_int), C.POINTER(Result),
+                                               C.POINTER(C.c_int)]),
+                "ibip_router_stats": (C.c_int, [P, C.c_int, C.POINTER(i64), C.c_int]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -602,6 +610,122 @@ class Server:
     def close(self):
         if getattr(self, "_h", None):
             _lib().ibip_server_destroy(self._h)
+            self._h = None
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def route_pick(loads, capacities, footprint) -> int:
+    """The routing rule of ibip_route_pick (host only): the replica with the
+    least outstanding work among those whose arena holds `footprint` bytes,
+    the lowest index on ties; -1 when none can hold it."""
+    n = len(loads)
+    if n < 1 or len(capacities) != n:
+        raise ValueError("one capacity per load, at least one replica")
+    L = (C.c_int64 * n)(*[int(x) for x in loads])
+    Cp = (C.c_int64 * n)(*[int(x) for x in capacities])
+    r = _lib().ibip_route_pick(n, L, Cp, int(footprint))
+    if r == ERR_OOM:
+        return -1
+    if r < 0:
+        raise IbipError("ibip_route_pick", r)
+    return r
+
+
+def route_requests(voxels, n_replicas, capacity=None, footprints=None):
+    """Static routing of a request stream over `n_replicas` processes (one
+    GPU each) that cannot see each other's progress: request j goes, in
+    arrival order, by ibip_route_pick to the replica with the fewest voxels
+    routed so far (among those whose arena `capacity` holds its footprint,
+    when given).  Every process computes the same assignment from the same
+    stream, so no message is needed.  Returns the replica of each request."""
+    loads = [0] * n_replicas
+    caps = [capacity if capacity is not None else (1 << 62)] * n_replicas
+    out = []
+    for j, v in enumerate(voxels):
+        r = route_pick(loads, caps, 0 if footprints is None else footprints[j])
+        if r < 0:
+            raise ValueError("request %d fits no replica" % j)
+        loads[r] += int(v)
+        out.append(r)
+    return out
+
+
+class Router:
+    """Serving replicas: one continuous-batching server per entry of
+    `devices` (a device may appear more than once).  Each request goes to
+    the replica with the least outstanding work (ibip_router_route); its
+    image is copied to that replica's device and its outputs are allocated
+    there."""
+
+    def __init__(self, devices, mem_budget: int, max_slots: int = 16):
+        devs = [int(torch.device(d).index if not isinstance(d, int) else d) for d in devices]
+        arr = (C.c_int * len(devs))(*devs)
+        h = C.c_void_p()
+        st = _lib().ibip_router_create(C.byref(h), len(devs), arr, int(mem_budget), int(max_slots))
+        if st != OK:
+            raise IbipError("ibip_router_create", st)
+        self._h = h
+        self.devices = devs
+        self._live = {}
+
+    def route(self, shape):
+        """(replica, device index) a job of this shape would go to now."""
+        r, d = C.c_int(), C.c_int()
+        st = _lib().ibip_router_route(self._h, _dims(shape), 1, C.byref(r), C.byref(d))
+        if st != OK:
+            raise IbipError("ibip_router_route", st)
+        return r.value, d.value
+
+    def submit(self, image, inlet=0, outlet=1, trapping=True, curve=True, voxel_m=5e-6, sigma=0.072,
+               theta_deg=180.0) -> int:
+        """Routes one request: the image (a uint8 tensor on the host or any
+        device) goes to the chosen replica's device; returns a ticket."""
+        replica, dev = self.route(image.shape)
+        im = image.to(torch.device("cuda", dev), non_blocking=False).contiguous()
+        J = Job()
+        r = _fill_job(J, im, int(inlet), int(outlet), trapping, curve, voxel_m, sigma, theta_deg)
+        torch.cuda.current_stream(im.device).synchronize()
+        t = C.c_uint64()
+        st = _lib().ibip_router_submit(self._h, replica, C.byref(J), C.byref(t))
+        if st != OK:
+            raise IbipError("ibip_router_submit", st)
+        self._live[t.value] = (J, im, r)
+        return t.value
+
+    def wait(self, ticket, timeout=None):
+        """The job's result dict (with its `replica`) once complete, else None
+        after `timeout` seconds."""
+        done, res, rep = C.c_int(), Result(), C.c_int()
+        us = -1 if timeout is None else int(timeout * 1e6)
+        st = _lib().ibip_router_wait(self._h, int(ticket), us, C.byref(done), C.byref(res), C.byref(rep))
+        if st != OK:
+            raise IbipError("ibip_router_wait", st)
+        if not done.value:
+            return None
+        _, _, r = self._live.pop(ticket)
+        K = int(res.n_steps)
+        r.update(K=K, status=int(res.status), slot=int(res.slot), replica=int(rep.value),
+                 t_submit_ns=int(res.t_submit_ns), t_start_ns=int(res.t_start_ns), t_end_ns=int(res.t_end_ns))
+        return _trim(r, K)
+
+    def stats(self, replica) -> dict:
+        v = (C.c_int64 * 12)()
+        st = _lib().ibip_router_stats(self._h, int(replica), v, 12)
+        if st != OK:
+            raise IbipError("ibip_router_stats", st)
+        keys = ("device", "routed", "outstanding_voxels", "submitted", "completed", "running", "waiting",
+                "arena_used", "arena_bytes", "peak_running", "peak_arena_used", "launches")
+        return dict(zip(keys, (int(x) for x in v)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib().ibip_router_destroy(self._h)
             self._h = None
             self._live.clear()
 
