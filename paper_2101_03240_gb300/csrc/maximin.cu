@@ -10,18 +10,15 @@
 // started from M = val on F.  Trapping thresholds it against seq (a voxel of
 // step k is trapped iff M < k); opening keeps {M >= T}.
 //
-// GPU: one persistent cooperative grid.  The image is cut into 16 x 16 x 32
-// tiles (z contiguous); a block loads a tile's values and its field with a
-// one-voxel face halo into shared memory and relaxes it to the tile's own
-// fixed point by directional line walks: a thread walks one line of the
-// tile along z, y or x, forwards then backwards, carrying the running
-// max-min of the line, so a value crosses the whole tile in one walk; the
-// three directions alternate until three walks in a row change nothing.  A
-// tile whose face rose above a neighbour's value queues that neighbour on
-// the next round's work list; rounds are separated by a grid-wide barrier
-// and end when a list is empty (or at the round cap).  Contexts that share
-// the device with other streams run the same rounds as one ordinary launch
-// each instead.
+// GPU: one persistent cooperative grid.  The image is cut into 4 x 8 x 32
+// tiles (z contiguous); a block loads a tile with a one-voxel halo into
+// shared memory and relaxes it until it stops changing.  A tile that changed
+// puts its six neighbours on the next round's work list; rounds are separated
+// by a grid-wide barrier and end when a list is empty (or at the round cap).
+// Contexts that share the device with other streams run the same rounds as
+// one ordinary launch each instead.
+// Everything other blocks write (the field, the lists, the counters) is read
+// with L2-coherent loads: the SM's L1 may hold a line from an earlier round.
 #include <cooperative_groups.h>
 
 #include <vector>
@@ -32,27 +29,16 @@ namespace cg = cooperative_groups;
 
 namespace {
 
-constexpr int TX = 16, TY = 16, TZ = 32;
-constexpr int kThreads = 512;
-constexpr int kWarps = kThreads / 32;
-// shared-memory strides: the field has a one-voxel halo on every face and a
-// z stride of 35 words, the values a z stride of 33, so that the z walks
-// (one thread per (x, y) line, lanes along y) read distinct banks
-constexpr int HY = TY + 2, PZ = TZ + 3, VZ = TZ + 1;
-constexpr int kFieldWords = (TX + 2) * HY * PZ;
-constexpr int kValWords = TX * TY * VZ;
-constexpr size_t kSmemBytes = (size_t)(kFieldWords + kValWords) * sizeof(int32_t);
-constexpr int kMaxWalks = 3 * 32;               // line walks per activation before it re-queues itself
+constexpr int TX = 4, TY = 8, TZ = 32;
+constexpr int kThreads = 256;
+constexpr int kPer = TX * TY * TZ / kThreads;   // voxels per thread
+constexpr int kInner = 96;                      // relaxation sweeps per activation
+// resident blocks per SM the register budget is sized for (measured on the
+// 512^3 blobs' trapping: 4 -> 36.7 ms, 5 -> 39.2 ms, 6 -> 43.8 ms)
+constexpr int kMinBlocks = 4;
 constexpr int kMaxRoundsDev = 1 << 16;
 
 __device__ __forceinline__ int as_val(int v) { return v == -1 ? IBIP_INF32 : v; }
-
-// the walk value of a voxel: blocked (0) never carries a path, never
-// invaded (-1) is +infinity
-__device__ __forceinline__ int walk_val(int v) { return v == 0 ? -1 : as_val(v); }
-
-__device__ __forceinline__ int fidx(int hx, int hy, int hz) { return (hx * HY + hy) * PZ + hz; }
-__device__ __forceinline__ int vidx(int lx, int ly, int lz) { return (lx * TY + ly) * VZ + lz; }
 
 __global__ void k_mm_init(const int32_t *__restrict__ val, int nx, int ny, int nz, int face, int32_t *M)
 {
@@ -108,57 +94,35 @@ struct MMArgs {
     int *list0, *list1;   // work lists of global tile ids, alternating by round
     int *count, *head;    // per-round list sizes and take counters [max_rounds + 2]
     int *mark;            // per tile: last round it was queued for
-    int *status;          // [0] rounds run, [1] 1 if the round cap was hit, [2] line walks
+    int *status;          // [0] rounds run, [1] 1 if the round cap was hit, [2] relaxation sweeps
     int max_rounds;
 };
-
-// One walk along a line of n voxels: field entries f[0], f[fs], ..., values
-// v[0], v[vs], ...; the running value enters from the halo entry before the
-// first voxel (f[-fs]) and leaves into nothing.  Forward then backward.
-// Bit i of the result: entry i rose.
-template <int n>
-__device__ __forceinline__ uint32_t walk_line(int32_t *f, int fs, const int32_t *v, int vs)
-{
-    uint32_t ch = 0;
-    int m = f[-fs];
-#pragma unroll 8
-    for (int i = 0; i < n; i++) {
-        const int cur = f[i * fs];
-        const int nm = max(cur, min(v[i * vs], m));
-        if (nm != cur) { f[i * fs] = nm; ch |= 1u << i; }
-        m = nm;
-    }
-    m = f[n * fs];
-#pragma unroll 8
-    for (int i = n - 1; i >= 0; i--) {
-        const int cur = f[i * fs];
-        const int nm = max(cur, min(v[i * vs], m));
-        if (nm != cur) { f[i * fs] = nm; ch |= 1u << i; }
-        m = nm;
-    }
-    return ch;
-}
 
 // Claims and relaxes the tiles of round r's list until the list is drained.
 // A tile queues a neighbour for round r + 1 only where one of its face
 // voxels rose in this activation above the neighbour's value across that
 // face (as loaded): M only grows, so no other neighbour can improve.  In
 // round 0 the seeded values count as risen.
-__device__ void mm_round(const MMArgs &a, int r, int32_t *sM, int32_t *sV, uint32_t *sRise, int *s_tile,
-                         int *s_wake)
+__device__ void mm_round(const MMArgs &a, int r, int32_t (*sM)[TY + 2][TZ + 2], int *s_tile, int *s_wake)
 {
     const int cnt = __ldcg(a.count + r);
     const int *list = (r & 1) ? a.list1 : a.list0;
     int *next = (r & 1) ? a.list0 : a.list1;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    // thread 0 claims one tile ahead: the claim is issued when the current
+    // tile starts and its list entry read after the relaxation, so neither
+    // round trip lies on the path between two tiles
+    int next_g = -1;
+    if (threadIdx.x == 0) {
+        const int q = atomicAdd(&a.head[r], 1);
+        next_g = q < cnt ? __ldcg(list + q) : -1;
+    }
     for (;;) {
-        if (threadIdx.x == 0) {
-            const int q = atomicAdd(&a.head[r], 1);
-            *s_tile = q < cnt ? __ldcg(list + q) : -1;
-        }
+        if (threadIdx.x == 0) *s_tile = next_g;
         __syncthreads();
         const int g = *s_tile;
         if (g < 0) break;
+        int q_next = 0;
+        if (threadIdx.x == 0) q_next = atomicAdd(&a.head[r], 1);
         int lo = 0, hi = a.njobs;
         while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
@@ -168,132 +132,83 @@ __device__ void mm_round(const MMArgs &a, int r, int32_t *sM, int32_t *sV, uint3
         const int t = g - J.tile0;
         const int bz = t % J.tz, by = (t / J.tz) % J.ty, bx = t / (J.tz * J.ty);
         const int x0 = bx * TX, y0 = by * TY, z0 = bz * TZ;
-        const int z = z0 + lane;
-        const bool zin = z < J.nz;
-        // rows of 32 z voxels: the tile's 256 rows (values, field and the
-        // two z-end halo entries) and the 64 rows of the x / y face halos
-        // (field only); a warp takes every 16th row, all loads of four rows
-        // issued before their shared-memory stores
-        constexpr int kRows = TX * TY + 2 * TX + 2 * TY;
-#pragma unroll 1
-        for (int r0 = w; r0 < kRows; r0 += 4 * kWarps) {
-            int fv[4], vv[4], ez[4];
-            int hx[4], hy[4];
+        // the tile's values and the field on the tile plus a one-voxel halo:
+        // every load is issued before the first store to shared memory
+        int sval[kPer], lx[kPer], ly[kPer], lz[kPer];
 #pragma unroll
-            for (int u = 0; u < 4; u++) {
-                const int row = r0 + u * kWarps;
-                fv[u] = -1; vv[u] = 0; ez[u] = -1;
-                hx[u] = -1; hy[u] = -1;
-                if (row >= kRows) continue;
-                if (row < TX * TY) {
-                    hx[u] = row / TY + 1; hy[u] = row % TY + 1;
-                } else {
-                    const int q = row - TX * TY;   // 0..63: x0-1, x0+16 faces (16 rows each), then y faces
-                    if (q < 2 * TY) { hx[u] = q < TY ? 0 : TX + 1; hy[u] = q % TY + 1; }
-                    else { const int p = q - 2 * TY; hy[u] = p < TX ? 0 : TY + 1; hx[u] = p % TX + 1; }
-                }
-                const int x = x0 + hx[u] - 1, y = y0 + hy[u] - 1;
-                if (x < 0 || y < 0 || x >= J.nx || y >= J.ny) continue;
-                const int64_t rb = d_lin(x, y, 0, J.ny, J.nz);
-                if (zin) {
-                    fv[u] = __ldcg(J.M + rb + z);
-                    if (row < TX * TY) vv[u] = __ldg(J.val + rb + z);
-                }
-                if (row < TX * TY) {   // z-end halo: lane 0 the entry before, lane 31 the one after
-                    if (lane == 0 && z0 > 0) ez[u] = __ldcg(J.M + rb + z0 - 1);
-                    if (lane == 31 && z0 + TZ < J.nz) ez[u] = __ldcg(J.M + rb + z0 + TZ);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < 4; u++) {
-                const int row = r0 + u * kWarps;
-                if (row >= kRows) continue;
-                sM[fidx(hx[u], hy[u], lane + 1)] = fv[u];
-                if (row < TX * TY) {
-                    sV[vidx(hx[u] - 1, hy[u] - 1, lane)] = walk_val(vv[u]);
-                    if (lane == 0) sM[fidx(hx[u], hy[u], 0)] = ez[u];
-                    if (lane == 31) sM[fidx(hx[u], hy[u], TZ + 1)] = ez[u];
-                }
-            }
+        for (int k = 0; k < kPer; k++) {
+            const int i = threadIdx.x + k * kThreads;
+            lz[k] = i % TZ; ly[k] = (i / TZ) % TY; lx[k] = i / (TZ * TY);
+            const int x = x0 + lx[k], y = y0 + ly[k], z = z0 + lz[k];
+            sval[k] = (x < J.nx && y < J.ny && z < J.nz) ? J.val[d_lin(x, y, z, J.ny, J.nz)] : 0;
         }
+        constexpr int kHalo = (TX + 2) * (TY + 2) * (TZ + 2);
+        constexpr int kHaloPer = (kHalo + kThreads - 1) / kThreads;
+        int hv[kHaloPer];
+#pragma unroll
+        for (int u = 0; u < kHaloPer; u++) {
+            const int i = threadIdx.x + u * kThreads;
+            const int hz = i % (TZ + 2), hy = (i / (TZ + 2)) % (TY + 2), hx = i / ((TZ + 2) * (TY + 2));
+            const int x = x0 + hx - 1, y = y0 + hy - 1, z = z0 + hz - 1;
+            hv[u] = -1;
+            if (i < kHalo && x >= 0 && y >= 0 && z >= 0 && x < J.nx && y < J.ny && z < J.nz)
+                hv[u] = __ldcg(J.M + d_lin(x, y, z, J.ny, J.nz));
+        }
+        int32_t *sflat = &sM[0][0][0];
+#pragma unroll
+        for (int u = 0; u < kHaloPer; u++) {
+            const int i = threadIdx.x + u * kThreads;
+            if (i < kHalo) sflat[i] = hv[u];
+        }
+#pragma unroll
+        for (int k = 0; k < kPer; k++) sval[k] = as_val(sval[k]);
         if (threadIdx.x < 6) s_wake[threadIdx.x] = 0;
-        if (threadIdx.x < TX * TY) sRise[threadIdx.x] = 0;
         __syncthreads();
-        // the tile's face values as loaded (round 0: the seeds count as
-        // risen): per thread the x- and y-face voxels of one (row, z) and,
-        // for threads 0..255, the z-face voxels of one (x, y) line
-        const int fa = w;
-        const int zx = threadIdx.x >> 4 & 15, zy = threadIdx.x & 15;
-        int mold[6];
-        mold[0] = r == 0 ? -1 : sM[fidx(1, fa + 1, lane + 1)];          // x = 0 face, y = fa
-        mold[1] = r == 0 ? -1 : sM[fidx(TX, fa + 1, lane + 1)];         // x = 15 face
-        mold[2] = r == 0 ? -1 : sM[fidx(fa + 1, 1, lane + 1)];          // y = 0 face, x = fa
-        mold[3] = r == 0 ? -1 : sM[fidx(fa + 1, TY, lane + 1)];         // y = 15 face
-        mold[4] = r == 0 ? -1 : sM[fidx(zx + 1, zy + 1, 1)];            // z = 0 face
-        mold[5] = r == 0 ? -1 : sM[fidx(zx + 1, zy + 1, TZ)];           // z = 31 face
-        // walks: z (threads 0..255, one (x, y) line each), y (warp = x,
-        // lane = z), x (warp = y, lane = z), cycled until three walks in a
-        // row change nothing; sRise[x * 16 + y] collects the z bits of the
-        // voxels that rose (each row word has one writer per walk)
-        int quiet = 0, walks = 0;
-        for (int dir = 0; walks < kMaxWalks; dir = dir == 2 ? 0 : dir + 1) {
-            bool ch = false;
-            if (dir == 0) {
-                if (threadIdx.x < TX * TY) {
-                    const int lx = threadIdx.x / TY, ly = threadIdx.x % TY;
-                    const uint32_t b = walk_line<TZ>(sM + fidx(lx + 1, ly + 1, 1), 1, sV + vidx(lx, ly, 0), 1);
-                    if (b) { sRise[threadIdx.x] |= b; ch = true; }
-                }
-            } else if (dir == 1) {
-                const uint32_t b = walk_line<TY>(sM + fidx(w + 1, 1, lane + 1), PZ, sV + vidx(w, 0, lane), VZ);
+        int mold[kPer];
 #pragma unroll
-                for (int i = 0; i < TY; i++) {   // voxel (w, i, lane) rose: bit lane of row (w, i)
-                    const uint32_t m = __ballot_sync(0xffffffffu, b >> i & 1u);
-                    if (lane == 0 && m) sRise[w * TY + i] |= m;
-                }
-                ch = b != 0;
-            } else {
-                const uint32_t b = walk_line<TX>(sM + fidx(1, w + 1, lane + 1), HY * PZ, sV + vidx(0, w, lane), TY * VZ);
+        for (int k = 0; k < kPer; k++) mold[k] = r == 0 ? -1 : sM[lx[k] + 1][ly[k] + 1][lz[k] + 1];
+        bool any = false, conv = false;
+        int sweeps = 0;
+        for (int it = 0; it < kInner; it++) {
+            sweeps++;
+            int ch = 0;
 #pragma unroll
-                for (int i = 0; i < TX; i++) {   // voxel (i, w, lane): bit lane of row (i, w)
-                    const uint32_t m = __ballot_sync(0xffffffffu, b >> i & 1u);
-                    if (lane == 0 && m) sRise[i * TY + w] |= m;
-                }
-                ch = b != 0;
+            for (int k = 0; k < kPer; k++) {
+                if (sval[k] == 0) continue;
+                const int hx = lx[k] + 1, hy = ly[k] + 1, hz = lz[k] + 1;
+                const int b = max(max(max(sM[hx - 1][hy][hz], sM[hx + 1][hy][hz]), max(sM[hx][hy - 1][hz], sM[hx][hy + 1][hz])),
+                                  max(sM[hx][hy][hz - 1], sM[hx][hy][hz + 1]));
+                const int nv = min(b, sval[k]);
+                if (nv > sM[hx][hy][hz]) { sM[hx][hy][hz] = nv; ch = 1; }
             }
-            walks++;
-            if (__syncthreads_or(ch)) quiet = 0;
-            else if (++quiet == 3) break;
+            if (!__syncthreads_or(ch)) { conv = true; break; }
+            any = true;
         }
-        const bool conv = quiet == 3;
-        if (threadIdx.x == 0) atomicAdd(a.status + 2, walks);
-        // wake a neighbour across a face where a face voxel rose above the
-        // neighbour's value there
-        if (z0 + lane < J.nz) {
-            const int zz = lane + 1;
-            int v;
-            v = sM[fidx(1, fa + 1, zz)];
-            if (v > mold[0] && v > sM[fidx(0, fa + 1, zz)]) s_wake[0] = 1;
-            v = sM[fidx(TX, fa + 1, zz)];
-            if (v > mold[1] && v > sM[fidx(TX + 1, fa + 1, zz)]) s_wake[1] = 1;
-            v = sM[fidx(fa + 1, 1, zz)];
-            if (v > mold[2] && v > sM[fidx(fa + 1, 0, zz)]) s_wake[2] = 1;
-            v = sM[fidx(fa + 1, TY, zz)];
-            if (v > mold[3] && v > sM[fidx(fa + 1, TY + 1, zz)]) s_wake[3] = 1;
+        if (threadIdx.x == 0) {
+            atomicAdd(a.status + 2, sweeps);
+            next_g = q_next < cnt ? __ldcg(list + q_next) : -1;
         }
-        if (threadIdx.x < TX * TY) {
-            int v = sM[fidx(zx + 1, zy + 1, 1)];
-            if (v > mold[4] && v > sM[fidx(zx + 1, zy + 1, 0)]) s_wake[4] = 1;
-            v = sM[fidx(zx + 1, zy + 1, TZ)];
-            if (v > mold[5] && v > sM[fidx(zx + 1, zy + 1, TZ + 1)]) s_wake[5] = 1;
+#pragma unroll
+        for (int k = 0; k < kPer; k++) {
+            if (sval[k] == 0) continue;
+            const int hx = lx[k] + 1, hy = ly[k] + 1, hz = lz[k] + 1;
+            const int mv = sM[hx][hy][hz];
+            if (mv <= mold[k]) continue;   // not risen here
+            if (lx[k] == 0 && mv > sM[0][hy][hz]) s_wake[0] = 1;
+            if (lx[k] == TX - 1 && mv > sM[TX + 1][hy][hz]) s_wake[1] = 1;
+            if (ly[k] == 0 && mv > sM[hx][0][hz]) s_wake[2] = 1;
+            if (ly[k] == TY - 1 && mv > sM[hx][TY + 1][hz]) s_wake[3] = 1;
+            if (lz[k] == 0 && mv > sM[hx][hy][0]) s_wake[4] = 1;
+            if (lz[k] == TZ - 1 && mv > sM[hx][hy][TZ + 1]) s_wake[5] = 1;
         }
         __syncthreads();
-        // store the voxels that rose (each belongs to this tile alone)
-#pragma unroll 4
-        for (int row = w; row < TX * TY; row += kWarps) {
-            if (!(sRise[row] >> lane & 1u)) continue;
-            const int lx = row / TY, ly = row % TY;
-            J.M[d_lin(x0 + lx, y0 + ly, z, J.ny, J.nz)] = sM[fidx(lx + 1, ly + 1, lane + 1)];
+        if (any) {
+#pragma unroll
+            for (int k = 0; k < kPer; k++) {
+                const int x = x0 + lx[k], y = y0 + ly[k], z = z0 + lz[k];
+                if (x < J.nx && y < J.ny && z < J.nz && sval[k] != 0)
+                    J.M[d_lin(x, y, z, J.ny, J.nz)] = sM[lx[k] + 1][ly[k] + 1][lz[k] + 1];
+            }
         }
         if (threadIdx.x < 7) {   // one lane per neighbour (6) and the tile itself: the atomics overlap
             const int q = threadIdx.x, nr = r + 1;
@@ -314,16 +229,15 @@ __device__ void mm_round(const MMArgs &a, int r, int32_t *sM, int32_t *sV, uint3
 }
 
 // All rounds in one cooperative launch, a grid barrier between rounds.
-__global__ void __launch_bounds__(kThreads, 2) k_mm_persistent(MMArgs a)
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_mm_persistent(MMArgs a)
 {
     cg::grid_group grid = cg::this_grid();
-    extern __shared__ int32_t s_mm[];
-    __shared__ uint32_t sRise[TX * TY];
+    __shared__ int32_t sM[TX + 2][TY + 2][TZ + 2];
     __shared__ int s_tile, s_wake[6];
     int r = 0;
     for (;; r++) {
         if (__ldcg(a.count + r) == 0 || r >= a.max_rounds) break;
-        mm_round(a, r, s_mm, s_mm + kFieldWords, sRise, &s_tile, s_wake);
+        mm_round(a, r, sM, &s_tile, s_wake);
         __threadfence();
         grid.sync();
     }
@@ -335,13 +249,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_mm_persistent(MMArgs a)
 
 // One round per launch: for contexts whose kernels share the device with
 // other streams (a cooperative grid could not be made resident beside them).
-__global__ void __launch_bounds__(kThreads, 2) k_mm_round(MMArgs a, int r)
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_mm_round(MMArgs a, int r)
 {
-    extern __shared__ int32_t s_mm[];
-    __shared__ uint32_t sRise[TX * TY];
+    __shared__ int32_t sM[TX + 2][TY + 2][TZ + 2];
     __shared__ int s_tile, s_wake[6];
     if (r >= a.max_rounds || __ldcg(a.count + r) == 0) return;
-    mm_round(a, r, s_mm, s_mm + kFieldWords, sRise, &s_tile, s_wake);
+    mm_round(a, r, sM, &s_tile, s_wake);
 }
 
 }  // namespace
@@ -387,13 +300,6 @@ int ibip_maximin_multi(ibip_ctx *ctx, int n, const IbipMaximinJob *jobs, int max
     k_mm_seed<<<(nt + 255) / 256, 256, 0, s>>>(djobs, n, nt, a.list0, a.count, a.mark);
     IBIP_LAUNCH(ctx);
     int *h = (int *)ctx->h_pinned;
-    if (cudaFuncSetAttribute(k_mm_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(k_mm_round, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes) !=
-            cudaSuccess) {
-        cudaGetLastError();
-        return IBIP_ERR_CUDA;
-    }
     if (ctx->no_coop) {
         // rounds in chunks; the next round's list size is read back after
         // each chunk (an empty round's launch returns at once)
@@ -402,7 +308,7 @@ int ibip_maximin_multi(ibip_ctx *ctx, int n, const IbipMaximinJob *jobs, int max
         int r = 0;
         for (;;) {
             for (int q = 0; q < kChunkRounds && r < rounds; q++, r++) {
-                k_mm_round<<<grid, kThreads, kSmemBytes, s>>>(a, r);
+                k_mm_round<<<grid, kThreads, 0, s>>>(a, r);
                 IBIP_LAUNCH(ctx);
             }
             cudaMemcpyAsync(h, a.count + r, sizeof(int), cudaMemcpyDeviceToHost, s);
@@ -418,7 +324,7 @@ int ibip_maximin_multi(ibip_ctx *ctx, int n, const IbipMaximinJob *jobs, int max
         return IBIP_OK;
     }
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mm_persistent, kThreads, kSmemBytes) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mm_persistent, kThreads, 0) != cudaSuccess ||
         per_sm < 1) {
         cudaGetLastError();
         return IBIP_ERR_CUDA;
@@ -426,7 +332,7 @@ int ibip_maximin_multi(ibip_ctx *ctx, int n, const IbipMaximinJob *jobs, int max
     int grid = ctx->sm_count * per_sm;
     if (grid > nt) grid = nt;
     void *args[] = {&a};
-    cudaError_t e = cudaLaunchCooperativeKernel((void *)k_mm_persistent, grid, kThreads, args, kSmemBytes, s);
+    cudaError_t e = cudaLaunchCooperativeKernel((void *)k_mm_persistent, grid, kThreads, args, 0, s);
     IBIP_LAUNCH(ctx);
     if (e != cudaSuccess) return ibip_cuda_status(e);
     cudaMemcpyAsync(h, a.status, 3 * sizeof(int), cudaMemcpyDeviceToHost, s);

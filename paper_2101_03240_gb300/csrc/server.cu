@@ -147,7 +147,7 @@ extern "C" int64_t ibip_job_footprint(ibip_dims d, int with_dt2)
     for (int q = 0; q < 3; q++) add(scan_work_bytes(nscan));     // scan work, regrown at most thrice
     // trapping: widest-path field, tile lists and round counters
     add(4 * N);
-    const int64_t nt = (int64_t)((d.nx + 15) / 16) * ((d.ny + 15) / 16) * ((d.nz + 31) / 32);
+    const int64_t nt = (int64_t)((d.nx + 3) / 4) * ((d.ny + 7) / 8) * ((d.nz + 31) / 32);
     add(256 + (3 * nt + 2 * ((1 << 16) + 2) + 4) * 4);
     // curve: per-step histogram (steps <= pore voxels <= N)
     add(4 * (N + 2));
