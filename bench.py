@@ -42,6 +42,9 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# hardware work queues for the server's streams (see ibip_server_create);
+# must be set before the CUDA context exists
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 L2_BYTES = 129 * 1024 * 1024
 CLASS_NAMES = ["edt", "rank", "invade", "maximin", "trap", "pc", "dilate"]
@@ -102,10 +105,12 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", choices=["spheres200", "blobs48", "blobs512", "batch256", "serve"],
                     default="blobs512")
-    ap.add_argument("--requests", type=int, default=64, help="serve: requests in the Poisson stream")
+    ap.add_argument("--requests", type=int, default=600, help="serve: requests in the Poisson stream")
     ap.add_argument("--budget-gb", type=float, default=20.0,
                     help="serve: device arena of the server (20 GB: below the stream's peak demand, so admission binds)")
-    ap.add_argument("--slots", type=int, default=64, help="serve: worker slots")
+    ap.add_argument("--slots", type=int, default=16,
+                    help="serve: worker slots (the stream keeps ~6 jobs in flight on average; 16 slots keep the "
+                         "jobs' kernels from crowding each other's one-CTA invasions)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rule", choices=["frontier", "paper"], default="frontier",
                     help="invasion rule: the frontier rule, or Section 2.1 as printed (all ties, trunc radius)")
@@ -317,146 +322,188 @@ def _request_image(j):
     return synth.mixed_image(j, 5000, 64, 384)
 
 
-def serve_images(n):
+def serve_images(which):
     """The request stream's images (image j is mixed_image(j) of the
-    64^3..384^3 stream), generated by a spawn pool before any GPU call."""
+    64^3..384^3 stream) for the request indices `which`, generated by a
+    spawn pool before any GPU call."""
     import multiprocessing as mp
-    with mp.get_context("spawn").Pool(min(n, os.cpu_count() or 1)) as pool:
-        return pool.map(_request_image, range(n))
+    which = list(which)
+    if not which:
+        return []
+    with mp.get_context("spawn").Pool(min(len(which), os.cpu_count() or 1)) as pool:
+        return pool.map(_request_image, which)
+
+
+def serve_stream(srv, imgs, arrivals, keep=(), host=None, stage=None):
+    """Submits imgs[i] at time arrivals[i] (seconds from now, ascending) and
+    waits for all of them.  Results are dropped once seen complete (their
+    device buffers freed), except those of the indices in `keep`.  With
+    `host` (pinned host images), request i's image is first copied from
+    host[i] into a fresh device buffer, and with `stage` (a pinned int32
+    buffer) every result's seq_out is copied back into it when seen
+    complete.  Returns (records, kept): per request (submit ns, end ns, K,
+    status)."""
+    import collections
+
+    import torch
+    t0 = time.monotonic()
+    out = [None] * len(imgs)
+    kept = {}
+    pending = collections.deque()
+
+    def collect(i, r):
+        out[i] = (r["t_submit_ns"], r["t_end_ns"], r["K"], r["status"])
+        if stage is not None:
+            stage[:r["seq_out"].numel()].copy_(r["seq_out"].view(-1))
+        if i in keep:
+            kept[i] = r
+
+    for i, (im, ta) in enumerate(zip(imgs, arrivals)):
+        d = t0 + ta - time.monotonic()
+        if d > 0:
+            time.sleep(d)
+        if host is not None:
+            im = torch.empty(host[i].shape, dtype=torch.uint8, device=im.device)
+            im.copy_(host[i], non_blocking=True)
+        pending.append((i, srv.submit(im, inlet=0, outlet=1)))
+        while pending:   # drop what has completed, in arrival order
+            r = srv.poll(pending[0][1])
+            if r is None:
+                break
+            collect(pending[0][0], r)
+            pending.popleft()
+    for i, t in pending:
+        collect(i, srv.wait(t))
+    return out, kept
 
 
 def run_serve(args, rank, world):
     """Poisson request stream (20 requests/s, 64^3..384^3, half blobs, half
-    sphere packs), each request EDT + invasion + trapping + Pc, through the
-    continuous-batching server: p50/p99 latency at the offered load, and
-    images/s with every request queued at once."""
+    sphere packs; 600 requests by default), each request EDT + invasion +
+    trapping + Pc, through the continuous-batching server.  One timed step
+    is the whole stream: every request submitted at its arrival time;
+    value = requests / (last completion - first arrival), and p50/p99 of
+    (completion - arrival) over all requests.  Under torchrun the stream is
+    split over the ranks by ibip.route_requests (fewest routed voxels, the
+    same split computed on every rank, no messages)."""
     import numpy as np
     from paper_2101_03240_gb300 import synth
     reqs = synth.c5_requests(n=args.requests)
-    imgs_h = serve_images(len(reqs))
+    n_all = len(reqs)
+    from paper_2101_03240_gb300 import ibip
+    assign = ibip.route_requests([L ** 3 for _, L, _ in reqs], world) if world > 1 else [0] * n_all
+    mine = [j for j in range(n_all) if assign[j] == rank]
+    imgs_h = serve_images(mine)
     import torch
     import torch.distributed as dist
-
-    from paper_2101_03240_gb300 import ibip
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    nvox_total = sum(a.size for a in imgs_h)
+    nvox_mine = sum(a.size for a in imgs_h)
     imgs = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in imgs_h]
+    arrivals = [reqs[j][0] for j in mine]
     ctx = ibip.Context(local)
     if args.autotune:
         ctx.set_autotune(True)
     budget = int(args.budget_gb * (1 << 30))
     srv = ibip.Server(ctx, budget, max_slots=args.slots)
     torch.cuda.synchronize()
-
-    def saturated(which):
-        ts = [srv.submit(imgs[j], inlet=0, outlet=1) for j in which]
-        return [srv.wait(t) for t in ts]
+    sample = list(range(min(8, len(imgs))))   # kept for the bit-exactness check
 
     for _ in range(max(1, args.warmup)):
-        saturated(range(min(8, len(imgs))))
+        serve_stream(srv, imgs[:8], [0.0] * min(8, len(imgs)))
     if world > 1:
         dist.barrier()
     clocks = Clocks(local) if rank == 0 else None
-    # capacity: every request queued at once
     l0 = srv.stats()["launches"]
-    pass_s = []
-    for _ in range(args.steps):
+    spans, recs, kept = [], None, None
+    for _ in range(max(1, args.steps)):
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        res = saturated(range(len(imgs)))
-        torch.cuda.synchronize()
-        pass_s.append(time.perf_counter() - t0)
-    st_sat = srv.stats()
-    launches = (st_sat["launches"] - l0) // max(args.steps, 1)
-    # offered load: requests submitted at their Poisson arrival times
-    t0 = time.monotonic()
-    tick = []
-    for j, (ta, L, kind) in enumerate(reqs):
-        d = t0 + ta - time.monotonic()
-        if d > 0:
-            time.sleep(d)
-        tick.append(srv.submit(imgs[j], inlet=0, outlet=1))
-    lat = [srv.wait(t) for t in tick]
+        recs, kept = serve_stream(srv, imgs, arrivals, keep=set(sample))
+        spans.append((max(r[1] for r in recs) - min(r[0] for r in recs)) * 1e-9)
     ck = clocks.stop() if clocks else None
-    st_off = srv.stats()
-    lat_ms = np.array([(r["t_end_ns"] - r["t_submit_ns"]) * 1e-6 for r in lat])
-    span_s = (max(r["t_end_ns"] for r in lat) - min(r["t_submit_ns"] for r in lat)) * 1e-9
-    Ks = [r["K"] for r in res]
-    assert all(r["status"] == 0 for r in res + lat) and Ks == [r["K"] for r in lat]
-    # end to end: host images in (pinned H2D), seq_out back to host
+    st = srv.stats()
+    launches = (st["launches"] - l0) // max(args.steps, 1)
+    assert all(r[3] == 0 for r in recs)
+    span = max(spans)
+    # end to end through the same stream: every request's image copied in
+    # from pinned host memory at its arrival time, its seq_out copied back
+    # to pinned host memory when it completes
     pins = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in imgs_h]
-    outs = [torch.empty(a.shape, dtype=torch.int32).pin_memory() for a in imgs_h]
+    stage = torch.empty(max(a.size for a in imgs_h), dtype=torch.int32).pin_memory()
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    ts = []
-    for d, p_ in zip(imgs, pins):
-        d.copy_(p_, non_blocking=True)
-        ts.append(srv.submit(d, inlet=0, outlet=1))
-    for o, t in zip(outs, ts):
-        o.copy_(srv.wait(t)["seq_out"])
-    torch.cuda.synchronize()
-    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+    erecs, _ = serve_stream(srv, imgs, arrivals, host=pins, stage=stage)
+    e2e_s = (max(r[1] for r in erecs) - min(r[0] for r in erecs)) * 1e-9
+    del pins
     srv.close()
-    # the plain one-image-per-call path on the same requests
-    alone_s = []
-    for j, im in enumerate(imgs):
+    # bit-exactness of served results against the one-image calls (sample)
+    alone_s, exact = [], 0
+    for i in sample:
         torch.cuda.synchronize()
         t1 = time.perf_counter()
-        dd = ctx.edt(im)
-        s_, r2, cen, K, st = ctx.invade(im, dd, inlet=0)
+        dd = ctx.edt(imgs[i])
+        s_, r2, cen, K, st_ = ctx.invade(imgs[i], dd, inlet=0)
         tr, so = ctx.trapping(s_, 1)
-        ctx.pc_curve(so, r2)
+        S_, P_, _ = ctx.pc_curve(so, r2)
         torch.cuda.synchronize()
         alone_s.append(time.perf_counter() - t1)
-        assert K == Ks[j]
-    single_s = sum(alone_s)
-    service_s = [(r["t_end_ns"] - r["t_start_ns"]) * 1e-9 for r in res]
-    sat_s = sum(pass_s) / len(pass_s)
-    sat_s = max_over_ranks(sat_s, world, dev)
+        r = kept[i]
+        exact += int(K == r["K"] and torch.equal(s_, r["seq"]) and torch.equal(so, r["seq_out"]) and
+                     torch.equal(tr, r["trapped"]) and torch.equal(P_, r["Pc"]) and torch.equal(S_, r["S"]))
+    # gather every rank's records
+    if world > 1:
+        allrec = [None] * world
+        dist.all_gather_object(allrec, recs)
+        recs_all = [r for part in allrec for r in part]
+        span = max_over_ranks(span, world, dev)
+        e2e_s = max_over_ranks(e2e_s, world, dev)
+    else:
+        recs_all = recs
     if rank != 0:
         return None
-    n = len(imgs)
+    lat_all = np.array([(r[1] - r[0]) * 1e-6 for r in recs_all])
+    n = len(recs_all)
     out = {
         "metric": "served images/s and p50/p99 latency (EDT+rank+invasion+trapping+Pc per request, bit-exact)",
-        "value": job_rate(n, world, sat_s), "unit": "images/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": sat_s * 1e3, "higher_is_better": True, "scaling": "weak",
+        "value": n / span, "unit": "images/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": span * 1e3, "higher_is_better": True,
+        "scaling": "strong" if world > 1 else "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": "serve", "requests": n, "rate_per_s": 20.0, "voxels": int(nvox_total),
+        "config": {"workload": "serve", "requests": n_all, "rate_per_s": 20.0,
                    "edge": "64..384 log-uniform", "mix": "half blobs, half sphere packs",
                    "budget_bytes": budget, "slots": args.slots,
                    "l2": "inputs larger than L2 (whole stream resident)", "parallelism": "replicas%d" % world,
-                   "timing": "host clock around device-synchronised passes (jobs span many streams)"},
-        "latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99)),
-                       "max": float(lat_ms.max()), "offered_images_per_s": n / reqs[-1][0],
-                       "achieved_images_per_s": n / span_s},
-        "server": {"saturated": st_sat, "offered": st_off},
-        "per_image_path_images_per_s": n / single_s,
-        "served_over_per_image": (n / sat_s) / (n / single_s),
-        "jobs": {"alone_s_max": max(alone_s), "alone_s_sum": single_s,
-                 "served_service_s_max": max(service_s), "served_service_s_mean": sum(service_s) / n,
-                 "largest_edge": max(a.shape[0] for a in imgs_h),
-                 "note": "a served pass cannot end before its longest job; alone_s_max bounds it from below"},
-        "invasion_steps": int(sum(Ks)),
-        "e2e": {"value": job_rate(n, world, e2e_s), "unit": "images/s", "h2d_bytes_per_step": int(nvox_total),
-                "d2h_bytes_per_step": int(4 * nvox_total)},
+                   "routing": "least routed voxels per rank" if world > 1 else None,
+                   "timing": "host clock: one step = the whole Poisson stream, first arrival to last completion"},
+        "latency_ms": {"p50": float(np.percentile(lat_all, 50)), "p99": float(np.percentile(lat_all, 99)),
+                       "max": float(lat_all.max()), "mean": float(lat_all.mean())},
+        "offered_images_per_s": n_all / reqs[-1][0],
+        "server": st,
+        "bit_exact_sample": "%d of %d served results equal the one-image calls" % (exact, len(sample)),
+        "sample_alone_s": alone_s,
+        "invasion_steps": int(sum(r[2] for r in recs_all)),
+        "e2e": {"value": n / e2e_s, "unit": "images/s",
+                "h2d_bytes_per_step": int(nvox_mine), "d2h_bytes_per_step": int(4 * nvox_mine),
+                "note": "the same stream with each image copied in from pinned host memory at its arrival "
+                        "and its seq_out copied back when complete (per rank's share)"},
         "gpu_launches": int(launches),
         "clocks": ck,
         "gpu": torch.cuda.get_device_name(dev), "host_cores": os.cpu_count(), "seed": 5,
     }
+    assert exact == len(sample), out["bit_exact_sample"]
     if world == 1 and not args.no_cpu_baseline:
         import oracle as O
-        sample = sorted(imgs_h, key=lambda a: a.size)[:4]
+        small = sorted(imgs_h, key=lambda a: a.size)[:4]
         t = time.perf_counter()
-        for a in sample:
+        for a in small:
             dd = O.edt(a)
             sq = O.invade(a, dd, inlet=0)
             so = O.trapping(sq[0], 1)[1]
             O.pc_curve(so, sq[1])
         t = time.perf_counter() - t
-        out["cpu_baseline"] = {"value": sum(a.size for a in sample) / t / (nvox_total / n), "unit": "images/s",
+        mean_vox = sum(L ** 3 for _, L, _ in reqs) / n_all
+        out["cpu_baseline"] = {"value": sum(a.size for a in small) / t / mean_vox, "unit": "images/s",
                                "cores": os.cpu_count(), "kind": "oracle",
                                "sample": "the 4 smallest request images, whole path each; images/s = their "
                                          "voxels/s / the stream's mean voxels per image"}
@@ -623,6 +670,38 @@ def run_ours(args, rank, world):
                     "note": "pore voxels trapped (defending phase cut from the outlet) after the invasion and "
                             "after the opening's last level, the opening's levels read as a sequence"}
 
+    # ---- Section 3.1.1 / Fig. 8 and the Pc envelope (Sections 2.2.2, 3.1.1),
+    # once, untimed: each invasion rule against the opening with its own
+    # structuring element, by integer counts over all pore voxels
+    rules_vs_opening = None
+    if w.outlet is not None:
+        npore_ = int((img_d > 0).sum().item())
+        d_ = ctx.edt(img_d)
+        s_f, r2_f, _, K_f, _ = ctx.invade(img_d, d_, inlet=w.inlet)
+        s_p, _, r2_p, _, K_p, _ = ctx.invade_literal(img_d, d_, inlet=w.inlet)
+        lev_o, cnt_o = ctx.morph_drainage(img_d, d_, levels, inlet=w.inlet)
+        Te, Td = synth.integer_radius_levels(maxd)
+        lev_m, cnt_m = ctx.morph_drainage(img_d, d_, Te, inlet=w.inlet, dilate_levels=Td)
+
+        def compare(seq_, r2_, K_, lev_, cnt_, T_):
+            _, diff, _ = ctx.equal_saturation(seq_, lev_, K_, len(T_))
+            _, n_env = ctx.pc_envelope(seq_, r2_, T_)
+            env = [abs(a - b) for a, b in zip(n_env, cnt_)]
+            return {"levels": len(T_), "equal_saturation_max": max(diff) / npore_,
+                    "equal_saturation_mean": sum(diff) / len(diff) / npore_,
+                    "envelope_max": max(env) / npore_, "envelope_mean": sum(env) / len(env) / npore_}
+
+        rules_vs_opening = {
+            "frontier_rule_vs_opening": compare(s_f, r2_f, K_f, lev_o, cnt_o, levels),
+            "paper_rule_vs_closed_ball_opening": compare(s_p, r2_p, K_p, lev_m, cnt_m, Te),
+            "paper_rule_vs_opening": compare(s_p, r2_p, K_p, lev_o, cnt_o, levels),
+            "frontier_rule_vs_closed_ball_opening": compare(s_f, r2_f, K_f, lev_m, cnt_m, Te),
+            "note": "fractions of the pore voxels: equal_saturation = voxels in exactly one of the opening's set "
+                    "and the invasion's set of the same count; envelope = |voxels invaded before the running "
+                    "minimum sphere drops below the level - the opening's count at that level|.  The opening "
+                    "erodes at T and dilates by d^2 < T at the A9 radii; the closed-ball opening erodes at R^2 "
+                    "and dilates by d^2 <= R^2 at every integer R, the sphere of the paper-literal rule"}
+
     # ---- time per invasion step by radius class, once, untimed
     step_times = invasion_step_times(ctx, img_d, w) if args.rule == "frontier" else None
 
@@ -699,6 +778,7 @@ def run_ours(args, rank, world):
                              "note": "voxels in exactly one of the opening's level set and the invasion's "
                                      "matched-count set, over all pore voxels (Section 3.1.1)"},
         "trapping_vs_opening": trap_cmp,
+        "rules_vs_opening": rules_vs_opening,
         "invasion_steps_per_s": K / (prof["invade"][0] / args.steps * 1e-3) if prof["invade"][1] else None,
         "invasion_us_per_step": us_per_step,
         "invasion_step_times": step_times,

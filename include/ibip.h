@@ -290,6 +290,26 @@ IBIP_API int ibip_pc_curve(ibip_ctx *ctx, const int32_t *seq, ibip_dims dims, co
                   int64_t n_steps, double voxel_m, double sigma, double theta_deg,
                   float *sat_per_step, float *pc_per_step, float *sat_image);
 
+/* Drainage envelope of an invasion at the pressures of opening levels
+ * (Section 2.2.2: the envelope of the invasion's peak pressures; Section
+ * 3.1.1: it matches the opening's capillary-pressure curve).  Pc falls as
+ * the sphere grows, so the running peak of Pc up to step k is the Pc of the
+ * smallest step_r2 so far; at the pressure of level i (squared radius
+ * h_r2_levels[i]) the invasion has taken every step before its running
+ * minimum of step_r2 first drops below h_r2_levels[i].
+ *   seq:          int32[N] sequence image (or a trapping-corrected seq_out).
+ *   step_r2:      int32[n_steps].
+ *   h_r2_levels:  host int32[n_levels], strictly decreasing, >= 1;
+ *                 1 <= n_levels <= 254.
+ *   h_steps:      host int64[n_levels] output: the number of steps taken at
+ *                 level i (the first step below it, 0-based; n_steps if none).
+ *   h_count:      host int64[n_levels] output: voxels with 1 <= seq <=
+ *                 h_steps[i], to compare with ibip_morph_drainage's counts.
+ * Synchronous. */
+IBIP_API int ibip_pc_envelope(ibip_ctx *ctx, const int32_t *seq, ibip_dims dims, const int32_t *step_r2,
+                              int64_t n_steps, const int32_t *h_r2_levels, int32_t n_levels, int64_t *h_steps,
+                              int64_t *h_count);
+
 /* One image of a batched call.  Device pointers unless stated; the caller
  * owns every buffer.  Outputs are those of ibip_edt, ibip_invade,
  * ibip_trapping and ibip_pc_curve for this image. */
@@ -355,7 +375,18 @@ typedef struct {
 IBIP_API int64_t ibip_job_footprint(ibip_dims dims, int with_dt2);
 
 /* Creates a server on ctx's device (ctx itself is not used afterwards).
- * 1 <= max_slots <= 128.  Allocates the arena (IBIP_ERR_OOM if it cannot). */
+ * 1 <= max_slots <= 128.  Allocates the arena (IBIP_ERR_OOM if it cannot).
+ * Each slot has two streams: its wide kernels (EDT, rank sort, curve) at
+ * the device's lowest stream priority, its one-CTA invasion and the
+ * per-round widest-path launches at the highest; its waits sleep on
+ * blocking-sync events.  CUDA maps streams onto CUDA_DEVICE_MAX_CONNECTIONS
+ * hardware queues (8 by default): with more streams than queues a long
+ * invasion kernel holds up the later launches of every stream sharing its
+ * queue, so set CUDA_DEVICE_MAX_CONNECTIONS=32 in the environment before
+ * the process creates its CUDA context and keep 2 * max_slots <= 32 (the
+ * Python binding sets it when imported first).  Measured on the 600-request
+ * stream (20 req/s, 64^3-384^3): 13.5 images/s served with 8 queues, 20.9
+ * with 32. */
 IBIP_API int ibip_server_create(ibip_server **out, ibip_ctx *ctx, size_t mem_budget, int max_slots);
 
 /* Waits for every submitted job, stops the slots and frees the arena. */

@@ -128,7 +128,7 @@ void *ibip_scratch(ibip_ctx *ctx, int slot, size_t bytes)
         return ctx->slot[slot];
     }
     if (ctx->slot[slot]) {
-        cudaStreamSynchronize(ctx->stream);
+        ibip_sync(ctx, ctx->stream);
         cudaFree(ctx->slot[slot]);
         ctx->slot[slot] = nullptr;
         ctx->slot_bytes[slot] = 0;
@@ -191,7 +191,7 @@ int ibip_run_job(ibip_ctx *ctx, ibip_job &J)
                             cos(J.theta_deg * pi / 180.0), J.sat_per_step, J.pc_per_step, nullptr);
         if (st) return st;
     }
-    return ibip_cuda_status(cudaStreamSynchronize(ctx->stream));
+    return ibip_cuda_status(ibip_sync(ctx, ctx->stream));
 }
 
 // Post-processing of a batched call (trapping, curves) for a group of its
@@ -256,6 +256,14 @@ int batch_early(void *user, int n_done, const int *done)
     ctx->stream = keep;
     P.early_err = st;
     return st;
+}
+
+cudaError_t ibip_sync(ibip_ctx *ctx, cudaStream_t s)
+{
+    if (!ctx->ev_block) return cudaStreamSynchronize(s);
+    const cudaError_t e = cudaEventRecord(ctx->ev_block, s);
+    if (e != cudaSuccess) return e;
+    return cudaEventSynchronize(ctx->ev_block);
 }
 
 extern "C" {
@@ -327,6 +335,12 @@ int ibip_destroy(ibip_ctx *ctx)
         cudaStreamSynchronize(ctx->own_stream);
         cudaStreamDestroy(ctx->own_stream);
     }
+    if (ctx->stream_inv) {
+        cudaStreamSynchronize(ctx->stream_inv);
+        cudaStreamDestroy(ctx->stream_inv);
+    }
+    if (ctx->ev_inv) cudaEventDestroy(ctx->ev_inv);
+    if (ctx->ev_block) cudaEventDestroy(ctx->ev_block);
     if (ctx->h_done) cudaFreeHost(ctx->h_done);
     if (ctx->h_cancel) cudaFreeHost((void *)ctx->h_cancel);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
@@ -361,7 +375,7 @@ int ibip_synchronize(ibip_ctx *ctx)
 {
     if (!ctx) return IBIP_ERR_ARG;
     DeviceGuard g(ctx->device);
-    return ibip_cuda_status(cudaStreamSynchronize(ctx->stream));
+    return ibip_cuda_status(ibip_sync(ctx, ctx->stream));
 }
 
 int64_t ibip_launch_count(const ibip_ctx *ctx) { return ctx ? ctx->launches : -1; }
@@ -428,10 +442,10 @@ int ibip_profile_enable(ibip_ctx *ctx, int on)
     if (on) {
         if (!ctx->prof) ctx->prof = new (std::nothrow) ProfLog;
         if (!ctx->prof) return IBIP_ERR_OOM;
-        cudaStreamSynchronize(ctx->stream);
+        ibip_sync(ctx, ctx->stream);
         ((ProfLog *)ctx->prof)->clear();
     } else if (ctx->prof) {
-        cudaStreamSynchronize(ctx->stream);
+        ibip_sync(ctx, ctx->stream);
         delete (ProfLog *)ctx->prof;
         ctx->prof = nullptr;
     }
@@ -446,7 +460,7 @@ int ibip_profile_read(ibip_ctx *ctx, int cls, double *h_ms, int64_t *h_spans)
     *h_spans = 0;
     ProfLog *p = (ProfLog *)ctx->prof;
     if (!p) return IBIP_OK;
-    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    cudaError_t e = ibip_sync(ctx, ctx->stream);
     if (e != cudaSuccess) return ibip_cuda_status(e);
     for (auto &r : p->recs) {
         if (r.cls != cls) continue;
@@ -561,7 +575,7 @@ int ibip_trapping(ibip_ctx *ctx, const int32_t *seq, ibip_dims dims, int outlet,
     if (st) return st;
     st = ibip_trap_finish(ctx, seq, M, dims, rerank, trapped, seq_out);
     if (st) return st;
-    return ibip_cuda_status(cudaStreamSynchronize(ctx->stream));
+    return ibip_cuda_status(ibip_sync(ctx, ctx->stream));
 }
 
 int ibip_trapping_ex(ibip_ctx *ctx, const int32_t *seq, ibip_dims dims, int outlet, uint8_t *trapped,
@@ -579,7 +593,7 @@ int ibip_trapping_ex(ibip_ctx *ctx, const int32_t *seq, ibip_dims dims, int outl
     if (st) return st;
     st = ibip_trap_finish(ctx, seq, M, dims, 1, trapped, seq_out, step_r2, n_steps, step_r2_out, h_n_steps_out);
     if (st) return st;
-    return ibip_cuda_status(cudaStreamSynchronize(ctx->stream));
+    return ibip_cuda_status(ibip_sync(ctx, ctx->stream));
 }
 
 int ibip_size_image(ibip_ctx *ctx, const int32_t *seq, ibip_dims dims, const int32_t *step_r2, int64_t n_steps,
@@ -611,7 +625,7 @@ int ibip_morph_drainage_ex(ibip_ctx *ctx, const uint8_t *image, const int32_t *d
     if (!W) return IBIP_ERR_OOM;
     int st = ibip_level_init(ctx, image, dims, level);
     if (st) return st;
-    if (n_levels == 0) return ibip_cuda_status(cudaStreamSynchronize(ctx->stream));
+    if (n_levels == 0) return ibip_cuda_status(ibip_sync(ctx, ctx->stream));
     st = ibip_maximin_launch(ctx, dt2, dims, inlet, W, kMaxRounds);
     if (st) return st;
     // radii above the largest widest-path value trim to the empty set: skip
@@ -707,7 +721,7 @@ int ibip_invade_batched(ibip_ctx *ctx, int32_t n, ibip_job *jobs)
         !ibip_scratch(ctx, SC_SCAN, ibip_scan_scratch_bytes(cnt_total + 1)) || !ibip_scratch(ctx, SC_SMALL, kSmallBytes))
         return IBIP_ERR_OOM;
     st = ibip_invade_batch_run(ctx, n, it.data(), batch_early, &P);
-    cudaError_t e2 = cudaStreamSynchronize(ctx->stream2);
+    cudaError_t e2 = ibip_sync(ctx, ctx->stream2);
     if (st && st != P.early_err) return st;
     if (e2 != cudaSuccess) return ibip_cuda_status(e2);
     std::vector<int> rest;
@@ -715,7 +729,7 @@ int ibip_invade_batched(ibip_ctx *ctx, int32_t n, ibip_job *jobs)
         if (!P.early[j]) rest.push_back(j);
     st = batch_post_group(P, rest, false);
     if (st) return st;
-    cudaError_t e = cudaStreamSynchronize(s);
+    cudaError_t e = ibip_sync(ctx, s);
     if (e != cudaSuccess) return ibip_cuda_status(e);
     for (int j = 0; j < n; j++)
         if (jobs[j].status == IBIP_ERR_CANCELLED && ctx->h_cancel) *ctx->h_cancel = 0;   // the request is served
@@ -734,6 +748,21 @@ int ibip_equal_saturation(ibip_ctx *ctx, const int32_t *seq, const int32_t *leve
         return IBIP_ERR_ARG;
     DeviceGuard g(ctx->device);
     return ibip_eqsat_launch(ctx, seq, level, dims, n_steps, n_levels, h_steps, h_diff, h_count);
+}
+
+int ibip_pc_envelope(ibip_ctx *ctx, const int32_t *seq, ibip_dims dims, const int32_t *step_r2, int64_t n_steps,
+                     const int32_t *h_r2_levels, int32_t n_levels, int64_t *h_steps, int64_t *h_count)
+{
+    NvtxRange nvtx_range("ibip_pc_envelope");
+    if (!ctx || !seq || !dims_ok(dims) || n_steps < 0 || n_steps >= (1ll << 31) || (n_steps > 0 && !step_r2) ||
+        n_levels < 1 || n_levels > 254 || !h_r2_levels || !h_steps || !h_count)
+        return IBIP_ERR_ARG;
+    for (int i = 0; i < n_levels; i++) {
+        if (h_r2_levels[i] < 1) return IBIP_ERR_ARG;
+        if (i > 0 && h_r2_levels[i] >= h_r2_levels[i - 1]) return IBIP_ERR_ARG;
+    }
+    DeviceGuard g(ctx->device);
+    return ibip_envelope_launch(ctx, seq, dims, step_r2, n_steps, h_r2_levels, n_levels, h_steps, h_count);
 }
 
 int ibip_pc_curve(ibip_ctx *ctx, const int32_t *seq, ibip_dims dims, const int32_t *step_r2, int64_t n_steps,

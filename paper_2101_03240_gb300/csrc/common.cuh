@@ -63,6 +63,18 @@ struct ibip_ctx {
     size_t arena_size, arena_used;
     // Kernels share the device with other streams: no cooperative launches.
     int no_coop;
+    // Server slots: the invasion kernel goes to this stream (of the
+    // device's highest priority, owned by the context, with an event that
+    // orders it after the work queued before it), so that its one CTA is
+    // placed ahead of the waiting blocks of other jobs' wide kernels; null
+    // elsewhere.
+    cudaStream_t stream_inv;
+    cudaEvent_t ev_inv;
+    // Server slots: an event created with cudaEventBlockingSync; the
+    // library's waits record it and sleep on it instead of spinning, so
+    // that many slot threads on few host cores do not starve each other's
+    // launches.  Null elsewhere (plain stream synchronisation).
+    cudaEvent_t ev_block;
     // Batched invasion: a second stream for post-processing images whose
     // invasion is done while others still run, and host-mapped completion
     // records written by the invasion CTAs.
@@ -92,6 +104,8 @@ typedef int (*IbipBatchEarly)(void *user, int n_done, const int *done_items);
 
 // Profiling: CUDA-event pairs around each kernel class, on the context's
 // stream, only while ibip_profile_enable(ctx, 1) is in effect.
+// Waits for the work queued on stream s (see ibip_ctx::ev_block).
+cudaError_t ibip_sync(ibip_ctx *ctx, cudaStream_t s);
 void ibip_prof_begin(ibip_ctx *ctx, int cls);
 void ibip_prof_end(ibip_ctx *ctx, int cls);
 
@@ -169,6 +183,9 @@ int ibip_literal_run(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, 
 // Equal-saturation comparison of a sequence image with opening levels.
 int ibip_eqsat_launch(ibip_ctx *ctx, const int32_t *seq, const int32_t *level, ibip_dims d, int64_t K, int L,
                       int64_t *h_steps, int64_t *h_diff, int64_t *h_count);
+// Drainage envelope at opening levels (ibip_pc_envelope).
+int ibip_envelope_launch(ibip_ctx *ctx, const int32_t *seq, ibip_dims d, const int32_t *step_r2, int64_t K,
+                         const int32_t *h_levels, int L, int64_t *h_steps, int64_t *h_count);
 // Trapped mask and saturation / Pc curve of many images in one launch per
 // stage (batched call): M null = no trapping, S null = no curve.
 struct IbipCurveItem {

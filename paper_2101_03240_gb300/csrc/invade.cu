@@ -1951,7 +1951,7 @@ int invade_setup(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, int6
         int st = ibip_scan_incl_i32(ctx, incl, incl, (int64_t)maxd + 1);
         if (st) return st;
         cudaMemcpyAsync(h, incl + maxd, sizeof(int), cudaMemcpyDeviceToHost, s);
-        if (cudaStreamSynchronize(s) != cudaSuccess) return IBIP_ERR_CUDA;
+        if (ibip_sync(ctx, s) != cudaSuccess) return IBIP_ERR_CUDA;
         B = h[0];
     }
     Bucket bk{incl, B, hasinf};
@@ -2015,7 +2015,7 @@ int ibip_invade_run(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, i
     k_stats<<<ctx->sm_count * 8, 256, 0, s>>>(dt2, N, stats);
     IBIP_LAUNCH(ctx);
     cudaMemcpyAsync(h, stats, 3 * sizeof(int), cudaMemcpyDeviceToHost, s);
-    if (cudaStreamSynchronize(s) != cudaSuccess) return IBIP_ERR_CUDA;
+    if (ibip_sync(ctx, s) != cudaSuccess) return IBIP_ERR_CUDA;
     const int maxd = h[0], npore = h[1], hasinf = h[2];
     if (npore == 0) {
         if (!resume) {
@@ -2026,7 +2026,7 @@ int ibip_invade_run(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, i
         for (int i = 0; i < kNOut; i++) h_out[i] = 0;
         h_out[0] = k0;
         h_out[1] = IBIP_OK;
-        return ibip_cuda_status(cudaStreamSynchronize(s));
+        return ibip_cuda_status(ibip_sync(ctx, s));
     }
     const JobSizes z = job_sizes(d, npore);
     JobMem mem;
@@ -2052,6 +2052,14 @@ int ibip_invade_run(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, i
     const bool prof = a.trace != nullptr;   // phase timers and the trace: a separate kernel
     const size_t dyn = invade_dyn_smem(a, l1smem);
     ibip_prof_begin(ctx, IBIP_K_INVADE);
+    if (ctx->stream_inv) {
+        // server slot: the kernel runs on the high-priority stream, after
+        // everything queued so far on the slot's own stream
+        if (cudaEventRecord(ctx->ev_inv, s) != cudaSuccess ||
+            cudaStreamWaitEvent(ctx->stream_inv, ctx->ev_inv, 0) != cudaSuccess)
+            return ibip_cuda_status(cudaGetLastError());
+        s = ctx->stream_inv;
+    }
     if (l1smem) {
         if (prof) {
             allow_max_dyn_smem((const void *)k_invade<true, true>);
@@ -2073,7 +2081,7 @@ int ibip_invade_run(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, i
     ibip_prof_end(ctx, IBIP_K_INVADE);
     int64_t *ho = (int64_t *)ctx->h_pinned;
     cudaMemcpyAsync(ho, mem.out, kNOut * sizeof(int64_t), cudaMemcpyDeviceToHost, s);
-    cudaError_t e = cudaStreamSynchronize(s);
+    cudaError_t e = ibip_sync(ctx, s);
     if (e != cudaSuccess) return ibip_cuda_status(e);
     for (int i = 0; i < kNOut; i++) h_out[i] = ho[i];
     if (h_out[1] == IBIP_ERR_CANCELLED && ctx->h_cancel) *ctx->h_cancel = 0;   // the request is served
@@ -2114,7 +2122,7 @@ int ibip_invade_batch_run(ibip_ctx *ctx, int n, IbipBatchItem *it, IbipBatchEarl
     k_stats_b<<<blk_st, kVoxBlock, 0, s>>>(dsj, n, st3);
     IBIP_LAUNCH(ctx);
     cudaMemcpyAsync(h, st3, (size_t)3 * n * sizeof(int), cudaMemcpyDeviceToHost, s);
-    if (cudaStreamSynchronize(s) != cudaSuccess) return IBIP_ERR_CUDA;
+    if (ibip_sync(ctx, s) != cudaSuccess) return IBIP_ERR_CUDA;
     std::vector<int> maxd(n), npore(n), hasinf(n);
     size_t total = 0;
     std::vector<JobSizes> z(n);
@@ -2177,7 +2185,7 @@ int ibip_invade_batch_run(ibip_ctx *ctx, int n, IbipBatchItem *it, IbipBatchEarl
         k_pres_base_b<<<(m0 + 127) / 128, 128, 0, s>>>(djobs, m0, pres);
         IBIP_LAUNCH(ctx);
         cudaMemcpyAsync(sj.data(), djobs, (size_t)m0 * sizeof(SortJob), cudaMemcpyDeviceToHost, s);
-        if (cudaStreamSynchronize(s) != cudaSuccess) return IBIP_ERR_CUDA;
+        if (ibip_sync(ctx, s) != cudaSuccess) return IBIP_ERR_CUDA;
         // chunking of each image's counting sort, as in the one-image set-up
         const int wpb = 4;
         int64_t mat_total = 0;
@@ -2287,14 +2295,14 @@ int ibip_invade_batch_run(ibip_ctx *ctx, int n, IbipBatchItem *it, IbipBatchEarl
                 }
                 std::this_thread::yield();
             }
-            cudaError_t e = cudaStreamSynchronize(s);
+            cudaError_t e = ibip_sync(ctx, s);
             if (e != cudaSuccess) return ibip_cuda_status(e);
             return first_err;
         }
         // steps and status of every job
         int64_t *ho = (int64_t *)ctx->h_pinned;
         for (int q = 0; q < m; q++) cudaMemcpyAsync(ho + 2 * q, outs[idx[q]], 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s);
-        cudaError_t e = cudaStreamSynchronize(s);
+        cudaError_t e = ibip_sync(ctx, s);
         if (e != cudaSuccess) return ibip_cuda_status(e);
         for (int q = 0; q < m; q++) {
             it[idx[q]].n_steps = ho[2 * q];
@@ -2302,7 +2310,7 @@ int ibip_invade_batch_run(ibip_ctx *ctx, int n, IbipBatchItem *it, IbipBatchEarl
         }
     } else {
         ibip_prof_end(ctx, IBIP_K_RANK);
-        cudaError_t e = cudaStreamSynchronize(s);
+        cudaError_t e = ibip_sync(ctx, s);
         if (e != cudaSuccess) return ibip_cuda_status(e);
     }
     return IBIP_OK;

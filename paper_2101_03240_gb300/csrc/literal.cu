@@ -413,7 +413,7 @@ int ibip_literal_run(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, 
     cudaMemsetAsync(stats, 0, 3 * sizeof(int), s);
     ibip_stats_launch(ctx, dt2, N, stats);
     cudaMemcpyAsync(h, stats, 3 * sizeof(int), cudaMemcpyDeviceToHost, s);
-    if (cudaStreamSynchronize(s) != cudaSuccess) return IBIP_ERR_CUDA;
+    if (ibip_sync(ctx, s) != cudaSuccess) return IBIP_ERR_CUDA;
     const int maxd = h[0], npore = h[1], hasinf = h[2];
     k_lit_init<<<gs, 256, 0, s>>>(dt2, N, seq, cstep);
     IBIP_LAUNCH(ctx);
@@ -421,7 +421,7 @@ int ibip_literal_run(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, 
         ibip_prof_end(ctx, IBIP_K_RANK);
         h_out[0] = 0;
         h_out[1] = IBIP_OK;
-        return ibip_cuda_status(cudaStreamSynchronize(s));
+        return ibip_cuda_status(ibip_sync(ctx, s));
     }
     // buckets: distinct values in decreasing order
     int32_t *incl = (int32_t *)ibip_scratch(ctx, SC_PRES, ((size_t)maxd + 2) * sizeof(int32_t));
@@ -434,7 +434,7 @@ int ibip_literal_run(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, 
         int st = ibip_scan_incl_i32(ctx, incl, incl, (int64_t)maxd + 1);
         if (st) return st;
         cudaMemcpyAsync(h, incl + maxd, sizeof(int), cudaMemcpyDeviceToHost, s);
-        if (cudaStreamSynchronize(s) != cudaSuccess) return IBIP_ERR_CUDA;
+        if (ibip_sync(ctx, s) != cudaSuccess) return IBIP_ERR_CUDA;
         B = h[0];
     }
     const int nw = (B + 31) / 32;
@@ -506,7 +506,7 @@ int ibip_literal_run(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, 
     ibip_prof_end(ctx, IBIP_K_INVADE);
     int64_t *ho = (int64_t *)ctx->h_pinned;
     cudaMemcpyAsync(ho, a.out, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s);
-    cudaError_t e = cudaStreamSynchronize(s);
+    cudaError_t e = ibip_sync(ctx, s);
     if (e != cudaSuccess) return ibip_cuda_status(e);
     h_out[0] = ho[0];
     h_out[1] = ho[1];

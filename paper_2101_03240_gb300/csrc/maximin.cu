@@ -302,7 +302,16 @@ int ibip_maximin_multi(ibip_ctx *ctx, int n, const IbipMaximinJob *jobs, int max
     int *h = (int *)ctx->h_pinned;
     if (ctx->no_coop) {
         // rounds in chunks; the next round's list size is read back after
-        // each chunk (an empty round's launch returns at once)
+        // each chunk (an empty round's launch returns at once).  A server
+        // slot issues them on its high-priority stream: each round is a
+        // short launch that would otherwise wait behind the wide kernels of
+        // the other jobs.
+        if (ctx->stream_inv) {
+            if (cudaEventRecord(ctx->ev_inv, s) != cudaSuccess ||
+                cudaStreamWaitEvent(ctx->stream_inv, ctx->ev_inv, 0) != cudaSuccess)
+                return ibip_cuda_status(cudaGetLastError());
+            s = ctx->stream_inv;
+        }
         constexpr int kChunkRounds = 16;
         const int grid = ctx->sm_count;
         int r = 0;
@@ -312,7 +321,7 @@ int ibip_maximin_multi(ibip_ctx *ctx, int n, const IbipMaximinJob *jobs, int max
                 IBIP_LAUNCH(ctx);
             }
             cudaMemcpyAsync(h, a.count + r, sizeof(int), cudaMemcpyDeviceToHost, s);
-            cudaError_t e = cudaStreamSynchronize(s);
+            cudaError_t e = ibip_sync(ctx, s);
             if (e != cudaSuccess) return ibip_cuda_status(e);
             if (h[0] == 0) break;
             if (r >= rounds) {
@@ -336,7 +345,7 @@ int ibip_maximin_multi(ibip_ctx *ctx, int n, const IbipMaximinJob *jobs, int max
     IBIP_LAUNCH(ctx);
     if (e != cudaSuccess) return ibip_cuda_status(e);
     cudaMemcpyAsync(h, a.status, 3 * sizeof(int), cudaMemcpyDeviceToHost, s);
-    e = cudaStreamSynchronize(s);
+    e = ibip_sync(ctx, s);
     ibip_prof_end(ctx, IBIP_K_MAXIMIN);
     if (e != cudaSuccess) return ibip_cuda_status(e);
     // diagnostics of the last propagation: rounds, tile activations, sweeps
@@ -347,7 +356,7 @@ int ibip_maximin_multi(ibip_ctx *ctx, int n, const IbipMaximinJob *jobs, int max
         for (int r0 = 0; r0 < nr; r0 += 8192) {
             const int c = nr - r0 < 8192 ? nr - r0 : 8192;
             cudaMemcpyAsync(hc, a.count + r0, (size_t)c * sizeof(int), cudaMemcpyDeviceToHost, s);
-            if (cudaStreamSynchronize(s) != cudaSuccess) return IBIP_ERR_CUDA;
+            if (ibip_sync(ctx, s) != cudaSuccess) return IBIP_ERR_CUDA;
             for (int q = 0; q < c; q++) act += hc[q];
         }
         ctx->inv_stats[30] = nr;

@@ -2,6 +2,7 @@
 // 2.2.2; Washburn relation as written in Section 2.4.1), plus the helpers
 // trapping and opening need: thresholding against seq, re-ranking and
 // level counts.
+#include <algorithm>
 #include <vector>
 
 #include "common.cuh"
@@ -148,6 +149,25 @@ __global__ void k_eqsat(const int32_t *__restrict__ seq, const int32_t *__restri
     __syncthreads();
     for (int i = threadIdx.x; i <= L; i += blockDim.x)
         if (s_h[i]) atomicAdd(dh + i, s_h[i]);
+}
+
+// Drainage envelope at the opening's levels (Sections 2.2.2 and 3.1.1): the
+// levels a step's sphere lies below are a prefix [0, p) of the strictly
+// decreasing T (p = the first level with T <= r2); the first step below
+// level i is the smallest step with p > i, collected as a minimum per p - 1
+// and completed by a suffix minimum over the levels.
+__global__ void k_env_first(const int32_t *__restrict__ r2, int64_t K, const int32_t *__restrict__ T, int L,
+                            int32_t *first)
+{
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < K; j += (int64_t)gridDim.x * blockDim.x) {
+        const int v = r2[j];
+        int lo = 0, hi = L;   // first level with T <= v
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (T[mid] <= v) hi = mid; else lo = mid + 1;
+        }
+        if (lo > 0) atomicMin(first + lo - 1, (int32_t)j);
+    }
 }
 
 // re-ranked trapping: the radius of every surviving step, in its new order
@@ -303,7 +323,7 @@ int ibip_trap_finish(ibip_ctx *ctx, const int32_t *seq, const int32_t *M, ibip_d
     IBIP_LAUNCH(ctx);
     int *h = (int *)ctx->h_pinned;
     cudaMemcpyAsync(h, mx, sizeof(int), cudaMemcpyDeviceToHost, s);
-    if (cudaStreamSynchronize(s) != cudaSuccess) return IBIP_ERR_CUDA;
+    if (ibip_sync(ctx, s) != cudaSuccess) return IBIP_ERR_CUDA;
     const int K = h[0];
     int32_t *mark = (int32_t *)ibip_scratch(ctx, SC_HIST, ((size_t)K + 2) * sizeof(int32_t));
     if (!mark) return IBIP_ERR_OOM;
@@ -321,7 +341,7 @@ int ibip_trap_finish(ibip_ctx *ctx, const int32_t *seq, const int32_t *M, ibip_d
     }
     if (h_nout) {
         cudaMemcpyAsync(h, mark + K, sizeof(int), cudaMemcpyDeviceToHost, s);
-        if (cudaStreamSynchronize(s) != cudaSuccess) return IBIP_ERR_CUDA;
+        if (ibip_sync(ctx, s) != cudaSuccess) return IBIP_ERR_CUDA;
         *h_nout = h[0];
     }
     ibip_prof_end(ctx, IBIP_K_TRAP);
@@ -345,7 +365,7 @@ int ibip_max_launch(ibip_ctx *ctx, const int32_t *a, int64_t n, int *h_max)
     k_max_seq<<<ctx->sm_count * 8, 256, 0, s>>>(a, n, mx);
     IBIP_LAUNCH(ctx);
     cudaMemcpyAsync(ctx->h_pinned, mx, sizeof(int), cudaMemcpyDeviceToHost, s);
-    cudaError_t e = cudaStreamSynchronize(s);
+    cudaError_t e = ibip_sync(ctx, s);
     if (e != cudaSuccess) return ibip_cuda_status(e);
     *h_max = *(int *)ctx->h_pinned;
     return IBIP_OK;
@@ -368,7 +388,7 @@ int ibip_level_counts(ibip_ctx *ctx, const int32_t *level, ibip_dims d, int L, i
     IBIP_LAUNCH(ctx);
     int32_t *h = (int32_t *)ctx->h_pinned;
     cudaMemcpyAsync(h, cnt, ((size_t)L + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-    cudaError_t e = cudaStreamSynchronize(s);
+    cudaError_t e = ibip_sync(ctx, s);
     if (e != cudaSuccess) return ibip_cuda_status(e);
     int64_t run = 0;
     for (int i = 0; i < L; i++) { run += h[i + 1]; h_counts[i] = run; }
@@ -403,7 +423,7 @@ int ibip_eqsat_launch(ibip_ctx *ctx, const int32_t *seq, const int32_t *level, i
     cudaMemcpyAsync(h, lv + 1, (size_t)L * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
     cudaMemcpyAsync(h + L, kq, (size_t)L * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
     cudaMemcpyAsync(h + 2 * L, dh, ((size_t)L + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-    cudaError_t e = cudaStreamSynchronize(s);
+    cudaError_t e = ibip_sync(ctx, s);
     if (e != cudaSuccess) return ibip_cuda_status(e);
     int64_t run = 0;
     for (int i = 0; i < L; i++) {
@@ -412,6 +432,47 @@ int ibip_eqsat_launch(ibip_ctx *ctx, const int32_t *seq, const int32_t *level, i
         if (h_steps) h_steps[i] = h[L + i];
         h_diff[i] = run;
     }
+    return IBIP_OK;
+}
+
+int ibip_envelope_launch(ibip_ctx *ctx, const int32_t *seq, ibip_dims d, const int32_t *step_r2, int64_t K,
+                         const int32_t *h_levels, int L, int64_t *h_steps, int64_t *h_count)
+{
+    cudaStream_t s = ctx->stream;
+    const int64_t N = nvox(d);
+    const int gs = ctx->sm_count * 8;
+    // layout: cum[K + 2] | T[L] | first[L] | npore
+    const size_t words = (size_t)K + 2 + 2 * (size_t)L + 1;
+    int32_t *w = (int32_t *)ibip_scratch(ctx, SC_HIST, words * sizeof(int32_t));
+    if (!w) return IBIP_ERR_OOM;
+    int32_t *cum = w, *T = cum + K + 2, *first = T + L, *np = first + L;
+    cudaMemsetAsync(cum, 0, ((size_t)K + 2) * sizeof(int32_t), s);
+    cudaMemsetAsync(first, 0x7f, (size_t)L * sizeof(int32_t), s);   // 0x7f7f7f7f: no step below
+    cudaMemcpyAsync(T, h_levels, (size_t)L * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+    k_hist_seq<<<gs, 256, 0, s>>>(seq, N, K, cum, np);
+    IBIP_LAUNCH(ctx);
+    int st = ibip_scan_incl_i32(ctx, cum, cum, K + 1);   // cum[k] = voxels with 1 <= seq <= k
+    if (st) return st;
+    if (K > 0) {
+        k_env_first<<<(int)std::min<int64_t>((K + 255) / 256, gs), 256, 0, s>>>(step_r2, K, T, L, first);
+        IBIP_LAUNCH(ctx);
+    }
+    int32_t *h = (int32_t *)ctx->h_pinned;   // L <= 254
+    cudaMemcpyAsync(h, first, (size_t)L * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    cudaError_t e = ibip_sync(ctx, s);
+    if (e != cudaSuccess) return ibip_cuda_status(e);
+    int64_t run = K;
+    for (int i = L - 1; i >= 0; i--) {   // suffix minimum: steps below level i+1 are below level i too
+        if ((int64_t)h[i] < run) run = h[i];
+        h_steps[i] = run;
+    }
+    // the counts at those steps
+    for (int i = 0; i < L; i++) {
+        cudaMemcpyAsync(h + i, cum + h_steps[i], sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    }
+    e = ibip_sync(ctx, s);
+    if (e != cudaSuccess) return ibip_cuda_status(e);
+    for (int i = 0; i < L; i++) h_count[i] = h[i];
     return IBIP_OK;
 }
 

@@ -193,7 +193,7 @@ void slot_main(ibip_server *S, int slot)
         const int st = ibip_run_job(ctx, job);
         // an early error return may leave kernels queued that still write
         // into this job's piece: drain the stream before the piece is freed
-        cudaStreamSynchronize(ctx->stream);
+        ibip_sync(ctx, ctx->stream);
         if (st == IBIP_ERR_CUDA) cudaGetLastError();
         const int64_t t_end = now_ns();
         const int64_t used = (int64_t)ctx->arena_used;
@@ -237,17 +237,40 @@ int ibip_server_create(ibip_server **out, ibip_ctx *ctx, size_t mem_budget, int 
         st = IBIP_ERR_OOM;
     }
     S->alloc = RangeAlloc(S->arena ? mem_budget : 0);
+    // every slot's wide kernels (EDT, rank sort, widest path, curve) queue
+    // at the device's lowest stream priority and its one-CTA invasion at the
+    // highest: when an SM frees up, a waiting invasion is placed before more
+    // blocks of the other jobs' wide kernels
+    int prio_low = 0, prio_high = 0;
+    if (cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high) != cudaSuccess) {
+        cudaGetLastError();
+        prio_low = prio_high = 0;
+    }
     for (int i = 0; st == IBIP_OK && i < max_slots; i++) {
         ibip_ctx *c = nullptr;
-        cudaStream_t s = nullptr;
-        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaStream_t s = nullptr, si = nullptr;
+        cudaEvent_t ev = nullptr, evb = nullptr;
+        if (cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, prio_low) != cudaSuccess) {
             cudaGetLastError();
             st = IBIP_ERR_CUDA;
             break;
         }
+        if (cudaStreamCreateWithPriority(&si, cudaStreamNonBlocking, prio_high) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&evb, cudaEventDisableTiming | cudaEventBlockingSync) != cudaSuccess) {
+            cudaGetLastError();
+            if (ev) cudaEventDestroy(ev);
+            if (si) cudaStreamDestroy(si);
+            cudaStreamDestroy(s);
+            st = IBIP_ERR_CUDA;
+            break;
+        }
         st = ibip_create(&c, S->device, s);
-        if (st) { cudaStreamDestroy(s); break; }
+        if (st) { cudaStreamDestroy(s); cudaStreamDestroy(si); cudaEventDestroy(ev); cudaEventDestroy(evb); break; }
         c->no_coop = 1;
+        c->stream_inv = si;   // owned by the context from here on
+        c->ev_inv = ev;
+        c->ev_block = evb;
         S->ctxs.push_back(c);
     }
     if (st == IBIP_OK) {

@@ -12,7 +12,16 @@ import ctypes as C
 import os
 import threading
 
-import torch
+# CUDA maps streams onto CUDA_DEVICE_MAX_CONNECTIONS hardware work queues
+# (8 unless set).  A server runs many slots, each with two streams; when
+# they outnumber the queues, a slot's long one-CTA invasion kernel holds up
+# every later launch of the other streams sharing its queue (small requests
+# then wait for seconds behind a large one).  32 is the largest value; it
+# only takes effect if set before the process creates its CUDA context, and
+# a value the user set is kept.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
+import torch  # noqa: E402
 
 from . import build_lib
 
@@ -109,6 +118,7 @@ def _lib():
                 "ibip_server_wait": (C.c_int, [P, C.c_uint64, i64, C.POINTER(C.c_int), C.POINTER(Result)]),
                 "ibip_server_stats": (C.c_int, [P, C.POINTER(i64), C.c_int]),
                 "ibip_route_pick": (C.c_int, [C.c_int, C.POINTER(i64), C.POINTER(i64), i64]),
+                "ibip_pc_envelope": (C.c_int, [P, P, Dims, P, i64, P, i32, C.POINTER(i64), C.POINTER(i64)]),
                 "ibip_router_create": (C.c_int, [C.POINTER(P), C.c_int, C.POINTER(C.c_int), C.c_size_t, C.c_int]),
                 "ibip_router_destroy": (C.c_int, [P]),
                 "ibip_router_route": (C.c_int, [P, Dims, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
@@ -526,6 +536,23 @@ class Context:
         if st != OK:
             raise IbipError("ibip_equal_saturation", st)
         return list(k), list(d), list(n)
+
+    def pc_envelope(self, seq, step_r2, levels):
+        """Drainage envelope at opening levels (ibip_pc_envelope): per level,
+        (steps taken before the running-minimum sphere drops below it,
+        voxels invaded by then)."""
+        _need(seq, torch.int32, "seq")
+        K = int(step_r2.numel())
+        L = len(levels)
+        T = (C.c_int32 * max(L, 1))(*[int(t) for t in levels])
+        ks = (C.c_int64 * max(L, 1))()
+        ns = (C.c_int64 * max(L, 1))()
+        self._stream()
+        st = _lib().ibip_pc_envelope(self._h, _ptr(seq), _dims(seq.shape), _ptr(step_r2) if K else None, K, T, L,
+                                     ks, ns)
+        if st != OK:
+            raise IbipError("ibip_pc_envelope", st)
+        return [int(x) for x in ks[:L]], [int(x) for x in ns[:L]]
 
     def pc_curve(self, seq, step_r2, voxel_m=5e-6, sigma=0.072, theta_deg=180.0, sat_image=False):
         _need(seq, torch.int32, "seq")

@@ -92,3 +92,38 @@ def test_matched_opening_spheres200(ctx):
                                   dilate_levels=Td)
     rlev, rcnt = O.morph_drainage(w.image, d, Te, inlet=0, dilate_levels=Td)
     assert np.array_equal(lev.cpu().numpy(), rlev) and cnt == rcnt.tolist()
+
+
+@pytest.mark.parametrize("seed", range(8))
+@pytest.mark.parametrize("rule", ["frontier", "paper"])
+def test_pc_envelope_random(ctx, seed, rule):
+    """The drainage envelope at opening levels (ibip_pc_envelope) against
+    the oracle, on both rules' invasions (the paper rule with its integer
+    radius levels)."""
+    rng = np.random.default_rng(1300 + seed)
+    shape = tuple(int(x) for x in rng.integers(6, 40, 3))
+    img = S.blobs(shape, rng.uniform(1.5, 3.0), rng.uniform(0.5, 0.75), rng) if seed % 2 else \
+        S.sphere_pack(shape, int(rng.integers(2, 5)), rng.uniform(0.35, 0.5), rng)
+    dev = torch.from_numpy(img).cuda()
+    d = ctx.edt(dev)
+    if rule == "paper":
+        seq, _, r2, _, K, st = ctx.invade_literal(dev, d, inlet=seed % 6)
+    else:
+        seq, r2, cen, K, st = ctx.invade(dev, d, inlet=seed % 6)
+    dmax = int(d[dev > 0].max().item()) if bool((dev > 0).any()) else 1
+    T = S.integer_radius_levels(dmax)[0] if rule == "paper" else S.mio_levels(dmax, int(rng.integers(1, 60)))
+    ks, ns = ctx.pc_envelope(seq, r2, T)
+    rk, rn = O.pc_envelope(seq.cpu().numpy(), r2.cpu().numpy(), T)
+    assert ks == list(rk) and ns == list(rn)
+
+
+def test_pc_envelope_blobs48_and_empty(ctx):
+    w = S.c1_blobs48()
+    d = O.edt(w.image)
+    seq, r2, cen, st, K = O.invade(w.image, d, inlet=0)
+    T = S.mio_levels(int(d[w.image > 0].max()), 40)
+    ks, ns = ctx.pc_envelope(torch.from_numpy(seq).cuda(), torch.from_numpy(r2).cuda(), T)
+    rk, rn = O.pc_envelope(seq, r2, T)
+    assert ks == list(rk) and ns == list(rn)
+    z = torch.zeros((3, 4, 5), dtype=torch.int32, device="cuda")
+    assert ctx.pc_envelope(z, torch.zeros(0, dtype=torch.int32, device="cuda"), [4, 1]) == ([0, 0], [0, 0])
