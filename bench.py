@@ -103,7 +103,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--config", choices=["spheres200", "blobs48", "blobs512", "batch256", "serve"],
+    ap.add_argument("--config", choices=["spheres200", "blobs48", "blobs512", "blobs256", "batch256", "serve"],
                     default="blobs512")
     ap.add_argument("--requests", type=int, default=600, help="serve: requests in the Poisson stream")
     ap.add_argument("--budget-gb", type=float, default=20.0,
@@ -123,7 +123,7 @@ def parse():
 def workload(name):
     from paper_2101_03240_gb300 import synth
     return {"spheres200": synth.c2_spheres200, "blobs48": synth.c1_blobs48,
-            "blobs512": synth.c3_blobs512}[name]()
+            "blobs512": synth.c3_blobs512, "blobs256": synth.c3_blobs256}[name]()
 
 
 def peaks():
@@ -792,7 +792,7 @@ def run_ours(args, rank, world):
         "wall_s_timed": t_wall,
         "gpu": torch.cuda.get_device_name(dev),
         "host_cores": os.cpu_count(),
-        "seed": {"spheres200": 2, "blobs48": 1, "blobs512": 3}.get(w.name),
+        "seed": {"spheres200": 2, "blobs48": 1, "blobs512": 3, "blobs256": 3}.get(w.name),
         "paper_context": "about 5 steps/s for the first 3,000 steps of a 250^3 blob image on a laptop CPU "
                          "(Python/SciPy, Fig. 4 caption); context, not a target",
     }

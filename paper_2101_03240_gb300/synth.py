@@ -149,6 +149,14 @@ def c3_blobs512(seed=3) -> Workload:
                     0, 1, mio_levels=40)
 
 
+def c3_blobs256(seed=3) -> Workload:
+    """The 512^3 blob recipe at 256^3 (sigma=(4,8,4), porosity 0.60, inlet
+    x=0, outlet x=255, 40 radii): a smaller case of the same workload for
+    profiler captures."""
+    rng = np.random.default_rng(seed)
+    return Workload("blobs256", blobs((256, 256, 256), (4.0, 8.0, 4.0), 0.60, rng), 0, 1, mio_levels=40)
+
+
 def mixed_edge(i, seed_base, lo, hi):
     """Edge length of mixed_image(i, seed_base, lo, hi) without building it."""
     rng = np.random.default_rng(seed_base + i)
