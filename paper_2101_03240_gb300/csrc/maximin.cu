@@ -40,15 +40,27 @@ constexpr int kMaxRoundsDev = 1 << 16;
 
 __device__ __forceinline__ int as_val(int v) { return v == -1 ? IBIP_INF32 : v; }
 
+// M = val on the unblocked voxels of the face, -1 elsewhere; a warp per
+// row (x, y), lanes along z, no per-voxel division
 __global__ void k_mm_init(const int32_t *__restrict__ val, int nx, int ny, int nz, int face, int32_t *M)
 {
-    const int64_t N = (int64_t)nx * ny * nz;
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (int64_t)gridDim.x * blockDim.x) {
-        int z = (int)(v % nz);
-        int64_t r = v / nz;
-        int y = (int)(r % ny), x = (int)(r / ny);
-        int s = val[v];
-        M[v] = (s != 0 && d_on_face(x, y, z, nx, ny, nz, face)) ? as_val(s) : -1;
+    const int lane = threadIdx.x & 31;
+    const int64_t nrows = (int64_t)nx * ny;
+    const int64_t wstride = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < nrows; row += wstride) {
+        const int x = (int)(row / ny), y = (int)(row - (int64_t)x * ny);
+        const bool row_on = (face == 0 && x == 0) || (face == 1 && x == nx - 1) || (face == 2 && y == 0) ||
+                            (face == 3 && y == ny - 1);
+        const int64_t b = row * nz;
+        for (int z = lane; z < nz; z += 32) {
+            const bool on = row_on || (face == 4 && z == 0) || (face == 5 && z == nz - 1);
+            int m = -1;
+            if (on) {
+                const int sv = val[b + z];
+                if (sv != 0) m = as_val(sv);
+            }
+            M[b + z] = m;
+        }
     }
 }
 

@@ -84,9 +84,14 @@ __global__ void k_level_init(const uint8_t *__restrict__ img, int64_t N, int32_t
         level[v] = img[v] ? -1 : 0;
 }
 
-// maximin value field for opening: dt2 on pore, 0 on solid (blocked)
+// cnt[l] += 1 for 1 <= level <= L: a per-block histogram in shared memory
+// (warp-aggregated: equal levels in a warp cost one shared atomic), added to
+// the global one once per bin and block
 __global__ void k_level_hist(const int32_t *__restrict__ level, int64_t N, int L, int32_t *cnt)
 {
+    extern __shared__ int32_t s_lh[];   // L + 1 bins
+    for (int i = threadIdx.x; i <= L; i += blockDim.x) s_lh[i] = 0;
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < N; base += stride) {
@@ -94,8 +99,11 @@ __global__ void k_level_hist(const int32_t *__restrict__ level, int64_t N, int L
         int l = v < N ? level[v] : 0;
         int key = (l >= 1 && l <= L) ? l : 0;
         unsigned peers = __match_any_sync(0xffffffffu, key);
-        if (key && lane == __ffs(peers) - 1) atomicAdd(cnt + key, __popc(peers));
+        if (key && lane == __ffs(peers) - 1) atomicAdd(s_lh + key, __popc(peers));
     }
+    __syncthreads();
+    for (int i = threadIdx.x + 1; i <= L; i += blockDim.x)
+        if (s_lh[i]) atomicAdd(cnt + i, s_lh[i]);
 }
 
 // Equal-saturation comparison with the opening (Section 3.1.1, by integer
@@ -159,14 +167,24 @@ __global__ void k_eqsat(const int32_t *__restrict__ seq, const int32_t *__restri
 __global__ void k_env_first(const int32_t *__restrict__ r2, int64_t K, const int32_t *__restrict__ T, int L,
                             int32_t *first)
 {
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < K; j += (int64_t)gridDim.x * blockDim.x) {
-        const int v = r2[j];
-        int lo = 0, hi = L;   // first level with T <= v
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (T[mid] <= v) hi = mid; else lo = mid + 1;
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < K; base += stride) {   // block-uniform
+        const int64_t j = base + threadIdx.x;
+        int lo = -1;
+        if (j < K) {
+            const int v = r2[j];
+            int hi = L;   // first level with T <= v
+            lo = 0;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (T[mid] <= v) hi = mid; else lo = mid + 1;
+            }
         }
-        if (lo > 0) atomicMin(first + lo - 1, (int32_t)j);
+        // steps of a warp are consecutive: the lowest lane of each group
+        // with the same target holds the group's smallest step
+        const unsigned peers = __match_any_sync(0xffffffffu, lo);
+        if (lo > 0 && lane == __ffs(peers) - 1) atomicMin(first + lo - 1, (int32_t)j);
     }
 }
 
@@ -384,7 +402,7 @@ int ibip_level_counts(ibip_ctx *ctx, const int32_t *level, ibip_dims d, int L, i
     int32_t *cnt = (int32_t *)ibip_scratch(ctx, SC_HIST, ((size_t)L + 2) * sizeof(int32_t));
     if (!cnt) return IBIP_ERR_OOM;
     cudaMemsetAsync(cnt, 0, ((size_t)L + 2) * sizeof(int32_t), s);
-    k_level_hist<<<ctx->sm_count * 8, 256, 0, s>>>(level, nvox(d), L, cnt);
+    k_level_hist<<<ctx->sm_count * 8, 256, ((size_t)L + 1) * sizeof(int32_t), s>>>(level, nvox(d), L, cnt);
     IBIP_LAUNCH(ctx);
     int32_t *h = (int32_t *)ctx->h_pinned;
     cudaMemcpyAsync(h, cnt, ((size_t)L + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
@@ -411,7 +429,7 @@ int ibip_eqsat_launch(ibip_ctx *ctx, const int32_t *seq, const int32_t *level, i
     IBIP_LAUNCH(ctx);
     int st = ibip_scan_incl_i32(ctx, cum, cum, K + 1);
     if (st) return st;
-    k_level_hist<<<gs, 256, 0, s>>>(level, N, L, lv);
+    k_level_hist<<<gs, 256, ((size_t)L + 1) * sizeof(int32_t), s>>>(level, N, L, lv);
     IBIP_LAUNCH(ctx);
     st = ibip_scan_incl_i32(ctx, lv + 1, lv + 1, L);   // lv[1 + i] = voxels with 1 <= level <= i + 1
     if (st) return st;
