@@ -285,6 +285,27 @@ __device__ __forceinline__ void line_min4_smem(const int32_t *col, int i0, int n
     }
 }
 
+// 16-byte asynchronous copies global -> shared (bypassing L1): a strip's
+// rows are all in flight at once, with no registers holding them
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Shared memory of a staged pass-y block: the int32 squares of the column
+// strip, plus (when rows of the pass-z output start on 16-byte boundaries,
+// nz % 8 == 0) the raw uint16 strip that the asynchronous copies land in.
+__host__ __device__ __forceinline__ size_t edt_y_smem(int ny, int nz)
+{
+    return (size_t)ny * kStripW * sizeof(int32_t) + ((nz & 7) == 0 ? (size_t)ny * kStripW * sizeof(uint16_t) : 0);
+}
+
 // pass y: strip = (x, all y, 32 z).  blockIdx.x = z strip, blockIdx.y = x.
 // Output: partial sums < cap2, kNone elsewhere.  The staged column holds
 // the squared pass-z distances.
@@ -303,11 +324,38 @@ __device__ __forceinline__ void edt_y_block_smem(const uint16_t *__restrict__ d1
     if (threadIdx.x < kStripW) s_any[threadIdx.x] = 0;
     __syncthreads();
     bool any = false;
+    if ((nz & 7) == 0) {
+        // rows of 32 uint16 as four 16-byte pieces, copied asynchronously
+        // into the raw strip (pieces past nz hold "no feature"), then
+        // squared into the column; element i of the strip is z lane i % 32
+        uint16_t *s_raw = (uint16_t *)(s_col + (size_t)ny * kStripW);
+        const int zs = strip * kStripW;
+        const int npc = min(4, (nz - zs) >> 3);
+        const uint16_t *row0 = d1 + (int64_t)x * ny * nz + zs;
+        for (int q = threadIdx.x; q < ny * 4; q += blockDim.x) {
+            const int y = q >> 2, pc = q & 3;
+            uint16_t *dst = s_raw + y * kStripW + pc * 8;
+            if (pc < npc) {
+                cp_async16(dst, row0 + (int64_t)y * nz + pc * 8);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 8; k++) dst[k] = 0xffff;
+            }
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        for (int i = threadIdx.x; i < ny * kStripW; i += blockDim.x) {   // i % 32 == lane
+            const int v = s_raw[i];
+            any |= v != 0xffff;
+            s_col[i] = v == 0xffff ? kNone : v * v;
+        }
+    } else {
 #pragma unroll 8
-    for (int y = w; y < ny; y += SW) {
-        const int v = ok ? __ldg(d1 + b + (int64_t)y * nz) : 0xffff;
-        any |= v != 0xffff;
-        s_col[y * kStripW + lane] = v == 0xffff ? kNone : v * v;
+        for (int y = w; y < ny; y += SW) {
+            const int v = ok ? __ldg(d1 + b + (int64_t)y * nz) : 0xffff;
+            any |= v != 0xffff;
+            s_col[y * kStripW + lane] = v == 0xffff ? kNone : v * v;
+        }
     }
     if (any) s_any[lane] = 1;
     __syncthreads();
@@ -391,11 +439,31 @@ __device__ __forceinline__ void edt_x_block_smem(const int32_t *__restrict__ g2,
     if (threadIdx.x < kStripW) s_anyx[threadIdx.x] = 0;
     __syncthreads();
     bool any = false;
+    if ((nz & 3) == 0) {
+        // rows of 32 int32 as eight 16-byte pieces copied asynchronously
+        // straight into the column (pieces past nz hold kNone)
+        const int zs = strip * kStripW;
+        const int npc = min(8, (nz - zs) >> 2);
+        const int32_t *row0 = g2 + (int64_t)y * nz + zs;
+        for (int q = threadIdx.x; q < nx * 8; q += blockDim.x) {
+            const int xr = q >> 3, pc = q & 7;
+            int32_t *dst = s_colx + xr * kStripW + pc * 4;
+            if (pc < npc) {
+                cp_async16(dst, row0 + (int64_t)xr * st + pc * 4);
+            } else {
+                dst[0] = kNone; dst[1] = kNone; dst[2] = kNone; dst[3] = kNone;
+            }
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        for (int x = w; x < nx; x += SW) any |= s_colx[x * kStripW + lane] != kNone;
+    } else {
 #pragma unroll 8
-    for (int x = w; x < nx; x += SW) {
-        const int v = ok ? __ldg(g2 + b + x * st) : kNone;
-        any |= v != kNone;
-        s_colx[x * kStripW + lane] = v;
+        for (int x = w; x < nx; x += SW) {
+            const int v = ok ? __ldg(g2 + b + x * st) : kNone;
+            any |= v != kNone;
+            s_colx[x * kStripW + lane] = v;
+        }
     }
     if (any) s_anyx[lane] = 1;
     __syncthreads();
@@ -465,7 +533,7 @@ int edt_passes(ibip_ctx *ctx, Feat feat, ibip_dims d, int cap, int cap2, Epi epi
     k_edt_z<Feat, ZW><<<(nrows + ZW - 1) / ZW, ZW * 32, edt_z_smem(d.nz, ZW), s>>>(feat, nrows, d.nz, cap, d1);
     IBIP_LAUNCH(ctx);
     dim3 gy((d.nz + kStripW - 1) / kStripW, d.nx);
-    size_t sy = (size_t)d.ny * kStripW * sizeof(int32_t);
+    size_t sy = edt_y_smem(d.ny, d.nz);
     if (sy <= kSmemBudget) {
         cudaFuncSetAttribute(k_edt_y<true, SW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget);
         k_edt_y<true, SW><<<gy, SW * 32, sy, s>>>(d1, d.ny, d.nz, cap2, g2);
@@ -726,7 +794,7 @@ extern "C" int ibip_edt_noalloc(const uint8_t *image, ibip_dims d, int32_t *dt2,
     k_edt_z<FeatSolid><<<(nrows + kZWarps - 1) / kZWarps, kZWarps * 32, edt_z_smem(d.nz), s>>>(FeatSolid{image}, nrows,
                                                                                               d.nz, 0xfffe, d1);
     dim3 gy((d.nz + kStripW - 1) / kStripW, d.nx);
-    const size_t sy = (size_t)d.ny * kStripW * sizeof(int32_t);
+    const size_t sy = edt_y_smem(d.ny, d.nz);
     if (sy <= kSmemBudget) {
         cudaFuncSetAttribute(k_edt_y<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget);
         k_edt_y<true><<<gy, kStripWarps * 32, sy, s>>>(d1, d.ny, d.nz, IBIP_INF32, g2);
@@ -763,7 +831,7 @@ int ibip_edt_batch_launch(ibip_ctx *ctx, int n, const uint8_t *const *images, co
         J.blk_y = by; by += ns * d.nx;
         J.blk_x = bx; bx += ns * d.ny;
         smz = std::max(smz, edt_z_smem(d.nz));
-        smy = std::max(smy, (size_t)d.ny * kStripW * sizeof(int32_t));
+        smy = std::max(smy, edt_y_smem(d.ny, d.nz));
         smx = std::max(smx, (size_t)d.nx * kStripW * sizeof(int32_t));
         vox += (nvox(d) + 63) & ~(int64_t)63;
     }
