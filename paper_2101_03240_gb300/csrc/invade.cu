@@ -40,7 +40,7 @@ namespace {
 constexpr int kM = 64;           // batch size (items per iteration)
 constexpr int kNT = 384;         // threads of the persistent CTA
 constexpr int kChunk = 4096;     // voxels per rank-sort chunk (minimum)
-constexpr int kSmemL1Max = 12288;
+constexpr int kSmemL1Max = 12288;   // level-1 words of one image of a batched call (shared memory)
 constexpr int kNOut = kInvStats;   // int64 outputs of the invasion kernel
 static_assert(64 + kNOut * sizeof(long long) <= kSmallBytes, "output slot too small");
 
@@ -1994,6 +1994,29 @@ size_t invade_dyn_smem(const Inv &a, bool l1smem)
     return ((l1smem ? a.NL1 : 0) + (size_t)a.NL2 + a.NL3) * sizeof(u64) + (size_t)a.isq_n * sizeof(int);
 }
 
+// Level 1 of the rank bitmap goes to shared memory whenever it fits beside
+// the kernel's static shared memory within the device's per-block opt-in
+// limit (227 KB on this GPU: about 2.3 M summary bits, i.e. up to ~150 M
+// pore voxels); beyond that it stays in global memory.
+bool l1_fits_smem(const Inv &a)
+{
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, (const void *)k_invade<true, false>) != cudaSuccess) {
+        cudaGetLastError();
+        return a.NL1 <= kSmemL1Max;
+    }
+    cudaFuncAttributes fp;
+    if (cudaFuncGetAttributes(&fp, (const void *)k_invade<true, true>) != cudaSuccess) {
+        cudaGetLastError();
+        return a.NL1 <= kSmemL1Max;
+    }
+    const size_t stat = fa.sharedSizeBytes > fp.sharedSizeBytes ? fa.sharedSizeBytes : fp.sharedSizeBytes;
+    return invade_dyn_smem(a, true) + stat <= (size_t)optin;
+}
+
 }  // namespace
 
 int ibip_invade_run(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, int64_t max_steps,
@@ -2048,7 +2071,7 @@ int ibip_invade_run(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, i
     a.cancel = ctx->d_cancel;
     ibip_prof_end(ctx, IBIP_K_RANK);
     const FastDiv fd_nyz = make_fastdiv((uint32_t)d.ny * (uint32_t)d.nz), fd_nz = make_fastdiv((uint32_t)d.nz);
-    const bool l1smem = a.NL1 <= kSmemL1Max;
+    const bool l1smem = l1_fits_smem(a);
     const bool prof = a.trace != nullptr;   // phase timers and the trace: a separate kernel
     const size_t dyn = invade_dyn_smem(a, l1smem);
     ibip_prof_begin(ctx, IBIP_K_INVADE);
