@@ -209,13 +209,22 @@ def run_batch(args, rank, world):
         ctx.set_autotune(True)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=dev)
 
+    paper = args.rule == "paper"
+
     def batched():
+        if paper:   # EDT + the paper-literal invasion, one thread-block cluster per image
+            res, cs = ctx.invade_literal_batched(imgs, 0)
+            batched.cluster = cs
+            return res
         return ctx.invade_batched(imgs, 0, 1, trapping=True, curve=True)
 
     def single():
         out = []
         for im in imgs:
             d = ctx.edt(im)
+            if paper:
+                out.append(ctx.invade_literal(im, d, inlet=0)[4])
+                continue
             s_, r2, cen, K, st = ctx.invade(im, d, inlet=0)
             tr, so = ctx.trapping(s_, 1)
             Sa, Pc, _ = ctx.pc_curve(so, r2)
@@ -262,7 +271,7 @@ def run_batch(args, rank, world):
         d.copy_(p_, non_blocking=True)
     res = batched()
     for o, r in zip(outs, res):
-        o.copy_(r["seq_out"], non_blocking=True)
+        o.copy_(r["seq"] if paper else r["seq_out"], non_blocking=True)
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
     if rank != 0:
@@ -277,11 +286,14 @@ def run_batch(args, rank, world):
     alg = 8 * nvox_total + 8 * steps_total
     achieved = alg / (inv_ms * 1e-3) / 1e9
     out = {
-        "metric": "batched images/s (EDT+rank+invasion+trapping+Pc per image, bit-exact vs oracle)",
+        "metric": ("batched images/s (EDT+paper-literal invasion per image on its own thread-block cluster, "
+                   "bit-exact vs oracle)") if paper else
+                  "batched images/s (EDT+rank+invasion+trapping+Pc per image, bit-exact vs oracle)",
         "value": job_rate(nimg, world, ms_step * 1e-3), "unit": "images/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": "batch256", "images": nimg, "voxels": nvox_total, "edge": "32..160 log-uniform",
+        "config": {"workload": "batch256_paper_rule" if paper else "batch256", "images": nimg, "voxels": nvox_total,
+                   "edge": "32..160 log-uniform", "cluster_ctas_per_image": getattr(batched, "cluster", None),
                    "mix": "half blobs, half sphere packs", "l2": "flushed between steps (256 MB write)",
                    "parallelism": "replicas%d" % world},
         "per_image_path_images_per_s": nimg / single_s,
@@ -303,6 +315,9 @@ def run_batch(args, rank, world):
         t0 = time.perf_counter()
         for a in sample:
             dd = O.edt(a)
+            if paper:
+                O.invade_literal(a, dd, 0)
+                continue
             sq = O.invade(a, dd, inlet=0)
             so = O.trapping(sq[0], 1)[1]
             O.pc_curve(so, sq[1])

@@ -346,6 +346,44 @@ typedef struct {
  * capacity_steps). */
 IBIP_API int ibip_invade_batched(ibip_ctx *ctx, int32_t n, ibip_job *h_jobs);
 
+/* One image of a batched paper-literal invasion; device pointers unless
+ * stated, the caller owns every buffer.  Outputs as ibip_invade_literal. */
+typedef struct {
+    const uint8_t *image;     /* uint8[N] pore image */
+    ibip_dims dims;
+    int32_t inlet;            /* ibip_face */
+    const int32_t *dt2;       /* int32[N] squared EDT, or NULL (computed) */
+    int64_t max_steps;        /* < 0: no limit */
+    int32_t *seq;             /* int32[N] output */
+    int32_t *cstep;           /* int32[N] output */
+    int32_t *step_r2;         /* int32[capacity_steps] output */
+    int32_t *step_count;      /* int32[capacity_steps] output */
+    int64_t capacity_steps;
+    int64_t n_steps;          /* filled: steps K */
+    int32_t status;           /* filled: this image's status */
+} ibip_literal_job;
+
+/* The paper-literal invasion (ibip_invade_literal, Section 2.1 as printed)
+ * for n images of any sizes: the set-up of every image, then one launch in
+ * which each image runs on a thread-block cluster of its own (CTA 0 of the
+ * cluster keeps the image's bucket bookkeeping, every CTA stamps a share of
+ * each step's spheres), then the final pass of every image.  The CTAs per
+ * cluster come from ibip_set_literal_cluster, else, with autotuning on
+ * (ibip_set_autotune), from timing 1, 2, 4, 8 and 16 on the first call of
+ * each batch shape (image count, total voxels to a power of two), else
+ * enough to fill the SMs.  Results equal ibip_invade_literal per image bit
+ * for bit.  1 <= n <= 4096.  *h_cluster (if not NULL) gets the cluster size
+ * run (the fastest one when this call tuned; fewer CTAs than asked when the
+ * device cannot place the cluster with the batch's bucket bookkeeping; 0
+ * when some image's bookkeeping exceeds shared memory and the images ran
+ * one at a time).  Synchronous; returns IBIP_OK when every image
+ * succeeded, else the first failing image's status. */
+IBIP_API int ibip_invade_literal_batched(ibip_ctx *ctx, int32_t n, ibip_literal_job *h_jobs, int *h_cluster);
+
+/* CTAs per image cluster of ibip_invade_literal_batched: 1, 2, 4, 8 or 16,
+ * or 0 for the automatic choice. */
+IBIP_API int ibip_set_literal_cluster(ibip_ctx *ctx, int cluster);
+
 /* ---- serving: a continuous-batching request loop ----------------------
  * A server owns one device arena of mem_budget bytes and max_slots worker
  * slots, each a host thread with its own non-blocking stream.  Submitted

@@ -563,6 +563,62 @@ int ibip_invade_literal(ibip_ctx *ctx, const uint8_t *image, const int32_t *dt2,
     return IBIP_OK;
 }
 
+int ibip_invade_literal_batched(ibip_ctx *ctx, int32_t n, ibip_literal_job *jobs, int *h_cluster)
+{
+    NvtxRange nvtx_range("ibip_invade_literal_batched");
+    if (!ctx || !jobs || n < 1 || n > kMaxBatch) return IBIP_ERR_ARG;
+    int64_t need_dt2 = 0;
+    for (int j = 0; j < n; j++) {
+        const ibip_literal_job &J = jobs[j];
+        if (!J.image || !J.seq || !J.cstep || !dims_ok(J.dims) || !face_ok(J.inlet) || J.capacity_steps < 0 ||
+            (J.capacity_steps > 0 && (!J.step_r2 || !J.step_count)))
+            return IBIP_ERR_ARG;
+        if (!J.dt2) need_dt2 += (nvox(J.dims) + 63) & ~(int64_t)63;
+    }
+    DeviceGuard g(ctx->device);
+    int32_t *pool = need_dt2 ? (int32_t *)ibip_scratch(ctx, SC_BDT2, (size_t)need_dt2 * sizeof(int32_t)) : nullptr;
+    if (need_dt2 && !pool) return IBIP_ERR_OOM;
+    std::vector<IbipLitItem> it(n);
+    std::vector<const uint8_t *> ims;
+    std::vector<ibip_dims> dms;
+    std::vector<int32_t *> dts;
+    int64_t off = 0;
+    for (int j = 0; j < n; j++) {
+        ibip_literal_job &J = jobs[j];
+        const int32_t *d = J.dt2;
+        if (!d) {
+            int32_t *t = pool + off;
+            off += (nvox(J.dims) + 63) & ~(int64_t)63;
+            ims.push_back(J.image); dms.push_back(J.dims); dts.push_back(t);
+            d = t;
+        }
+        it[j] = IbipLitItem{d, J.dims, J.inlet, J.max_steps < 0 ? INT64_MAX : J.max_steps, J.seq, J.cstep,
+                            J.step_r2, J.step_count, J.capacity_steps, 0, 0};
+    }
+    if (!ims.empty()) {
+        const int st = ibip_edt_batch_launch(ctx, (int)ims.size(), ims.data(), dms.data(), dts.data());
+        if (st) return st;
+    }
+    const int st = ibip_literal_batch_run(ctx, n, it.data(), ctx->lit_cluster, h_cluster);
+    if (st) return st;
+    int first = IBIP_OK;
+    for (int j = 0; j < n; j++) {
+        jobs[j].n_steps = it[j].n_steps;
+        jobs[j].status = it[j].status;
+        if (jobs[j].status == IBIP_OK && jobs[j].n_steps > jobs[j].capacity_steps) jobs[j].status = IBIP_ERR_ARG;
+        if (first == IBIP_OK && jobs[j].status != IBIP_OK) first = jobs[j].status;
+    }
+    return first;
+}
+
+int ibip_set_literal_cluster(ibip_ctx *ctx, int cluster)
+{
+    if (!ctx || !(cluster == 0 || cluster == 1 || cluster == 2 || cluster == 4 || cluster == 8 || cluster == 16))
+        return IBIP_ERR_ARG;
+    ctx->lit_cluster = cluster;
+    return IBIP_OK;
+}
+
 int ibip_trapping(ibip_ctx *ctx, const int32_t *seq, ibip_dims dims, int outlet, int rerank, uint8_t *trapped,
                   int32_t *seq_out)
 {

@@ -33,6 +33,8 @@ enum ScratchSlot {
     SC_BJOBS,     // batched invasion: job table
     SC_BDT2,      // batched invasion: EDTs of images given without one
     SC_LIT,       // paper-literal invasion: bucket lists, counters, bit-plane
+    SC_LITB,      // batched paper-literal invasion: every image's buckets, lists, bit-planes
+    SC_LITJ,      // batched paper-literal invasion: job table, statistics, outputs
     SC_BSORT,     // batched invasion: sort job table, presence pool
     SC_NSLOTS
 };
@@ -83,6 +85,9 @@ struct ibip_ctx {
     // Tile shapes: autotune (0 off, 1 on), a forced EDT tile (index + 1,
     // 0 = automatic) and the file that keeps tuning results ("" = none).
     int autotune, edt_tile;
+    // CTAs per image cluster of the batched paper-literal invasion
+    // (0 = automatic).
+    int lit_cluster;
     char tune_path[512];
     // Cancellation: a host-mapped flag the invasion kernels poll (host and
     // device addresses), and a test hook that fails the n-th scratch
@@ -178,6 +183,21 @@ int ibip_maximin_multi(ibip_ctx *ctx, int n, const IbipMaximinJob *jobs, int max
 // pore voxels, [2] = 1 if any value is infinite (stats zeroed by the caller).
 int ibip_stats_launch(ibip_ctx *ctx, const int32_t *dt2, int64_t N, int *stats);
 // Paper-literal invasion (literal.cu); h_out = [steps, status].
+// One image of a batched paper-literal invasion (ibip_invade_literal_batched).
+struct IbipLitItem {
+    const int32_t *dt2;
+    ibip_dims d;
+    int inlet;
+    int64_t max_steps;
+    int32_t *seq, *cstep, *step_r2, *step_count;
+    int64_t cap;
+    int64_t n_steps;   // filled
+    int status;        // filled
+};
+// All images' setup, then one cluster per image in one launch (cluster =
+// CTAs per image; 0 = automatic, tuned on the first call of a batch shape
+// when ctx->autotune is on).  Writes the cluster size used to *h_cluster.
+int ibip_literal_batch_run(ibip_ctx *ctx, int n, IbipLitItem *items, int cluster, int *h_cluster);
 int ibip_literal_run(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, int64_t max_steps, int32_t *seq,
                      int32_t *cstep, int32_t *step_r2, int32_t *step_count, int64_t cap, int64_t *h_out);
 // Equal-saturation comparison of a sequence image with opening levels.

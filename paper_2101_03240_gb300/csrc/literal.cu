@@ -22,6 +22,8 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <string>
+#include <vector>
 
 #include "common.cuh"
 
@@ -218,7 +220,7 @@ __global__ void __launch_bounds__(kLT, 1) k_lit_steps(Lit a)
 // neighbours, reaching CTA 0's counters through distributed shared memory.
 // Two cluster barriers per step: after the pick, and after the step's work.
 // List entries written by other SMs are read with L2-coherent loads.
-__global__ void __launch_bounds__(kLT, 1) k_lit_cluster(Lit a)
+__device__ __forceinline__ void lit_cluster_run(const Lit &a)
 {
     cg::cluster_group cl = cg::this_cluster();
     extern __shared__ uint32_t s_litc[];
@@ -325,6 +327,25 @@ __global__ void __launch_bounds__(kLT, 1) k_lit_cluster(Lit a)
         a.out[1] = s_loc[3] == 2 ? IBIP_ERR_STEP_LIMIT : (s_loc[3] == 3 ? IBIP_ERR_BOUNDS : IBIP_OK);
     }
     cl.sync();   // CTA 0's shared memory stays alive until every CTA has read it
+}
+
+__global__ void __launch_bounds__(kLT, 1) k_lit_cluster(Lit a) { lit_cluster_run(a); }
+
+// Many images, one cluster each: cluster c (blocks c * size .. c * size +
+// size - 1) runs the steps of image jobs[c] from start to end.
+__global__ void __launch_bounds__(kLT, 1) k_lit_cluster_b(const Lit *__restrict__ jobs)
+{
+    cg::cluster_group cl = cg::this_cluster();
+    const Lit a = jobs[blockIdx.x / cl.num_blocks()];
+    lit_cluster_run(a);
+}
+
+// uninvaded voxels back to -1, every image of a batch (blockIdx.x = image)
+__global__ void k_lit_final_b(const Lit *__restrict__ jobs)
+{
+    const Lit &a = jobs[blockIdx.x];
+    for (int64_t v = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; v < a.N; v += (int64_t)gridDim.y * blockDim.x)
+        if (a.seq[v] == IBIP_INF32) a.seq[v] = -1;
 }
 
 __global__ void k_lit_final(int32_t *seq, int64_t N)
@@ -511,4 +532,276 @@ int ibip_literal_run(ibip_ctx *ctx, const int32_t *dt2, ibip_dims d, int inlet, 
     h_out[0] = ho[0];
     h_out[1] = ho[1];
     return IBIP_OK;
+}
+
+// ---------------------------------------------------------------- batched --
+// Many images, each on a thread-block cluster of its own, in one launch.
+// The set-up of every image (statistics, buckets, the first candidates) runs
+// first, each image's lists and counters carved from one pooled buffer with
+// room for its largest possible bucket count; then one launch of
+// k_lit_cluster_b with one cluster per image that has pore voxels.  Each
+// cluster runs exactly the steps of the one-image kernel, so results equal
+// the one-image calls bit for bit.
+
+namespace {
+
+// Whether clusters of cs CTAs with `book` bytes of shared memory can be
+// placed at all.
+bool lit_cluster_fits(int cs, size_t book)
+{
+    cudaFuncSetAttribute(k_lit_cluster_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLitSmem);
+    cudaFuncSetAttribute(k_lit_cluster_b, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(cs);
+    cfg.blockDim = dim3(kLT);
+    cfg.dynamicSmemBytes = book;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_lit_cluster_b, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return n > 0;
+}
+
+struct LitBatchSizes {
+    size_t incl, list, b4, ne, q, total;
+};
+
+// upper bounds of one image's pooled arrays (buckets bounded by the
+// largest possible squared distance of its box)
+LitBatchSizes lit_batch_sizes(ibip_dims d)
+{
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const int64_t N = nvox(d);
+    const int64_t maxd = (int64_t)(d.nx - 1) * (d.nx - 1) + (int64_t)(d.ny - 1) * (d.ny - 1) +
+                         (int64_t)(d.nz - 1) * (d.nz - 1) + 1;
+    LitBatchSizes z;
+    z.incl = up((size_t)(maxd + 2) * 4);
+    z.list = up((size_t)N * 4);
+    z.b4 = up((size_t)(maxd + 2) * 4);
+    z.ne = up((size_t)((maxd + 33) / 32) * 4);
+    z.q = up((size_t)((N + 31) / 32) * 4);
+    // incl | list | bstart | bval | tail | head | cnt | ne | queued
+    z.total = z.incl + z.list + 5 * z.b4 + z.ne + z.q;
+    return z;
+}
+
+// every image through the one-image path
+int lit_each(ibip_ctx *ctx, int n, IbipLitItem *items)
+{
+    for (int j = 0; j < n; j++) {
+        IbipLitItem &it = items[j];
+        int64_t out[2] = {0, 0};
+        const int st = ibip_literal_run(ctx, it.dt2, it.d, it.inlet, it.max_steps, it.seq, it.cstep, it.step_r2,
+                                        it.step_count, it.cap, out);
+        if (st) return st;
+        it.n_steps = out[0];
+        it.status = (int)out[1];
+    }
+    return IBIP_OK;
+}
+
+// One run of the whole batch with clusters of (at most) cs CTAs: fewer
+// when the device cannot place cs with the batch's bucket bookkeeping, and
+// the one-image path per image when some image's bookkeeping exceeds shared
+// memory.  *cs_used gets the cluster size run (0: one image at a time).
+int lit_batch_once(ibip_ctx *ctx, int n, IbipLitItem *items, int cs, int *cs_used)
+{
+    cudaStream_t s = ctx->stream;
+    const int gs = ctx->sm_count * 8;
+    *cs_used = 0;
+    if (cs == 0) return lit_each(ctx, n, items);
+    // job table | statistics (4 ints per image) | outputs (8 int64 per image)
+    const size_t jt = ((size_t)n * sizeof(Lit) + 255) & ~(size_t)255;
+    const size_t st_b = ((size_t)n * 4 * sizeof(int) + 255) & ~(size_t)255;
+    char *jw = (char *)ibip_scratch(ctx, SC_LITJ, jt + st_b + (size_t)n * 8 * sizeof(int64_t));
+    if (!jw) return IBIP_ERR_OOM;
+    Lit *djobs = (Lit *)jw;
+    int *stats = (int *)(jw + jt);
+    int64_t *outs = (int64_t *)(jw + jt + st_b);
+    std::vector<size_t> off(n + 1, 0);
+    for (int j = 0; j < n; j++) off[j + 1] = off[j] + lit_batch_sizes(items[j].d).total;
+    char *pool = (char *)ibip_scratch(ctx, SC_LITB, off[n]);
+    if (!pool) return IBIP_ERR_OOM;
+    ibip_prof_begin(ctx, IBIP_K_RANK);
+    // statistics of every image, one read-back
+    cudaMemsetAsync(stats, 0, (size_t)n * 4 * sizeof(int), s);
+    cudaMemsetAsync(outs, 0, (size_t)n * 8 * sizeof(int64_t), s);
+    for (int j = 0; j < n; j++) {
+        ibip_stats_launch(ctx, items[j].dt2, nvox(items[j].d), stats + 4 * j);
+    }
+    int *h = (int *)ctx->h_pinned;   // n <= 4096: 4n ints fit the pinned buffer
+    cudaMemcpyAsync(h, stats, (size_t)n * 4 * sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (ibip_sync(ctx, s) != cudaSuccess) return IBIP_ERR_CUDA;
+    std::vector<int> maxd(n), npore(n), hasinf(n), B(n, 1);
+    for (int j = 0; j < n; j++) { maxd[j] = h[4 * j]; npore[j] = h[4 * j + 1]; hasinf[j] = h[4 * j + 2]; }
+    // present distance values, scanned: the bucket count of every image
+    std::vector<int32_t *> incl(n);
+    for (int j = 0; j < n; j++) {
+        const IbipLitItem &it = items[j];
+        const int64_t N = nvox(it.d);
+        incl[j] = (int32_t *)(pool + off[j]);
+        k_lit_init<<<gs, 256, 0, s>>>(it.dt2, N, it.seq, it.cstep);
+        IBIP_LAUNCH(ctx);
+        if (npore[j] == 0 || hasinf[j]) continue;
+        cudaMemsetAsync(incl[j], 0, ((size_t)maxd[j] + 1) * sizeof(int32_t), s);
+        k_lit_presence<<<gs, 256, 0, s>>>(it.dt2, N, incl[j]);
+        IBIP_LAUNCH(ctx);
+        const int st = ibip_scan_incl_i32(ctx, incl[j], incl[j], (int64_t)maxd[j] + 1);
+        if (st) return st;
+        cudaMemcpyAsync(h + j, incl[j] + maxd[j], sizeof(int), cudaMemcpyDeviceToHost, s);
+    }
+    if (ibip_sync(ctx, s) != cudaSuccess) return IBIP_ERR_CUDA;
+    size_t book = 0;
+    for (int j = 0; j < n; j++) {
+        if (npore[j] > 0 && !hasinf[j]) B[j] = h[j];
+        if (npore[j] > 0) book = std::max(book, (size_t)((B[j] + 31) / 32) * 4 + (size_t)B[j] * 16);
+    }
+    if (book > kLitSmem) return lit_each(ctx, n, items);   // bookkeeping too large for shared memory
+    while (cs > 1 && !lit_cluster_fits(cs, book)) cs /= 2;
+    if (!lit_cluster_fits(cs, book)) return lit_each(ctx, n, items);
+    *cs_used = cs;
+    // buckets, first candidates and the job table
+    std::vector<Lit> jobs;
+    std::vector<int> which;
+    for (int j = 0; j < n; j++) {
+        IbipLitItem &it = items[j];
+        it.n_steps = 0;
+        it.status = IBIP_OK;
+        if (npore[j] == 0) continue;
+        const LitBatchSizes z = lit_batch_sizes(it.d);
+        char *w = pool + off[j] + z.incl;
+        const int64_t N = nvox(it.d);
+        const int nw = (B[j] + 31) / 32;
+        Lit a;
+        a.nx = it.d.nx; a.ny = it.d.ny; a.nz = it.d.nz; a.inlet = it.inlet; a.N = N;
+        a.dt2 = it.dt2; a.seq = it.seq; a.cstep = it.cstep; a.step_r2 = it.step_r2; a.step_count = it.step_count;
+        a.cap = it.cap; a.max_steps = it.max_steps; a.npore = npore[j];
+        a.list = (int32_t *)w;
+        a.bstart = (const int32_t *)(w + z.list);
+        a.bval = (const int32_t *)(w + z.list + z.b4);
+        a.tail = (int32_t *)(w + z.list + 2 * z.b4);
+        a.head = (int32_t *)(w + z.list + 3 * z.b4);
+        int32_t *cnt = (int32_t *)(w + z.list + 4 * z.b4);
+        a.ne = (uint32_t *)(w + z.list + 5 * z.b4);
+        a.queued = (uint32_t *)(w + z.list + 5 * z.b4 + z.ne);
+        a.incl = incl[j];
+        a.B = B[j]; a.hasinf = hasinf[j];
+        a.out = outs + 8 * jobs.size();
+        // tail, head, cnt, ne and the queued plane are contiguous
+        cudaMemsetAsync(a.tail, 0, 3 * z.b4 + z.ne + z.q, s);
+        k_lit_hist<<<gs, 256, 0, s>>>(it.dt2, N, incl[j], B[j], hasinf[j], cnt);
+        IBIP_LAUNCH(ctx);
+        const int st = ibip_scan_excl_i32(ctx, cnt, (int32_t *)a.bstart, B[j]);
+        if (st) return st;
+        k_lit_bval<<<std::max(1, std::min(gs, (maxd[j] + 255) / 256)), 256, 0, s>>>(incl[j], maxd[j], B[j], hasinf[j],
+                                                                                    (int32_t *)a.bval);
+        IBIP_LAUNCH(ctx);
+        const int f = it.inlet >> 1;
+        const int nface = f == 0 ? it.d.ny * it.d.nz : f == 1 ? it.d.nx * it.d.nz : it.d.nx * it.d.ny;
+        k_lit_seed<<<std::max(1, std::min(gs, (nface + 255) / 256)), 256, 0, s>>>(a);
+        IBIP_LAUNCH(ctx);
+        (void)nw;
+        jobs.push_back(a);
+        which.push_back(j);
+    }
+    ibip_prof_end(ctx, IBIP_K_RANK);
+    if (jobs.empty()) return ibip_cuda_status(ibip_sync(ctx, s));
+    const int nj = (int)jobs.size();
+    cudaMemcpyAsync(djobs, jobs.data(), (size_t)nj * sizeof(Lit), cudaMemcpyHostToDevice, s);
+    ibip_prof_begin(ctx, IBIP_K_INVADE);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)(nj * cs));
+    cfg.blockDim = dim3(kLT);
+    cfg.dynamicSmemBytes = book;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_lit_cluster_b, (const Lit *)djobs);
+    if (e != cudaSuccess) return ibip_cuda_status(e);
+    IBIP_LAUNCH(ctx);
+    k_lit_final_b<<<dim3((unsigned)nj, 16), 256, 0, s>>>(djobs);
+    IBIP_LAUNCH(ctx);
+    ibip_prof_end(ctx, IBIP_K_INVADE);
+    int64_t *ho = (int64_t *)ctx->h_pinned;   // 8 int64 per job: nj <= 1024 per read-back
+    for (int c0 = 0; c0 < nj; c0 += 1024) {
+        const int c = std::min(1024, nj - c0);
+        cudaMemcpyAsync(ho, outs + 8 * (size_t)c0, (size_t)c * 8 * sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+        e = ibip_sync(ctx, s);
+        if (e != cudaSuccess) return ibip_cuda_status(e);
+        for (int q = 0; q < c; q++) {
+            IbipLitItem &it = items[which[c0 + q]];
+            it.n_steps = ho[8 * q];
+            it.status = (int)ho[8 * q + 1];
+        }
+    }
+    return IBIP_OK;
+}
+
+}  // namespace
+
+int ibip_literal_batch_run(ibip_ctx *ctx, int n, IbipLitItem *items, int cluster, int *h_cluster)
+{
+    static const int kCand[] = {1, 2, 4, 8, 16};
+    int used = 0;
+    int cs = cluster;
+    if (cs <= 0) {
+        int64_t vox = 0;
+        for (int j = 0; j < n; j++) vox += nvox(items[j].d);
+        int p2 = 0;
+        while (p2 < 62 && ((int64_t)1 << p2) < vox) p2++;
+        const std::string key = "lit_b:" + std::to_string(n) + ":" + std::to_string(p2) + ":" +
+                                std::to_string(ctx->sm_count);
+        int t = 0;
+        if (ctx->autotune && ibip_tune_get(key, &t)) {
+            cs = t;
+        } else if (ctx->autotune) {
+            // time every cluster size on this batch; the runs give identical
+            // results, the last one's stay in the outputs
+            double best = 1e30;
+            int best_cs = 0;
+            cudaEvent_t e0, e1;
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+            for (int c : kCand) {
+                cudaEventRecord(e0, ctx->stream);
+                const int st = lit_batch_once(ctx, n, items, c, &used);
+                cudaEventRecord(e1, ctx->stream);
+                if (st) {
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    return st;
+                }
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (used == c && ms < best) { best = ms; best_cs = c; }
+                if (used != c) break;   // larger clusters cannot be placed either
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            ibip_tune_put(key, best_cs, best * 1e3, ctx->tune_path);
+            if (h_cluster) *h_cluster = best_cs;
+            return IBIP_OK;
+        } else {
+            // enough clusters to fill the SMs: more CTAs per image when few
+            cs = 1;
+            while (cs < 8 && (int64_t)n * cs * 2 <= ctx->sm_count) cs *= 2;
+        }
+    }
+    const int st = lit_batch_once(ctx, n, items, cs, &used);
+    if (h_cluster) *h_cluster = used;
+    return st;
 }

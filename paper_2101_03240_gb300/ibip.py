@@ -51,6 +51,13 @@ class Job(C.Structure):
                 ("sigma", C.c_double), ("theta_deg", C.c_double), ("n_steps", C.c_int64), ("status", C.c_int32)]
 
 
+class LiteralJob(C.Structure):
+    _fields_ = [("image", C.c_void_p), ("dims", Dims), ("inlet", C.c_int32), ("dt2", C.c_void_p),
+                ("max_steps", C.c_int64), ("seq", C.c_void_p), ("cstep", C.c_void_p), ("step_r2", C.c_void_p),
+                ("step_count", C.c_void_p), ("capacity_steps", C.c_int64), ("n_steps", C.c_int64),
+                ("status", C.c_int32)]
+
+
 class Result(C.Structure):
     _fields_ = [("status", C.c_int32), ("slot", C.c_int32), ("n_steps", C.c_int64), ("t_submit_ns", C.c_int64),
                 ("t_start_ns", C.c_int64), ("t_end_ns", C.c_int64), ("mem_reserved", C.c_int64),
@@ -118,6 +125,8 @@ def _lib():
                 "ibip_server_wait": (C.c_int, [P, C.c_uint64, i64, C.POINTER(C.c_int), C.POINTER(Result)]),
                 "ibip_server_stats": (C.c_int, [P, C.POINTER(i64), C.c_int]),
                 "ibip_route_pick": (C.c_int, [C.c_int, C.POINTER(i64), C.POINTER(i64), i64]),
+                "ibip_invade_literal_batched": (C.c_int, [P, i32, P, C.POINTER(C.c_int)]),
+                "ibip_set_literal_cluster": (C.c_int, [P, C.c_int]),
                 "ibip_pc_envelope": (C.c_int, [P, P, Dims, P, i64, P, i32, C.POINTER(i64), C.POINTER(i64)]),
                 "ibip_router_create": (C.c_int, [C.POINTER(P), C.c_int, C.POINTER(C.c_int), C.c_size_t, C.c_int]),
                 "ibip_router_destroy": (C.c_int, [P]),
@@ -401,6 +410,49 @@ class Context:
             raise IbipError("ibip_invade_literal", st)
         K = int(k.value)
         return seq, cstep, r2[:min(K, cap)], cnt[:min(K, cap)], K, st
+
+    def set_literal_cluster(self, cluster: int):
+        """CTAs per image cluster of invade_literal_batched (0 = automatic)."""
+        st = _lib().ibip_set_literal_cluster(self._h, int(cluster))
+        if st != OK:
+            raise IbipError("ibip_set_literal_cluster", st)
+
+    def invade_literal_batched(self, images, inlets=0, max_steps=None):
+        """The paper-literal invasion of many images, each on a thread-block
+        cluster of its own, in one launch (ibip_invade_literal_batched).
+        Returns (list of dicts with seq, cstep, step_r2, step_count, K,
+        status; the cluster size used)."""
+        n = len(images)
+        inl = inlets if isinstance(inlets, (list, tuple)) else [inlets] * n
+        jobs = (LiteralJob * n)()
+        outs = []
+        for j, im in enumerate(images):
+            _need(im, torch.uint8, "image")
+            dev, N = im.device, im.numel()
+            r = {"seq": torch.empty(im.shape, dtype=torch.int32, device=dev),
+                 "cstep": torch.empty(im.shape, dtype=torch.int32, device=dev),
+                 "step_r2": torch.empty(max(N, 1), dtype=torch.int32, device=dev),
+                 "step_count": torch.empty(max(N, 1), dtype=torch.int32, device=dev)}
+            J = jobs[j]
+            J.image = im.data_ptr()
+            J.dims = _dims(im.shape)
+            J.inlet = int(inl[j])
+            J.dt2 = None
+            J.max_steps = -1 if max_steps is None else int(max_steps)
+            J.seq, J.cstep = r["seq"].data_ptr(), r["cstep"].data_ptr()
+            J.step_r2, J.step_count = r["step_r2"].data_ptr(), r["step_count"].data_ptr()
+            J.capacity_steps = N
+            outs.append(r)
+        cs = C.c_int(0)
+        self._stream()
+        st = _lib().ibip_invade_literal_batched(self._h, n, jobs, C.byref(cs))
+        if st not in (OK, ERR_STEP_LIMIT):
+            raise IbipError("ibip_invade_literal_batched", st)
+        for r, J in zip(outs, jobs):
+            K = int(J.n_steps)
+            r["K"], r["status"] = K, int(J.status)
+            r["step_r2"], r["step_count"] = r["step_r2"][:K], r["step_count"][:K]
+        return outs, int(cs.value)
 
     def trapping(self, seq, outlet=1, rerank=False, seq_out=True):
         _need(seq, torch.int32, "seq")
