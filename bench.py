@@ -117,6 +117,9 @@ def parse():
     ap.add_argument("--mio-levels", type=int, default=40)
     ap.add_argument("--autotune", action="store_true",
                     help="tune the EDT tile shapes on the first call of each shape class (before warm-up)")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="single-image lines at N=1: skip the short batch256 and serve measurements added as "
+                         "extra keys")
     return ap.parse_args()
 
 
@@ -197,10 +200,10 @@ def run_batch(args, rank, world):
 
     from paper_2101_03240_gb300 import ibip, synth
 
+    imgs_h = batch_images(256)
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    imgs_h = synth.c4_batch()
     nimg = len(imgs_h)
     nvox_total = sum(a.size for a in imgs_h)
     imgs = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in imgs_h]
@@ -331,6 +334,19 @@ def run_batch(args, rank, world):
 
 
 # -------------------------------------------------------------- serve ----
+
+def _batch_image(i):
+    from paper_2101_03240_gb300 import synth
+    return synth.mixed_image(i, 4000, 32, 160)
+
+
+def batch_images(n):
+    """The 256-image batch (synth.c4_batch: image i is mixed_image(i) of the
+    32^3..160^3 mix), generated by a spawn pool."""
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(min(n, os.cpu_count() or 1)) as pool:
+        return pool.map(_batch_image, range(n))
+
 
 def _request_image(j):
     from paper_2101_03240_gb300 import synth
@@ -955,6 +971,32 @@ def run_reference(args, rank, world):
             "e2e": {"value": v, "unit": "voxels/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def extra_lines(args):
+    """The batched and served forms, measured briefly in the same run as the
+    single-image line (same process, after it): batch256 (3 timed batches
+    after 2 warm-up ones) and the first 200 requests of the Poisson stream
+    (one pass), each without its CPU baseline.  Their own lines
+    (--config batch256 | serve) give the full measurements."""
+    import gc
+
+    import torch
+    gc.collect()
+    torch.cuda.empty_cache()
+    ab = argparse.Namespace(**vars(args))
+    ab.steps, ab.warmup, ab.no_cpu_baseline, ab.rule = 3, 2, True, "frontier"
+    b = run_batch(ab, 0, 1)
+    gc.collect()
+    torch.cuda.empty_cache()
+    sv = argparse.Namespace(**vars(args))
+    sv.steps, sv.warmup, sv.no_cpu_baseline, sv.requests = 1, 1, True, 200
+    s = run_serve(sv, 0, 1)
+    keep_b = ("metric", "value", "unit", "ms_per_step", "steps", "warmup", "per_image_path_images_per_s",
+              "batched_over_per_image", "e2e", "gpu_launches", "clocks", "config")
+    keep_s = ("metric", "value", "unit", "ms_per_step", "latency_ms", "offered_images_per_s", "bit_exact_sample",
+              "e2e", "gpu_launches", "clocks", "config")
+    return {"batch256": {k: b[k] for k in keep_b if k in b}, "serve": {k: s[k] for k in keep_s if k in s}}
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -977,6 +1019,8 @@ def main():
             out = run_serve(args, rank, world)
         else:
             out = run_ours(args, rank, world)
+            if world == 1 and not args.no_extra and args.config == "blobs512":
+                out.update(extra_lines(args))
         if world > 1:
             dist.destroy_process_group()
     if out is not None:
