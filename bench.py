@@ -51,12 +51,25 @@ CLASS_NAMES = ["edt", "rank", "invade", "maximin", "trap", "pc", "dilate"]
 
 # DRAM traffic per voxel and launch of each kernel class, from ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum summed over the class's
-# kernels in one launch of a smaller image of the same kind, divided by its
-# voxels; the profiles/ summary named in "capture" gives the command and the
-# figures).  "src" lists the sources the counters were taken on with the
-# first 16 hex digits of their SHA-256: when one has changed since, the
-# class reports traffic null.
-NCU_TRAFFIC = {}
+# kernels in one launch on the named workload, divided by its voxels; the
+# profiles/ summary named in "capture" gives the command and the figures).
+# "src" lists the sources the counters were taken on with the first 16 hex
+# digits of their SHA-256: when one has changed since, or the line runs
+# another workload, the class reports traffic null.
+NCU_TRAFFIC = {
+    "edt": {"bytes_per_voxel": 15.698, "src": {"paper_2101_03240_gb300/csrc/edt.cu": "1dad9f25dc064510"},
+             "workload": "blobs512", "capture": "profiles/traffic_blobs512.md"},
+    "rank": {"bytes_per_voxel": 45.015, "src": {"paper_2101_03240_gb300/csrc/invade.cu": "d7c5962ee673defc", "paper_2101_03240_gb300/csrc/scan.cu": "7ae2dbb22ecb3ed4"},
+             "workload": "blobs512", "capture": "profiles/traffic_blobs512.md"},
+    "maximin": {"bytes_per_voxel": 190.906, "src": {"paper_2101_03240_gb300/csrc/maximin.cu": "9b942593e4c89a39"},
+             "workload": "blobs512", "capture": "profiles/traffic_blobs512.md"},
+    "trap": {"bytes_per_voxel": 12.613, "src": {"paper_2101_03240_gb300/csrc/pc.cu": "eb392979ed4ea0da"},
+             "workload": "blobs512", "capture": "profiles/traffic_blobs512.md"},
+    "pc": {"bytes_per_voxel": 4.631, "src": {"paper_2101_03240_gb300/csrc/pc.cu": "eb392979ed4ea0da", "paper_2101_03240_gb300/csrc/scan.cu": "7ae2dbb22ecb3ed4"},
+             "workload": "blobs512", "capture": "profiles/traffic_blobs512.md"},
+    "dilate": {"bytes_per_voxel": 14.725, "src": {"paper_2101_03240_gb300/csrc/edt.cu": "1dad9f25dc064510"},
+             "workload": "blobs512", "capture": "profiles/traffic_blobs512.md"},
+}
 
 
 def source_sha16(rel):
@@ -65,11 +78,12 @@ def source_sha16(rel):
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def traffic_per_launch(cls, units):
-    """ncu DRAM bytes of one launch of class `cls` scaled to `units` voxels,
-    or None when not captured or captured on sources that changed since."""
+def traffic_per_launch(cls, units, workload="blobs512"):
+    """ncu DRAM bytes of one launch of class `cls` on `units` voxels of
+    `workload`, or None when not captured on that workload or captured on
+    sources that changed since."""
     t = NCU_TRAFFIC.get(cls)
-    if not t:
+    if not t or t.get("workload") != workload:
         return None
     try:
         if any(source_sha16(f) != h for f, h in t["src"].items()):
@@ -769,13 +783,13 @@ def run_ours(args, rank, world):
             continue
         ach = kinfo[c]["algorithmic_GBps"]
         hbm_kernels[c] = {"bound": "hbm", "achieved": round(ach, 3), "peak": hbm_peak, "unit": "GB/s",
-                          "frac": ach / hbm_peak, "traffic": traffic_per_launch(c, N),
+                          "frac": ach / hbm_peak, "traffic": traffic_per_launch(c, N, w.name),
                           "algorithmic_bytes_per_launch": int(alg[c]),
                           "ms_per_launch": kinfo[c]["ms_per_span"], "launches_per_step": kinfo[c]["spans"]}
     per_launch = prof[dom][0] / max(prof[dom][1], 1)
     achieved = alg[dom] / (per_launch * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 3), "peak": hbm_peak,
-                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic_per_launch(dom, N),
+                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic_per_launch(dom, N, w.name),
                 "peak_source": "measured" if pk else "fallback",
                 "note": "the invasion is a serial, latency-bound loop on one CTA: its HBM bytes are the "
                         "algorithmic minimum (dt2 read + seq write + step arrays) and its figure of merit is "

@@ -58,3 +58,17 @@ def test_oracle_sample_is_a_corner_cube_of_large_images(monkeypatch):
     assert sw.inlet == w.inlet and sw.outlet == w.outlet and sw.name == "blobs48_corner20"
     d = O.edt(sw.image)
     assert levels == synth.mio_levels(int(d[sw.image > 0].max()), 40)
+
+
+def test_traffic_is_null_when_sources_or_workload_differ(monkeypatch):
+    """The bench line's ncu traffic holds only for the captured workload and
+    the sources it was captured on (checked by their SHA-256)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    for c, t in bench.NCU_TRAFFIC.items():
+        assert t["workload"] == "blobs512" and t["src"] and t["bytes_per_voxel"] > 0
+        assert bench.traffic_per_launch(c, 1000) == t["bytes_per_voxel"] * 1000
+        assert bench.traffic_per_launch(c, 1000, "spheres200") is None
+    assert bench.traffic_per_launch("invade", 1000) is None
+    monkeypatch.setattr(bench, "source_sha16", lambda rel: "0" * 16)
+    assert all(bench.traffic_per_launch(c, 1000) is None for c in bench.NCU_TRAFFIC)
