@@ -38,7 +38,7 @@
 namespace {
 
 constexpr int kM = 64;           // batch size (items per iteration)
-constexpr int kNT = 384;         // threads of the persistent CTA
+constexpr int kNT = 768;         // threads of the persistent CTA (measured: 384, 512, 640, 768, 896, 1024 -> 1742, 1626, 1517, 1493, 1509, 1564 ms on the 512^3 blobs)
 constexpr int kChunk = 4096;     // voxels per rank-sort chunk (minimum)
 constexpr int kSmemL1Max = 12288;   // level-1 words of one image of a batched call (shared memory)
 constexpr int kNOut = kInvStats;   // int64 outputs of the invasion kernel
