@@ -59,15 +59,15 @@ CLASS_NAMES = ["edt", "rank", "invade", "maximin", "trap", "pc", "dilate"]
 NCU_TRAFFIC = {
     "edt": {"bytes_per_voxel": 15.698, "src": {"paper_2101_03240_gb300/csrc/edt.cu": "1dad9f25dc064510"},
              "workload": "blobs512", "capture": "profiles/traffic_blobs512.md"},
-    "rank": {"bytes_per_voxel": 45.015, "src": {"paper_2101_03240_gb300/csrc/invade.cu": "d7c5962ee673defc", "paper_2101_03240_gb300/csrc/scan.cu": "7ae2dbb22ecb3ed4"},
+    "rank": {"bytes_per_voxel": 44.966, "src": {"paper_2101_03240_gb300/csrc/invade.cu": "0f50d49a6694434e", "paper_2101_03240_gb300/csrc/scan.cu": "7ae2dbb22ecb3ed4"},
              "workload": "blobs512", "capture": "profiles/traffic_blobs512.md"},
-    "maximin": {"bytes_per_voxel": 190.906, "src": {"paper_2101_03240_gb300/csrc/maximin.cu": "9b942593e4c89a39"},
+    "maximin": {"bytes_per_voxel": 181.487, "src": {"paper_2101_03240_gb300/csrc/maximin.cu": "9b942593e4c89a39"},
              "workload": "blobs512", "capture": "profiles/traffic_blobs512.md"},
     "trap": {"bytes_per_voxel": 12.613, "src": {"paper_2101_03240_gb300/csrc/pc.cu": "eb392979ed4ea0da"},
              "workload": "blobs512", "capture": "profiles/traffic_blobs512.md"},
-    "pc": {"bytes_per_voxel": 4.631, "src": {"paper_2101_03240_gb300/csrc/pc.cu": "eb392979ed4ea0da", "paper_2101_03240_gb300/csrc/scan.cu": "7ae2dbb22ecb3ed4"},
+    "pc": {"bytes_per_voxel": 4.630, "src": {"paper_2101_03240_gb300/csrc/pc.cu": "eb392979ed4ea0da", "paper_2101_03240_gb300/csrc/scan.cu": "7ae2dbb22ecb3ed4"},
              "workload": "blobs512", "capture": "profiles/traffic_blobs512.md"},
-    "dilate": {"bytes_per_voxel": 14.725, "src": {"paper_2101_03240_gb300/csrc/edt.cu": "1dad9f25dc064510"},
+    "dilate": {"bytes_per_voxel": 14.724, "src": {"paper_2101_03240_gb300/csrc/edt.cu": "1dad9f25dc064510"},
              "workload": "blobs512", "capture": "profiles/traffic_blobs512.md"},
 }
 
