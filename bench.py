@@ -61,6 +61,8 @@ NCU_TRAFFIC = {
              "workload": "blobs512", "capture": "profiles/traffic_blobs512.md"},
     "rank": {"bytes_per_voxel": 44.966, "src": {"paper_2101_03240_gb300/csrc/invade.cu": "0f50d49a6694434e", "paper_2101_03240_gb300/csrc/scan.cu": "7ae2dbb22ecb3ed4"},
              "workload": "blobs512", "capture": "profiles/traffic_blobs512.md"},
+    "invade": {"bytes_per_voxel": 38.414, "src": {"paper_2101_03240_gb300/csrc/invade.cu": "0f50d49a6694434e"},
+               "workload": "blobs512", "capture": "profiles/k_invade_blobs512_traffic.md"},
     "maximin": {"bytes_per_voxel": 181.487, "src": {"paper_2101_03240_gb300/csrc/maximin.cu": "9b942593e4c89a39"},
              "workload": "blobs512", "capture": "profiles/traffic_blobs512.md"},
     "trap": {"bytes_per_voxel": 12.613, "src": {"paper_2101_03240_gb300/csrc/pc.cu": "eb392979ed4ea0da"},
@@ -791,10 +793,11 @@ def run_ours(args, rank, world):
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 3), "peak": hbm_peak,
                 "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic_per_launch(dom, N, w.name),
                 "peak_source": "measured" if pk else "fallback",
-                "note": "the invasion is a serial, latency-bound loop on one CTA: its HBM bytes are the "
-                        "algorithmic minimum (dt2 read + seq write + step arrays) and its figure of merit is "
-                        "the step latency (invasion_step_times, invasion_us_per_step); hbm_kernels holds the "
-                        "HBM-bound classes against the measured copy bandwidth",
+                "note": "the invasion is a serial, latency-bound loop on one CTA: achieved counts its "
+                        "algorithmic bytes (dt2 read + seq write + step arrays), traffic is ncu's DRAM bytes per "
+                        "launch (lines re-read between overlapping balls); its figure of merit is the step "
+                        "latency (invasion_step_times, invasion_us_per_step); hbm_kernels holds the HBM-bound "
+                        "classes against the measured copy bandwidth",
                 "hbm_kernels": hbm_kernels}
     us_per_step = prof["invade"][0] / max(args.steps, 1) * 1e3 / max(K, 1)
 

@@ -69,6 +69,6 @@ def test_traffic_is_null_when_sources_or_workload_differ(monkeypatch):
         assert t["workload"] == "blobs512" and t["src"] and t["bytes_per_voxel"] > 0
         assert bench.traffic_per_launch(c, 1000) == t["bytes_per_voxel"] * 1000
         assert bench.traffic_per_launch(c, 1000, "spheres200") is None
-    assert bench.traffic_per_launch("invade", 1000) is None
+    assert bench.traffic_per_launch("no_such_class", 1000) is None
     monkeypatch.setattr(bench, "source_sha16", lambda rel: "0" * 16)
     assert all(bench.traffic_per_launch(c, 1000) is None for c in bench.NCU_TRAFFIC)
