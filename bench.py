@@ -230,12 +230,12 @@ def run_batch(args, rank, world):
 
     paper = args.rule == "paper"
 
-    def batched():
+    def batched(images=imgs):
         if paper:   # EDT + the paper-literal invasion, one thread-block cluster per image
-            res, cs = ctx.invade_literal_batched(imgs, 0)
+            res, cs = ctx.invade_literal_batched(images, 0)
             batched.cluster = cs
             return res
-        return ctx.invade_batched(imgs, 0, 1, trapping=True, curve=True)
+        return ctx.invade_batched(images, 0, 1, trapping=True, curve=True)
 
     def single():
         out = []
@@ -281,18 +281,31 @@ def run_batch(args, rank, world):
     torch.cuda.synchronize()
     single_s = time.perf_counter() - t0
     assert Ks == [r["K"] for r in res]
-    # end to end: host images in, seq_out out
-    pins = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in imgs_h]
-    outs = [torch.empty(a.shape, dtype=torch.int32).pin_memory() for a in imgs_h]
+    # end to end: host images in, seq_out out.  The caller keeps the batch
+    # packed back to back in one pinned buffer, so one copy brings it in
+    # (the device images are views of one buffer) and one copy takes the
+    # packed sequence images back (gathered on the device first).
+    offs = np.concatenate([[0], np.cumsum([a.size for a in imgs_h])]).astype(np.int64)
+    pin_in = torch.from_numpy(np.concatenate([a.reshape(-1) for a in imgs_h])).pin_memory()
+    pin_out = torch.empty(nvox_total, dtype=torch.int32).pin_memory()
+    dev_in = torch.empty(nvox_total, dtype=torch.uint8, device=dev)
+    views = [dev_in[int(offs[i]):int(offs[i + 1])].view(a.shape) for i, a in enumerate(imgs_h)]
+    e2e_ms = []
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for d, p_ in zip(imgs, pins):
-        d.copy_(p_, non_blocking=True)
-    res = batched()
-    for o, r in zip(outs, res):
-        o.copy_(r["seq"] if paper else r["seq_out"], non_blocking=True)
-    torch.cuda.synchronize()
-    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+    for _ in range(max(args.steps, 1)):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        dev_in.copy_(pin_in, non_blocking=True)
+        res = batched(views)
+        packed = torch.cat([(r["seq"] if paper else r["seq_out"]).reshape(-1) for r in res])
+        pin_out.copy_(packed, non_blocking=True)
+        b.record()
+        torch.cuda.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+    if not np.array_equal(pin_out.numpy(), packed.cpu().numpy()):
+        raise RuntimeError("batch e2e: the copied-back results differ from the device results")
+    e2e_s = max_over_ranks(sum(e2e_ms) / len(e2e_ms) * 1e-3, world, dev)
     if rank != 0:
         return None
     tot = sum(v[0] for v in prof.values()) or 1.0
