@@ -93,6 +93,16 @@ IBIP_API int ibip_set_stream(ibip_ctx *ctx, void *cuda_stream);
  * default stream reads as cudaStreamLegacy only if it was given as such). */
 IBIP_API int ibip_get_stream(const ibip_ctx *ctx, void **h_stream);
 
+/* Whether this context's kernels may run beside long-running kernels of
+ * other streams or contexts on the same device (on != 0), for instance an
+ * invasion running on another stream while this context computes the
+ * opening.  The widest-path propagation (trapping, the opening's trim) then
+ * runs one ordinary launch per round, the host reading the next round's
+ * list size every 16 rounds, instead of one cooperative grid, whose blocks
+ * must all be resident at once.  Results are the same either way.  Default
+ * off; server slots always run this way.  IBIP_ERR_ARG for a NULL ctx. */
+IBIP_API int ibip_set_shared_device(ibip_ctx *ctx, int on);
+
 /* Squared Euclidean distance transform of the pore space (Section 2.1,
  * Figure 2b).
  *   image: uint8[nx*ny*nz], nonzero = pore.

@@ -611,6 +611,13 @@ int ibip_invade_literal_batched(ibip_ctx *ctx, int32_t n, ibip_literal_job *jobs
     return first;
 }
 
+int ibip_set_shared_device(ibip_ctx *ctx, int on)
+{
+    if (!ctx) return IBIP_ERR_ARG;
+    ctx->no_coop = on ? 1 : 0;
+    return IBIP_OK;
+}
+
 int ibip_set_literal_cluster(ibip_ctx *ctx, int cluster)
 {
     if (!ctx || !(cluster == 0 || cluster == 1 || cluster == 2 || cluster == 4 || cluster == 8 || cluster == 16))

@@ -127,6 +127,7 @@ def _lib():
                 "ibip_route_pick": (C.c_int, [C.c_int, C.POINTER(i64), C.POINTER(i64), i64]),
                 "ibip_invade_literal_batched": (C.c_int, [P, i32, P, C.POINTER(C.c_int)]),
                 "ibip_set_literal_cluster": (C.c_int, [P, C.c_int]),
+                "ibip_set_shared_device": (C.c_int, [P, C.c_int]),
                 "ibip_pc_envelope": (C.c_int, [P, P, Dims, P, i64, P, i32, C.POINTER(i64), C.POINTER(i64)]),
                 "ibip_router_create": (C.c_int, [C.POINTER(P), C.c_int, C.POINTER(C.c_int), C.c_size_t, C.c_int]),
                 "ibip_router_destroy": (C.c_int, [P]),
@@ -410,6 +411,15 @@ class Context:
             raise IbipError("ibip_invade_literal", st)
         K = int(k.value)
         return seq, cstep, r2[:min(K, cap)], cnt[:min(K, cap)], K, st
+
+    def set_shared_device(self, on: bool):
+        """Let this context's kernels run beside long-running kernels of
+        other streams (ibip_set_shared_device): the widest-path propagation
+        then runs one ordinary launch per round instead of a cooperative
+        grid."""
+        st = _lib().ibip_set_shared_device(self._h, int(bool(on)))
+        if st != OK:
+            raise IbipError("ibip_set_shared_device", st)
 
     def set_literal_cluster(self, cluster: int):
         """CTAs per image cluster of invade_literal_batched (0 = automatic)."""

@@ -58,6 +58,8 @@ def test_null_arguments_rejected_on_host(lib):
     assert lib.ibip_get_stream(None, C.byref(out)) == -1
     lib.ibip_set_stream.argtypes = [C.c_void_p, C.c_void_p]
     assert lib.ibip_set_stream(None, None) == -1
+    lib.ibip_set_shared_device.argtypes = [C.c_void_p, C.c_int]
+    assert lib.ibip_set_shared_device(None, 1) == -1
 
 
 def test_oracle_and_cuda_path_share_nothing():
