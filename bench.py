@@ -59,17 +59,17 @@ CLASS_NAMES = ["edt", "rank", "invade", "maximin", "trap", "pc", "dilate"]
 NCU_TRAFFIC = {
     "edt": {"bytes_per_voxel": 15.699, "src": {"paper_2101_03240_gb300/csrc/edt.cu": "1dad9f25dc064510"},
              "workload": "blobs512", "capture": "profiles/traffic_blobs512.md"},
-    "rank": {"bytes_per_voxel": 44.986, "src": {"paper_2101_03240_gb300/csrc/invade.cu": "0f50d49a6694434e", "paper_2101_03240_gb300/csrc/scan.cu": "7ae2dbb22ecb3ed4"},
+    "rank": {"bytes_per_voxel": 45.067, "src": {"paper_2101_03240_gb300/csrc/invade.cu": "0f50d49a6694434e", "paper_2101_03240_gb300/csrc/scan.cu": "7ae2dbb22ecb3ed4"},
              "workload": "blobs512", "capture": "profiles/traffic_blobs512.md"},
-    "maximin": {"bytes_per_voxel": 293.399, "src": {"paper_2101_03240_gb300/csrc/maximin.cu": "9b942593e4c89a39"},
+    "maximin": {"bytes_per_voxel": 300.551, "src": {"paper_2101_03240_gb300/csrc/maximin.cu": "656b6e616e93922b"},
              "workload": "blobs512", "capture": "profiles/traffic_blobs512.md"},
-    "maximin_trim": {"bytes_per_voxel": 109.263, "src": {"paper_2101_03240_gb300/csrc/maximin.cu": "9b942593e4c89a39"},
+    "maximin_trim": {"bytes_per_voxel": 105.892, "src": {"paper_2101_03240_gb300/csrc/maximin.cu": "656b6e616e93922b"},
              "workload": "blobs512", "capture": "profiles/traffic_blobs512.md"},
-    "trap": {"bytes_per_voxel": 12.613, "src": {"paper_2101_03240_gb300/csrc/pc.cu": "eb392979ed4ea0da"},
+    "trap": {"bytes_per_voxel": 12.615, "src": {"paper_2101_03240_gb300/csrc/pc.cu": "eb392979ed4ea0da"},
              "workload": "blobs512", "capture": "profiles/traffic_blobs512.md"},
-    "pc": {"bytes_per_voxel": 4.634, "src": {"paper_2101_03240_gb300/csrc/pc.cu": "eb392979ed4ea0da", "paper_2101_03240_gb300/csrc/scan.cu": "7ae2dbb22ecb3ed4"},
+    "pc": {"bytes_per_voxel": 4.631, "src": {"paper_2101_03240_gb300/csrc/pc.cu": "eb392979ed4ea0da", "paper_2101_03240_gb300/csrc/scan.cu": "7ae2dbb22ecb3ed4"},
              "workload": "blobs512", "capture": "profiles/traffic_blobs512.md"},
-    "dilate": {"bytes_per_voxel": 14.722, "src": {"paper_2101_03240_gb300/csrc/edt.cu": "1dad9f25dc064510"},
+    "dilate": {"bytes_per_voxel": 14.721, "src": {"paper_2101_03240_gb300/csrc/edt.cu": "1dad9f25dc064510"},
              "workload": "blobs512", "capture": "profiles/traffic_blobs512.md"},
     "invade": {"bytes_per_voxel": 38.414, "src": {"paper_2101_03240_gb300/csrc/invade.cu": "0f50d49a6694434e"},
                "workload": "blobs512", "capture": "profiles/k_invade_blobs512_traffic.md"},

@@ -55,7 +55,7 @@ typedef enum {
     IBIP_ERR_CUDA = -2,          /* a CUDA runtime call failed */
     IBIP_ERR_OOM = -3,           /* scratch allocation failed */
     IBIP_ERR_STEP_LIMIT = -4,    /* invasion stopped at max_steps with candidates left */
-    IBIP_ERR_NOT_CONVERGED = -5, /* propagation hit its round limit */
+    IBIP_ERR_NOT_CONVERGED = -5, /* propagation hit its round or activation limit, or stalled */
     IBIP_ERR_CANCELLED = -6,     /* the invasion stopped at a cancel request (ibip_cancel) */
     IBIP_ERR_BOUNDS = -7,        /* a device-side index check failed (progress guard; any
                                     index of the invasion loop in a build with IBIP_CHECKED) */
@@ -98,8 +98,11 @@ IBIP_API int ibip_get_stream(const ibip_ctx *ctx, void **h_stream);
  * invasion running on another stream while this context computes the
  * opening.  The widest-path propagation (trapping, the opening's trim) then
  * runs one ordinary launch per round, the host reading the next round's
- * list size every 16 rounds, instead of one cooperative grid, whose blocks
- * must all be resident at once.  Results are the same either way.  Default
+ * list size every 16 rounds, so that the other streams' blocks get in
+ * between rounds.  It never runs as one cooperative grid, whose blocks must
+ * all be resident at once, nor on its work queue, whose resident blocks
+ * would hold the SMs until the propagation ends; those serve a context
+ * that has the device to itself.  Results are the same every way.  Default
  * off; server slots always run this way.  IBIP_ERR_ARG for a NULL ctx. */
 IBIP_API int ibip_set_shared_device(ibip_ctx *ctx, int on);
 
@@ -554,9 +557,10 @@ IBIP_API int ibip_profile_read(ibip_ctx *ctx, int cls, double *h_ms, int64_t *h_
  *   24-25 bound stages 1 (shell listing) and 2 (rank lookups),
  *   26-27 commit stage 1 (stamping) and the rest (queueing),
  *   28-29 and 33 the single-voxel loop's gather, bound and commit cycles,
- *   30-32 rounds, tile activations and relaxation sweeps of the context's
- *   last widest-path propagation (trapping or the opening's trim,
- *   one-launch form),
+ *   30-32 rounds (0 on the work queue, none counted in per-round
+ *   launches), tile activations and relaxation
+ *   sweeps of the context's last widest-path propagation (trapping or the
+ *   opening's trim),
  *   34 out-of-range accesses counted by a checked build (IBIP_CHECKED),
  *   35 rank of the first voxel with the smallest dt2,
  *   36 batches seen by the trace (ibip_invade_trace; counted beyond its

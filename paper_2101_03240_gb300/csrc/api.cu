@@ -852,7 +852,7 @@ const char *ibip_status_string(int s)
     case IBIP_ERR_CUDA: return "CUDA runtime error";
     case IBIP_ERR_OOM: return "out of device memory";
     case IBIP_ERR_STEP_LIMIT: return "step limit reached with candidates left";
-    case IBIP_ERR_NOT_CONVERGED: return "propagation did not converge within its round limit";
+    case IBIP_ERR_NOT_CONVERGED: return "propagation did not converge within its round or activation limit";
     case IBIP_ERR_CANCELLED: return "cancelled";
     case IBIP_ERR_BOUNDS: return "device index check failed";
     case IBIP_ERR_TOO_LARGE: return "image exceeds the fixed scratch of ibip_edt_noalloc (2^21 voxels)";

@@ -18,7 +18,8 @@
 //     side by side on different SMs; their EDT, rank, trapping and curve
 //     kernels interleave on the other streams.  Trapping uses the per-round
 //     launches of the widest-path propagation, never a cooperative grid,
-//     whose residency could not be guaranteed beside other streams' kernels.
+//     whose residency could not be guaranteed beside other streams' kernels,
+//     nor its work queue, whose resident blocks would hold the SMs.
 #include <chrono>
 #include <condition_variable>
 #include <deque>
