@@ -220,8 +220,14 @@ int batch_post_group(BatchPost &P, const std::vector<int> &group, bool shared_de
         mj.push_back(IbipMaximinJob{J.seq, J.dims, J.outlet, P.M + P.M_off[j]});
         mj_of.push_back(j);
     }
+    // Beside the batch's last running invasion CTAs no cooperative grid may
+    // start.  Several images run on the widest path's work queue, whose
+    // blocks take the free SMs without needing all to be resident (the
+    // remaining invasion CTAs are resident already, so nothing waits for
+    // those SMs); a single image, which could get the cooperative rounds,
+    // runs one launch per round instead.
     const int keep_nc = ctx->no_coop;
-    ctx->no_coop = shared_device ? 1 : keep_nc;   // beside a running kernel: no cooperative grid
+    ctx->no_coop = shared_device && mj.size() == 1 ? 1 : keep_nc;
     int st = mj.empty() ? IBIP_OK : ibip_maximin_multi(ctx, (int)mj.size(), mj.data(), kMaxRounds);
     ctx->no_coop = keep_nc;
     if (st) {
