@@ -505,12 +505,18 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_mm_queue(MMQ Q)
             if (lz[k] == 0 && mv > sM[hx][hy][0]) s_wake[4] = 1;
             if (lz[k] == TZ - 1 && mv > sM[hx][hy][TZ + 1]) s_wake[5] = 1;
         }
+        // A tile woken again while it is being relaxed can be taken by
+        // another block before this one finishes, so two blocks may relax
+        // it at once; the one that loaded older values must not overwrite
+        // the other's.  Only risen voxels are written, by atomic maximum:
+        // the field never falls.
         if (any) {
 #pragma unroll
             for (int k = 0; k < kPer; k++) {
                 const int x = x0 + lx[k], y = y0 + ly[k], z = z0 + lz[k];
-                if (x < J.nx && y < J.ny && z < J.nz && sval[k] != 0)
-                    J.M[d_lin(x, y, z, J.ny, J.nz)] = sM[lx[k] + 1][ly[k] + 1][lz[k] + 1];
+                const int mv = sM[lx[k] + 1][ly[k] + 1][lz[k] + 1];
+                if (x < J.nx && y < J.ny && z < J.nz && sval[k] != 0 && mv > mold[k])
+                    atomicMax(J.M + d_lin(x, y, z, J.ny, J.nz), mv);
             }
         }
         // the field's stores are visible before any neighbour is queued
