@@ -61,9 +61,9 @@ NCU_TRAFFIC = {
              "workload": "blobs512", "capture": "profiles/traffic_blobs512.md"},
     "rank": {"bytes_per_voxel": 45.067, "src": {"paper_2101_03240_gb300/csrc/invade.cu": "0f50d49a6694434e", "paper_2101_03240_gb300/csrc/scan.cu": "7ae2dbb22ecb3ed4"},
              "workload": "blobs512", "capture": "profiles/traffic_blobs512.md"},
-    "maximin": {"bytes_per_voxel": 300.551, "src": {"paper_2101_03240_gb300/csrc/maximin.cu": "80c5b824feea7733"},
+    "maximin": {"bytes_per_voxel": 300.551, "src": {"paper_2101_03240_gb300/csrc/maximin.cu": "2a905a8c9742daf6"},
              "workload": "blobs512", "capture": "profiles/traffic_blobs512.md"},
-    "maximin_trim": {"bytes_per_voxel": 105.892, "src": {"paper_2101_03240_gb300/csrc/maximin.cu": "80c5b824feea7733"},
+    "maximin_trim": {"bytes_per_voxel": 105.892, "src": {"paper_2101_03240_gb300/csrc/maximin.cu": "2a905a8c9742daf6"},
              "workload": "blobs512", "capture": "profiles/traffic_blobs512.md"},
     "trap": {"bytes_per_voxel": 12.615, "src": {"paper_2101_03240_gb300/csrc/pc.cu": "eb392979ed4ea0da"},
              "workload": "blobs512", "capture": "profiles/traffic_blobs512.md"},

@@ -47,8 +47,9 @@ constexpr int kMinBlocks = 4;
 constexpr int kMaxRoundsDev = 1 << 16;
 // Single images of fewer tiles use the queue.  Measured with both schedules
 // (trapping of the 200^3 sphere pack, 8,750 tiles: rounds 3.50 ms, queue
-// 2.24 ms; of the 512^3 blobs, 131,072 tiles: 37.2 / 43.0 ms); the bound
-// is the geometric midpoint of the two.
+// 2.24 ms; of the 512^3 blobs, 131,072 tiles: 37.2 / 43.0 ms; the queue
+// then still stored whole tiles, before its atomic write-back of risen
+// voxels); the bound is the geometric midpoint of the two.
 constexpr int kQueueTiles = 32768;
 // a queue block that waits for work gives up, and stops the propagation
 // with an error status, once the grid has made no progress for this long
